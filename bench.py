@@ -1,0 +1,332 @@
+"""Benchmark: all-neighbour self-search of 1,000,000 synthetic CDR3 sequences
+at Levenshtein distance <= 2 (Appendix A, XTNeighbor steps 0-7) on one GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+A step is one xtn_search_self call over the resident 1M-sequence input
+(encode, expand, sort, group, emit, pair sort, dedup + verify, count readback).
+`value` is verified pairs per second with inputs already in HBM; `e2e` is the
+same metric through the C ABI with pinned host buffers (host->device copy of
+the sequences and device->host copy of the result rows inside every step).
+Under torchrun each rank runs an independent replica (the search has no
+exchange step on one GPU), the slowest rank's time is used and `value` counts
+the pairs of all ranks.  `--impl reference` times the CPU oracle instead, on
+a bounded prefix of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cdr3_synth as gen  # noqa: E402
+
+WORKLOAD = gen.SELF_1M
+METRIC = "1M-seq d≤2 all-neighbour search time (s), verified pairs/s; query p50/p99 ms"
+UNIT = "verified pairs/s"
+L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE_N = 100_000
+ROOFLINE_KERNEL = "k_onesweep_records"
+ROOFLINE_SOURCE = os.path.join(ROOT, "paper_2403_09010_gb300", "csrc", "k_radix.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_onesweep_records_traffic.txt")
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic_per_record():
+    """DRAM bytes per sorted record from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    kv = dict(l.split("=", 1) for l in text.splitlines() if "=" in l and not l.startswith("#"))
+    src_hash = hashlib.sha256(open(ROOFLINE_SOURCE, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha256_16", "").strip() != src_hash:
+        return None
+    try:
+        return float(kv["dram_bytes_per_record"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_arm(args):
+    """--impl reference: the CPU oracle, as it stands, on a bounded prefix."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    seqs, off = gen.workload(WORKLOAD)
+    # size the per-step sample so warm-up + timed steps take ~2.5 minutes
+    t0 = time.perf_counter()
+    oracle.symdel_self(seqs[: off[5000]], off[:5001], WORKLOAD.d)
+    per_seq = max((time.perf_counter() - t0) / 5000, 1e-7)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n_s = int(min(CPU_SAMPLE_N, max(2000, budget / per_seq)))
+    s_seqs, s_off = seqs[: off[n_s]], off[: n_s + 1]
+    for _ in range(args.warmup):
+        oracle.symdel_self(s_seqs, s_off, WORKLOAD.d)
+    times, pairs = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rows = oracle.symdel_self(s_seqs, s_off, WORKLOAD.d)
+        times.append(time.perf_counter() - t0)
+        pairs = rows.shape[0]
+    total = sum(times)
+    value = pairs * args.steps / total
+    sample = f"first {n_s:,} sequences of the {WORKLOAD.n:,}-sequence d={WORKLOAD.d} workload"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.name, "n": WORKLOAD.n, "d": WORKLOAD.d,
+                   "sample_n": n_s, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def cpu_baseline():
+    import oracle
+    oracle.build()
+    seqs, off = gen.workload(WORKLOAD, CPU_SAMPLE_N)
+    t0 = time.perf_counter()
+    rows = oracle.symdel_self(seqs, off, WORKLOAD.d)
+    dt = time.perf_counter() - t0
+    return {"value": rows.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE_N:,} sequences of the {WORKLOAD.n:,}-sequence "
+                      f"d={WORKLOAD.d} workload, single thread, {dt:.1f} s, "
+                      f"{rows.shape[0]:,} pairs"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="xtn", choices=["xtn", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_oracle_arm(args)
+
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2403_09010_gb300 as xtn
+    from paper_2403_09010_gb300 import native
+    xtn.build()
+    lib = native.lib()
+
+    seqs, off = gen.workload(WORKLOAD)
+    n = off.size - 1
+    d_seqs = torch.from_numpy(seqs).cuda()
+    d_off = torch.from_numpy(off).cuda()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(d_seqs.data_ptr())
+    op = ctypes.c_void_p(d_off.data_ptr())
+    st = ctypes.c_void_p(stream.cuda_stream)
+    n_out = ctypes.c_int64(0)
+
+    # size the output once (a user would keep this buffer too)
+    rc = lib.xtn_search_self(sp, op, n, WORKLOAD.d, None, 0, None, 0, ctypes.byref(n_out), st)
+    assert rc in (0, native.XTN_ERR_BUFFER_TOO_SMALL), native.status_string(rc)
+    cap = int(n_out.value * 1.1) + 1024
+    out = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
+    outp = ctypes.c_void_p(out.data_ptr())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        r = lib.xtn_search_self(sp, op, n, WORKLOAD.d, None, 0, outp, cap, ctypes.byref(n_out), st)
+        if r != 0:
+            raise native.XtnError(r, "xtn_search_self")
+        return n_out.value
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    xtn.profile_report()          # clear
+    xtn.profile_enable(True)
+    pairs = 0
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k)                       # L2 flush outside the timed events
+            ev[k][0].record(stream)
+            pairs = step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    xtn.profile_enable(False)
+    prof = xtn.profile_report()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        torch.distributed.barrier()
+    value = pairs * args.steps * world / total_s
+    launches = sum(v[0] for v in prof.values())
+
+    # end to end through the C ABI with pinned host buffers
+    h_seqs = torch.from_numpy(seqs).pin_memory()
+    h_off = torch.from_numpy(off).pin_memory()
+    h_out = torch.empty((cap, 3), dtype=torch.int32).pin_memory()
+    hsp, hop, hout = (ctypes.c_void_p(t.data_ptr()) for t in (h_seqs, h_off, h_out))
+    e2e_steps = max(3, min(args.steps, 20))
+    lib.xtn_search_self(hsp, hop, n, WORKLOAD.d, None, 0, hout, cap, ctypes.byref(n_out), st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = lib.xtn_search_self(hsp, hop, n, WORKLOAD.d, None, 0, hout, cap,
+                                 ctypes.byref(n_out), st)
+        assert rc == 0, native.status_string(rc)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel
+    peak, peak_kind = _peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roofline = None
+    if top:
+        name, (nl, ms, nbytes) = top
+        achieved = nbytes / (ms / 1000.0) / 1e9
+        tpr = _traffic_per_record() if name == ROOFLINE_KERNEL else None
+        n_rec_per_launch = nbytes / nl / 16.0 if name == ROOFLINE_KERNEL else None
+        roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": (tpr * n_rec_per_launch) if tpr and n_rec_per_launch else None,
+                    "algorithmic_bytes_per_launch": nbytes / nl,
+                    "launches_in_timed_region": nl, "avg_launch_ms": ms / nl}
+    kernels = {k: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None,
+                   "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.name, "n": n, "d": WORKLOAD.d,
+                   "mean_len": float(np.diff(off).mean()),
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "search_time_s": total_s / args.steps,
+        "verified_pairs": pairs,
+        "e2e": {"value": pairs * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(seqs.nbytes + off.nbytes),
+                "d2h_bytes_per_step": int(pairs * 12), "search_time_s": e2e_s},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * xtn.h -- C ABI of the GB300 (sm_103a) symmetric-deletion neighbour search.
+ *
+ * The library finds every pair of amino-acid sequences within Levenshtein
+ * distance d by symmetric deletion lookup (XTNeighbor, arXiv 2403.09010):
+ * expand each sequence into its deletion variants with up to d deletions
+ * (Appendix A, "XTNeighbor algorithm step-by-step", steps 1-3), group equal
+ * variants (step 4), emit the index pairs that share a variant (step 5),
+ * remove duplicate pairs (step 6) and keep the pairs whose exact edit
+ * distance is <= d (step 7).  Every step runs in the library's own CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Sequences are passed packed: `seqs` holds the ASCII letters of all
+ *   sequences back to back (no separators, no terminator) and `offsets[k]`
+ *   .. `offsets[k+1]` delimit sequence k (`offsets` has n+1 entries,
+ *   offsets[0] = 0, non-decreasing).  Letters must be upper-case one-letter
+ *   amino-acid codes from "ACDEFGHIKLMNPQRSTVWY"; sequence lengths must be in
+ *   [0, XTN_MAX_LEN].  The paper packs 5 bits per residue into 12 bytes
+ *   (<= 18 residues, Appendix "Compression of TCR sequences"); this library
+ *   packs them into 16 bytes and so admits up to 25.
+ * - Every pointer argument except `n_out` and the index handle may be a host
+ *   pointer or a device pointer of the current CUDA device; the library
+ *   inspects it (cudaPointerGetAttributes) and copies host data to and from
+ *   the device itself.  The caller owns all buffers it passes.  `n_out` is
+ *   always a host pointer.
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Kernels
+ *   and copies are issued on it; every call returns only after the stream has
+ *   finished the call's work, because the result count is read back.
+ *   Scratch memory is taken from the device's stream-ordered pool
+ *   (cudaMallocAsync) and returned before the call ends.
+ * - Output rows are `xtn_triple {i, j, dist}` sorted ascending by (i, j),
+ *   without duplicates.  `*n_out` always receives the exact number of rows of
+ *   the full result.  If it exceeds `cap`, the first `cap` rows are written
+ *   and XTN_ERR_BUFFER_TOO_SMALL is returned; call again with a larger buffer.
+ * - Every function returns XTN_OK (0) or a negative status; see
+ *   xtn_status_string().  On an error no output row is guaranteed.
+ */
+#ifndef XTN_H_
+#define XTN_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream. */
+typedef struct CUstream_st* xtn_stream_t;
+
+/* One neighbour pair.  Self-search: i < j are sequence indices.  Batched
+ * self-search: i < j index the concatenation of all repertoires and always
+ * fall in the same repertoire.  Query search: i is the query index, j the
+ * reference index.  dist is the Levenshtein distance, 0 <= dist <= d. */
+typedef struct {
+  uint32_t i;
+  uint32_t j;
+  uint32_t dist;
+} xtn_triple;
+
+/* Device-resident deletion-variant index of a reference set (opaque). */
+typedef struct xtn_index xtn_index;
+
+#define XTN_MAX_LEN 25 /* longest admissible sequence */
+#define XTN_MAX_D 3    /* largest admissible distance threshold */
+
+enum {
+  XTN_OK = 0,
+  XTN_ERR_INVALID_ARG = -1,      /* bad size, pointer or d */
+  XTN_ERR_BAD_RESIDUE = -2,      /* a letter outside the 20-letter alphabet */
+  XTN_ERR_SEQ_TOO_LONG = -3,     /* a sequence longer than XTN_MAX_LEN */
+  XTN_ERR_OOM = -4,              /* device memory could not be allocated */
+  XTN_ERR_BUFFER_TOO_SMALL = -5, /* *n_out > cap; first cap rows written */
+  XTN_ERR_CUDA = -6,             /* a CUDA runtime call failed */
+  XTN_ERR_DEVICE_TIMEOUT = -7,   /* a bounded device-side wait gave up */
+  XTN_ERR_TOO_LARGE = -8         /* more than 2^32-1 variant records or pairs */
+};
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* xtn_status_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int xtn_version(void);
+
+/*
+ * All-pairs self-search (Appendix A, XTNeighbor steps 0-7).
+ *   seqs, offsets, n : the n input sequences (see conventions above).
+ *   d                : distance threshold, 0 <= d <= XTN_MAX_D.
+ *   rep_offsets      : NULL for one repertoire.  Otherwise n_rep+1
+ *                      non-decreasing int64 entries with rep_offsets[0] = 0
+ *                      and rep_offsets[n_rep] = n: the sequences
+ *                      [rep_offsets[r], rep_offsets[r+1]) form repertoire r
+ *                      and pairs are only reported within a repertoire
+ *                      (batched mode; indices stay global).
+ *   n_rep            : number of repertoires (ignored when rep_offsets is
+ *                      NULL; must be >= 1 otherwise).
+ *   out, cap         : output rows and their capacity (out may be NULL when
+ *                      cap == 0, to learn the count).
+ *   n_out            : host; receives the exact number of result rows.
+ * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, BUFFER_TOO_SMALL,
+ * CUDA, DEVICE_TIMEOUT, TOO_LARGE.
+ */
+int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                    const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
+                    int64_t* n_out, xtn_stream_t stream);
+
+/*
+ * Build a device-resident index of a reference set: its encoded sequences
+ * and its deletion variants, grouped by sorting (Appendix A, XTNeighbor steps
+ * 1-4; the paper's multi-value hash map of the SymDel step list, realised as a
+ * sorted array as Sec. 2.2 describes).  The index owns its device memory
+ * until xtn_index_free(); it is tied to the current device and may be used
+ * from any stream of it.  *out receives the handle.
+ * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, CUDA, DEVICE_TIMEOUT,
+ * TOO_LARGE.
+ */
+int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                    xtn_stream_t stream, xtn_index** out);
+
+/* Release an index (NULL is accepted). */
+int xtn_index_free(xtn_index* idx);
+
+/* Host-side facts about an index; any output pointer may be NULL. */
+int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
+                   int64_t* device_bytes);
+
+/*
+ * Query-vs-reference search (SymDel step 3 with the queries' own variants,
+ * the fuzzy database lookup of the Discussion): every (q, r) with
+ * Lev(query q, reference r) <= d, the d the index was built with.
+ * Rows are {i = q, j = r, dist}, sorted by (q, r).  Several calls may run
+ * concurrently on different streams against the same index.
+ * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, BUFFER_TOO_SMALL,
+ * CUDA, DEVICE_TIMEOUT, TOO_LARGE.
+ */
+int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
+                     int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out,
+                     xtn_stream_t stream);
+
+/*
+ * TCRdist post-filter of neighbour rows (Results, "SymDel lookup can be
+ * combined with more advanced similarity metrics").  For each input row
+ * {i, j, dist} the score of sequences i and j is computed as: with m the
+ * shorter length and g = |len_i - len_j|, the g gaps sit in the shorter
+ * sequence after its first floor(m/2) residues; each aligned position costs
+ * 0 if the residues agree, else min(4, 4 - BLOSUM62[a][b]); each gap costs
+ * 4; the sum is multiplied by 3.  Rows with score <= max_score are written
+ * to `out` in input order (out must hold n_in rows).
+ *   seqs, offsets, n : the sequences the row indices refer to.
+ *   in, n_in         : input rows (i, j < n).
+ * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, CUDA.
+ */
+int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                       const xtn_triple* in, int64_t n_in, int max_score, xtn_triple* out,
+                       int64_t* n_out, xtn_stream_t stream);
+
+/*
+ * Kernel timing.  While enabled, every kernel the library launches is
+ * bracketed by CUDA events on its stream and tagged with the algorithmic
+ * bytes it must move.  xtn_profile_report() synchronises those events and
+ * writes one line per kernel name, "name launches total_ms total_bytes\n",
+ * into buf (NUL-terminated, truncated to buf_len); it returns the number of
+ * lines, and clears the records.  Enabling costs two event records per launch.
+ */
+int xtn_profile_enable(int on);
+int xtn_profile_report(char* buf, int64_t buf_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XTN_H_ */

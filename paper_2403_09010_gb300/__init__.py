@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) symmetric-deletion Levenshtein neighbour search.
+
+The search (Appendix A of arXiv 2403.09010, XTNeighbor steps 0-7) runs in
+hand-written CUDA kernels behind the C ABI of include/xtn.h; this package is
+its thin Python binding.  ``build()`` compiles the library.
+"""
+from .buildlib import build  # noqa: F401
+from .native import XtnError, LIB_PATH  # noqa: F401
+from .xtn import (Index, index_build, profile_enable, profile_report,  # noqa: F401
+                  search_query, search_self, tcrdist_filter)

@@ -1,0 +1,781 @@
+// C ABI (include/xtn.h): argument checks, host/device buffer handling,
+// stream-ordered scratch, and the order of kernel launches for the
+// self-search, index build, query search and TCRdist filter.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "xtn_common.cuh"
+#include "xtn_kernels.h"
+
+namespace xtn {
+
+// ------------------------------------------------------------- profiler ---
+namespace {
+struct ProfRec {
+  const char* name;
+  double bytes;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_ev_pool;
+thread_local ProfRec t_pending{nullptr, 0.0, nullptr, nullptr};
+
+cudaEvent_t ev_get() {
+  {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_ev_pool.empty()) {
+      cudaEvent_t e = g_ev_pool.back();
+      g_ev_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void prof_begin(cudaStream_t s, const char* name, double bytes) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  t_pending.name = name;
+  t_pending.bytes = bytes;
+  t_pending.a = ev_get();
+  t_pending.b = ev_get();
+  cudaEventRecord(t_pending.a, s);
+}
+
+void prof_end(cudaStream_t s) {
+  if (!t_pending.name) return;
+  cudaEventRecord(t_pending.b, s);
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof.push_back(t_pending);
+  t_pending.name = nullptr;
+}
+
+// --------------------------------------------------------------- device ---
+namespace {
+
+struct DevInfo {
+  int sms = 0;
+  bool pool_ready = false;
+};
+std::mutex g_dev_mu;
+std::map<int, DevInfo> g_dev;
+
+int current_device_info(int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return XTN_ERR_CUDA;
+  std::lock_guard<std::mutex> g(g_dev_mu);
+  DevInfo& di = g_dev[dev];
+  if (!di.pool_ready) {
+    if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return XTN_ERR_CUDA;
+    // keep freed scratch cached in the pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    di.pool_ready = true;
+  }
+  *sms = di.sms;
+  return XTN_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered scratch owned by one call; returned to the pool at scope exit.
+class Arena {
+ public:
+  explicit Arena(cudaStream_t s) : s_(s) {}
+  ~Arena() {
+    for (void* p : ptrs_) cudaFreeAsync(p, s_);
+  }
+  template <class T>
+  T* get(size_t count) {
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, count * sizeof(T) + 64, s_) != cudaSuccess) {
+      cudaGetLastError();
+      failed_ = true;
+      return nullptr;
+    }
+    ptrs_.push_back(p);
+    return static_cast<T*>(p);
+  }
+  bool failed() const { return failed_; }
+
+ private:
+  cudaStream_t s_;
+  std::vector<void*> ptrs_;
+  bool failed_ = false;
+};
+
+int map_device_err(uint32_t e) {
+  if (e & DERR_TIMEOUT) return XTN_ERR_DEVICE_TIMEOUT;
+  if (e & DERR_BAD_RESIDUE) return XTN_ERR_BAD_RESIDUE;
+  if (e & DERR_TOO_LONG) return XTN_ERR_SEQ_TOO_LONG;
+  if (e & DERR_RANGE) return XTN_ERR_INVALID_ARG;
+  return XTN_OK;
+}
+
+#define XTN_CK(call)                         \
+  do {                                       \
+    if ((call) != cudaSuccess) {             \
+      cudaGetLastError();                    \
+      return XTN_ERR_CUDA;                   \
+    }                                        \
+  } while (0)
+#define XTN_ALLOC_OK(ar) \
+  do {                   \
+    if ((ar).failed()) return XTN_ERR_OOM; \
+  } while (0)
+
+// Read n elements of device memory into host memory and wait for the stream.
+template <class T>
+int read_back(T* host, const T* dev, size_t n, cudaStream_t s) {
+  XTN_CK(cudaMemcpyAsync(host, dev, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  return XTN_OK;
+}
+
+uint32_t bits_for(uint64_t n) {  // bits to hold every value in [0, n)
+  uint32_t b = 1;
+  while (b < 64 && (1ull << b) < n) ++b;
+  return b;
+}
+
+// Fingerprint bits used for grouping: the smallest multiple of 8 with
+// 2^hs >= 32 * n_rec (expected colliding pairs <= n_rec / 64), at least 16
+// and at most what the id field leaves free.
+int choose_hash_bits(uint64_t n_rec, uint32_t id_bits) {
+  int hs = 16;
+  while (hs < 64 && std::ldexp(1.0, hs) < 32.0 * (double)n_rec) hs += 8;
+  return std::min<int>(hs, 64 - (int)id_bits);
+}
+
+// Tunables (set by the autotuner through xtn_tune_set).
+std::atomic<int> g_cfg_records{0};
+std::atomic<int> g_cfg_pairs{3};
+
+// Sequences resident on the device for one call.
+struct DevSeqs {
+  const uint8_t* seqs = nullptr;
+  const int64_t* off = nullptr;
+  int64_t n = 0;
+};
+
+// Host-side check of host offsets: starts at 0, non-decreasing, lengths <= max.
+int check_host_offsets(const int64_t* off, int64_t n) {
+  if (off[0] != 0) return XTN_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t L = off[i + 1] - off[i];
+    if (L < 0) return XTN_ERR_INVALID_ARG;
+    if (L > XTN_MAX_LEN) return XTN_ERR_SEQ_TOO_LONG;
+  }
+  return XTN_OK;
+}
+
+int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar, cudaStream_t s,
+               DevSeqs* out) {
+  out->n = n;
+  int64_t total = 0;
+  if (is_device_ptr(offsets)) {
+    out->off = offsets;
+    int rc = read_back(&total, offsets + n, 1, s);
+    if (rc) return rc;
+    int64_t first = 0;
+    rc = read_back(&first, offsets, 1, s);
+    if (rc) return rc;
+    if (first != 0 || total < 0) return XTN_ERR_INVALID_ARG;
+  } else {
+    int rc = check_host_offsets(offsets, n);
+    if (rc) return rc;
+    total = offsets[n];
+    int64_t* d = ar.get<int64_t>(n + 1);
+    XTN_ALLOC_OK(ar);
+    XTN_CK(cudaMemcpyAsync(d, offsets, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    out->off = d;
+  }
+  if (total > 0 && !seqs) return XTN_ERR_INVALID_ARG;
+  if (is_device_ptr(seqs)) {
+    out->seqs = seqs;
+  } else {
+    uint8_t* d = ar.get<uint8_t>(total);
+    XTN_ALLOC_OK(ar);
+    if (total > 0) XTN_CK(cudaMemcpyAsync(d, seqs, total, cudaMemcpyHostToDevice, s));
+    out->seqs = d;
+  }
+  return XTN_OK;
+}
+
+// Encoded sequences plus their variant-record offsets.
+struct Encoded {
+  Key128* keys = nullptr;
+  uint8_t* lens = nullptr;
+  uint64_t* rec_off = nullptr;
+  uint64_t n_rec = 0;
+};
+
+int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStream_t s,
+                     Encoded* e) {
+  const int64_t n = in.n;
+  e->keys = ar.get<Key128>(n);
+  e->lens = ar.get<uint8_t>(n);
+  uint32_t* vcount = ar.get<uint32_t>(n);
+  e->rec_off = ar.get<uint64_t>(n + 1);
+  uint64_t* status = ar.get<uint64_t>(scan_status_bytes(n) / 8 + 1);
+  XTN_ALLOC_OK(ar);
+  launch_encode(in.seqs, in.off, n, d, e->keys, e->lens, vcount, err, s);
+  launch_scan_counts(vcount, n, e->rec_off, status, err, s);
+  XTN_CK(cudaGetLastError());
+  struct {
+    uint64_t n_rec;
+    uint32_t err;
+  } h{0, 0};
+  XTN_CK(cudaMemcpyAsync(&h.n_rec, e->rec_off + n, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err) return map_device_err(h.err);
+  e->n_rec = h.n_rec;
+  if (h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  return XTN_OK;
+}
+
+// Expand + sort variant records: returns the sorted buffer and the other one.
+struct Sorted {
+  uint64_t* rec = nullptr;
+  uint64_t* spare = nullptr;
+  uint32_t id_bits = 0;
+  int hs = 0;
+};
+
+int expand_and_sort(const Encoded& e, int64_t n, const uint32_t* seq_rep, int sms, Arena& ar,
+                    uint32_t* err, cudaStream_t s, Sorted* out) {
+  const uint64_t n_rec = e.n_rec;
+  out->id_bits = bits_for((uint64_t)n);
+  out->hs = choose_hash_bits(n_rec, out->id_bits);
+  const int lo = 64 - out->hs;
+  const int cfg = g_cfg_records.load();
+  uint64_t* A = ar.get<uint64_t>(n_rec + 8);
+  uint64_t* B = ar.get<uint64_t>(n_rec + 8);
+  uint32_t* hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
+  uint64_t* status = ar.get<uint64_t>(radix_status_bytes(n_rec, cfg) / 8 + 1);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
+  launch_expand(e.keys, e.lens, e.rec_off, n, seq_rep, out->id_bits, A, n_rec, hist, lo, 64, sms,
+                err, s);
+  XTN_CK(cudaGetLastError());
+  uint64_t* sorted = nullptr;
+  XTN_CK(radix_sort_passes(A, B, (int64_t)n_rec, lo, 64, hist, digit_base, status, cfg, err,
+                           &sorted, "k_onesweep_records", s));
+  out->rec = sorted;
+  out->spare = sorted == A ? B : A;
+  return XTN_OK;
+}
+
+// Sort candidate pair words, drop duplicates, verify; writes result rows.
+int pairs_to_rows(uint64_t* P1, uint64_t n_pairs, uint32_t pair_bits, const uint32_t* hist2,
+                  uint32_t j_bits, const Key128* keys_i, const uint8_t* lens_i, uint64_t n_i,
+                  const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                  const uint32_t* seq_rep, int self_mode, int d, xtn_triple* out, int64_t cap,
+                  Arena& ar, uint32_t* err, cudaStream_t s, uint64_t* n_rows) {
+  const int cfg = g_cfg_pairs.load();
+  uint64_t* P2 = ar.get<uint64_t>(n_pairs + 8);
+  uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
+  const size_t st = std::max(radix_status_bytes(n_pairs, cfg), verify_status_bytes(n_pairs));
+  uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
+  uint64_t* d_total = ar.get<uint64_t>(1);
+  XTN_ALLOC_OK(ar);
+  uint64_t* sorted = nullptr;
+  XTN_CK(radix_sort_passes(P1, P2, (int64_t)n_pairs, 0, (int)pair_bits, hist2, digit_base, status,
+                           cfg, err, &sorted, "k_onesweep_pairs", s));
+  launch_unique_verify(sorted, (int64_t)n_pairs, j_bits, keys_i, lens_i, keys_j, lens_j, n_i, n_j,
+                       seq_rep, self_mode, d, out, cap, status, err, d_total, s);
+  XTN_CK(cudaGetLastError());
+  struct {
+    uint64_t total;
+    uint32_t err;
+  } h{0, 0};
+  XTN_CK(cudaMemcpyAsync(&h.total, d_total, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err) return map_device_err(h.err);
+  *n_rows = h.total;
+  return XTN_OK;
+}
+
+// Result rows go to `out` directly when it is device memory; otherwise into
+// scratch and then to the host.
+struct OutRows {
+  xtn_triple* dev = nullptr;
+  int64_t dev_cap = 0;
+  bool host = false;
+};
+
+int prepare_out(xtn_triple* out, int64_t cap, uint64_t max_rows, Arena& ar, OutRows* o) {
+  if (cap > 0 && !out) return XTN_ERR_INVALID_ARG;
+  if (cap <= 0) {
+    o->dev = nullptr;
+    o->dev_cap = 0;
+    return XTN_OK;
+  }
+  if (is_device_ptr(out)) {
+    o->dev = out;
+    o->dev_cap = cap;
+  } else {
+    o->host = true;
+    o->dev_cap = (int64_t)std::min<uint64_t>((uint64_t)cap, max_rows);
+    o->dev = ar.get<xtn_triple>(o->dev_cap);
+    XTN_ALLOC_OK(ar);
+  }
+  return XTN_OK;
+}
+
+int finish_out(const OutRows& o, xtn_triple* out, int64_t cap, uint64_t n_rows, cudaStream_t s,
+               int64_t* n_out) {
+  *n_out = (int64_t)n_rows;
+  const int64_t w = std::min<int64_t>(cap, (int64_t)n_rows);
+  if (o.host && w > 0) {
+    XTN_CK(cudaMemcpyAsync(out, o.dev, w * sizeof(xtn_triple), cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaStreamSynchronize(s));
+  }
+  return (int64_t)n_rows > cap ? XTN_ERR_BUFFER_TOO_SMALL : XTN_OK;
+}
+
+int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                     const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
+                     int64_t* n_out, cudaStream_t s) {
+  if (!n_out) return XTN_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (n < 0 || d < 0 || d > XTN_MAX_D || cap < 0 || !offsets) return XTN_ERR_INVALID_ARG;
+  if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
+  if (rep_offsets && n_rep < 1) return XTN_ERR_INVALID_ARG;
+  if (n == 0) return XTN_OK;
+  int sms = 0;
+  int rc = current_device_info(&sms);
+  if (rc) return rc;
+  Arena ar(s);
+  uint32_t* err = ar.get<uint32_t>(4);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  DevSeqs in;
+  rc = stage_seqs(seqs, offsets, n, ar, s, &in);
+  if (rc) return rc;
+
+  // batched mode: repertoire of every sequence
+  uint32_t* seq_rep = nullptr;
+  if (rep_offsets) {
+    std::vector<int64_t> h(n_rep + 1);
+    if (is_device_ptr(rep_offsets)) {
+      rc = read_back(h.data(), rep_offsets, n_rep + 1, s);
+      if (rc) return rc;
+    } else {
+      std::memcpy(h.data(), rep_offsets, (n_rep + 1) * sizeof(int64_t));
+    }
+    if (h[0] != 0 || h[n_rep] != n) return XTN_ERR_INVALID_ARG;
+    for (int64_t r = 0; r < n_rep; ++r)
+      if (h[r + 1] < h[r]) return XTN_ERR_INVALID_ARG;
+    int64_t* d_rep = ar.get<int64_t>(n_rep + 1);
+    seq_rep = ar.get<uint32_t>(n);
+    XTN_ALLOC_OK(ar);
+    XTN_CK(cudaMemcpyAsync(d_rep, h.data(), (n_rep + 1) * 8, cudaMemcpyHostToDevice, s));
+    launch_seq_rep(d_rep, n_rep, seq_rep, n, s);
+  }
+
+  Encoded e;
+  rc = encode_and_count(in, d, ar, err, s, &e);
+  if (rc) return rc;
+  Sorted so;
+  rc = expand_and_sort(e, n, seq_rep, sms, ar, err, s, &so);
+  if (rc) return rc;
+
+  // groups of equal fingerprints with >= 2 records, inside the spare buffer
+  const uint64_t g_cap = e.n_rec / 2 + 1;
+  uint32_t* S = reinterpret_cast<uint32_t*>(so.spare);
+  uint32_t* E = S + g_cap;
+  uint64_t* pair_off = reinterpret_cast<uint64_t*>(E + g_cap);  // 8-byte aligned
+  const size_t st = std::max(group_status_bytes(e.n_rec), scan_status_bytes(g_cap));
+  uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
+  uint64_t* counters = ar.get<uint64_t>(2);
+  XTN_ALLOC_OK(ar);
+  launch_group_bounds(so.rec, (int64_t)e.n_rec, 64 - so.hs, S, E, g_cap, status, err, counters,
+                      s);
+  XTN_CK(cudaGetLastError());
+  uint64_t n_groups = 0;
+  rc = read_back(&n_groups, counters, 1, s);
+  if (rc) return rc;
+  uint64_t n_pairs = 0;
+  if (n_groups > 0) {
+    launch_scan_group_pairs(S, E, (int64_t)n_groups, pair_off, status, err, s);
+    XTN_CK(cudaGetLastError());
+    rc = read_back(&n_pairs, pair_off + n_groups, 1, s);
+    if (rc) return rc;
+  }
+  uint32_t herr = 0;
+  rc = read_back(&herr, err, 1, s);
+  if (rc) return rc;
+  if (herr) return map_device_err(herr);
+  if (n_pairs == 0) return XTN_OK;
+  if (n_pairs >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+
+  // candidate pairs, then dedup + verify
+  uint64_t* P1 = ar.get<uint64_t>(n_pairs + 8);
+  uint32_t* hist2 = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(hist2, 0, MAX_PASSES * RADIX * 4, s));
+  launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)n_groups, n_pairs, so.id_bits, P1,
+                    hist2, sms, err, s);
+  XTN_CK(cudaGetLastError());
+  OutRows o;
+  rc = prepare_out(out, cap, n_pairs, ar, &o);
+  if (rc) return rc;
+  uint64_t n_rows = 0;
+  rc = pairs_to_rows(P1, n_pairs, 2 * so.id_bits, hist2, so.id_bits, e.keys, e.lens, n, e.keys,
+                     e.lens, n, seq_rep, 1, d, o.dev, o.dev_cap, ar, err, s, &n_rows);
+  if (rc) return rc;
+  return finish_out(o, out, cap, n_rows, s, n_out);
+}
+
+}  // namespace
+}  // namespace xtn
+
+// ======================================================================
+// Query index
+// ======================================================================
+struct xtn_index {
+  int device = 0;
+  int d = 0;
+  int64_t n = 0;
+  uint64_t n_rec = 0;
+  uint32_t id_bits = 0;
+  int hs = 0;
+  int dir_bits = 0;
+  xtn::Key128* keys = nullptr;
+  uint8_t* lens = nullptr;
+  uint64_t* rec = nullptr;
+  uint32_t* dir = nullptr;
+  int64_t bytes = 0;
+};
+
+namespace xtn {
+void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_t* dir,
+                      cudaStream_t s);
+void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint64_t* q_rec_off,
+                         int64_t n_q, uint64_t n_qv, const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,
+                         int dir_bits, int gshift, uint32_t* qv_start, uint32_t* qv_cnt,
+                         uint32_t* qv_q, int sms, uint32_t* err, cudaStream_t s);
+void launch_query_emit(const uint64_t* rec, uint64_t n_rec, uint32_t ref_bits,
+                       const uint32_t* qv_start, const uint32_t* qv_q, const uint64_t* cand_off,
+                       uint64_t n_qv, uint64_t n_cand, uint64_t* out, uint32_t* hist,
+                       int hist_hi, int sms, uint32_t* err, cudaStream_t s);
+
+namespace {
+
+int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d, cudaStream_t s,
+                     xtn_index** out) {
+  if (!out) return XTN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || d < 0 || d > XTN_MAX_D || !offsets) return XTN_ERR_INVALID_ARG;
+  if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
+  int sms = 0;
+  int rc = current_device_info(&sms);
+  if (rc) return rc;
+  Arena ar(s);
+  uint32_t* err = ar.get<uint32_t>(4);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  DevSeqs in;
+  rc = stage_seqs(seqs, offsets, n, ar, s, &in);
+  if (rc) return rc;
+  Encoded e;
+  rc = encode_and_count(in, d, ar, err, s, &e);
+  if (rc) return rc;
+  Sorted so;
+  rc = expand_and_sort(e, n, nullptr, sms, ar, err, s, &so);
+  if (rc) return rc;
+
+  xtn_index* idx = new xtn_index;
+  cudaGetDevice(&idx->device);
+  idx->d = d;
+  idx->n = n;
+  idx->n_rec = e.n_rec;
+  idx->id_bits = so.id_bits;
+  idx->hs = so.hs;
+  idx->dir_bits = std::min(20, so.hs);
+  const size_t b_keys = n * sizeof(Key128), b_lens = n, b_rec = e.n_rec * 8,
+               b_dir = ((size_t(1) << idx->dir_bits) + 1) * 4;
+  bool ok = cudaMalloc(&idx->keys, b_keys) == cudaSuccess &&
+            cudaMalloc(&idx->lens, b_lens + 16) == cudaSuccess &&
+            cudaMalloc(&idx->rec, b_rec + 8) == cudaSuccess &&
+            cudaMalloc(&idx->dir, b_dir) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    xtn_index_free(idx);
+    return XTN_ERR_OOM;
+  }
+  idx->bytes = (int64_t)(b_keys + b_lens + b_rec + b_dir);
+  bool cp = cudaMemcpyAsync(idx->keys, e.keys, b_keys, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(idx->lens, e.lens, b_lens, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(idx->rec, so.rec, b_rec, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+  if (cp) launch_build_dir(idx->rec, idx->n_rec, idx->dir_bits, idx->dir, s);
+  uint32_t herr = 0;
+  if (!cp || cudaGetLastError() != cudaSuccess || read_back(&herr, err, 1, s) != XTN_OK) {
+    xtn_index_free(idx);
+    return XTN_ERR_CUDA;
+  }
+  if (herr) {
+    xtn_index_free(idx);
+    return map_device_err(herr);
+  }
+  *out = idx;
+  return XTN_OK;
+}
+
+int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
+                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out, cudaStream_t s) {
+  if (!n_out) return XTN_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (!idx || n_q < 0 || cap < 0 || !q_offsets) return XTN_ERR_INVALID_ARG;
+  if (n_q >= (1ll << 31)) return XTN_ERR_TOO_LARGE;
+  if (n_q == 0) return XTN_OK;
+  int sms = 0;
+  int rc = current_device_info(&sms);
+  if (rc) return rc;
+  Arena ar(s);
+  uint32_t* err = ar.get<uint32_t>(4);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  DevSeqs in;
+  rc = stage_seqs(q_seqs, q_offsets, n_q, ar, s, &in);
+  if (rc) return rc;
+  Encoded e;
+  rc = encode_and_count(in, idx->d, ar, err, s, &e);
+  if (rc) return rc;
+  const uint64_t n_qv = e.n_rec;
+  uint32_t* qv_start = ar.get<uint32_t>(n_qv);
+  uint32_t* qv_cnt = ar.get<uint32_t>(n_qv);
+  uint32_t* qv_q = ar.get<uint32_t>(n_qv);
+  uint64_t* cand_off = ar.get<uint64_t>(n_qv + 1);
+  uint64_t* status = ar.get<uint64_t>(scan_status_bytes(n_qv) / 8 + 1);
+  XTN_ALLOC_OK(ar);
+  launch_query_lookup(e.keys, e.lens, e.rec_off, n_q, n_qv, idx->rec, idx->n_rec, idx->dir,
+                      idx->dir_bits, 64 - idx->hs, qv_start, qv_cnt, qv_q, sms, err, s);
+  launch_scan_counts(qv_cnt, (int64_t)n_qv, cand_off, status, err, s);
+  XTN_CK(cudaGetLastError());
+  uint64_t n_cand = 0;
+  rc = read_back(&n_cand, cand_off + n_qv, 1, s);
+  if (rc) return rc;
+  uint32_t herr = 0;
+  rc = read_back(&herr, err, 1, s);
+  if (rc) return rc;
+  if (herr) return map_device_err(herr);
+  if (n_cand == 0) return XTN_OK;
+  if (n_cand >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  const uint32_t q_bits = bits_for((uint64_t)n_q);
+  const uint32_t pair_bits = q_bits + idx->id_bits;
+  if (pair_bits > 64) return XTN_ERR_TOO_LARGE;
+  uint64_t* P1 = ar.get<uint64_t>(n_cand + 8);
+  uint32_t* hist2 = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(hist2, 0, MAX_PASSES * RADIX * 4, s));
+  launch_query_emit(idx->rec, idx->n_rec, idx->id_bits, qv_start, qv_q, cand_off, n_qv, n_cand, P1,
+                    hist2, (int)pair_bits, sms, err, s);
+  XTN_CK(cudaGetLastError());
+  OutRows o;
+  rc = prepare_out(out, cap, n_cand, ar, &o);
+  if (rc) return rc;
+  uint64_t n_rows = 0;
+  rc = pairs_to_rows(P1, n_cand, pair_bits, hist2, idx->id_bits, e.keys, e.lens, (uint64_t)n_q,
+                     idx->keys, idx->lens, (uint64_t)idx->n, nullptr, 0, idx->d, o.dev, o.dev_cap,
+                     ar, err, s, &n_rows);
+  if (rc) return rc;
+  return finish_out(o, out, cap, n_rows, s, n_out);
+}
+
+int tcrdist_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, const xtn_triple* in_rows,
+                 int64_t n_in, int max_score, xtn_triple* out, int64_t* n_out, cudaStream_t s) {
+  if (!n_out) return XTN_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (n < 0 || n_in < 0 || !offsets || (n_in > 0 && (!in_rows || !out))) return XTN_ERR_INVALID_ARG;
+  if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
+  if (n_in == 0 || n == 0) return n_in == 0 ? XTN_OK : XTN_ERR_INVALID_ARG;
+  int sms = 0;
+  int rc = current_device_info(&sms);
+  if (rc) return rc;
+  Arena ar(s);
+  uint32_t* err = ar.get<uint32_t>(4);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  DevSeqs in;
+  rc = stage_seqs(seqs, offsets, n, ar, s, &in);
+  if (rc) return rc;
+  Encoded e;
+  rc = encode_and_count(in, 0, ar, err, s, &e);
+  if (rc) return rc;
+  const xtn_triple* d_in = in_rows;
+  if (!is_device_ptr(in_rows)) {
+    xtn_triple* t = ar.get<xtn_triple>(n_in);
+    XTN_ALLOC_OK(ar);
+    XTN_CK(cudaMemcpyAsync(t, in_rows, n_in * sizeof(xtn_triple), cudaMemcpyHostToDevice, s));
+    d_in = t;
+  }
+  const bool host_out = !is_device_ptr(out);
+  xtn_triple* d_out = host_out ? ar.get<xtn_triple>(n_in) : out;
+  uint64_t* status = ar.get<uint64_t>(verify_status_bytes(n_in) / 8 + 1);
+  uint64_t* d_total = ar.get<uint64_t>(1);
+  XTN_ALLOC_OK(ar);
+  launch_tcrdist_filter(d_in, n_in, e.keys, e.lens, n, max_score, d_out, status, err, d_total, s);
+  XTN_CK(cudaGetLastError());
+  uint64_t total = 0;
+  rc = read_back(&total, d_total, 1, s);
+  if (rc) return rc;
+  uint32_t herr = 0;
+  rc = read_back(&herr, err, 1, s);
+  if (rc) return rc;
+  if (herr) return map_device_err(herr);
+  if (host_out && total > 0) {
+    XTN_CK(cudaMemcpyAsync(out, d_out, total * sizeof(xtn_triple), cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaStreamSynchronize(s));
+  }
+  *n_out = (int64_t)total;
+  return XTN_OK;
+}
+
+}  // namespace
+}  // namespace xtn
+
+// ======================================================================
+// extern "C"
+// ======================================================================
+extern "C" {
+
+const char* xtn_status_string(int status) {
+  switch (status) {
+    case XTN_OK: return "ok";
+    case XTN_ERR_INVALID_ARG: return "invalid argument";
+    case XTN_ERR_BAD_RESIDUE: return "residue outside the 20-letter amino-acid alphabet";
+    case XTN_ERR_SEQ_TOO_LONG: return "sequence longer than XTN_MAX_LEN";
+    case XTN_ERR_OOM: return "out of device memory";
+    case XTN_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
+    case XTN_ERR_CUDA: return "CUDA runtime error";
+    case XTN_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case XTN_ERR_TOO_LARGE: return "problem exceeds 2^32-1 records or pairs";
+  }
+  return "unknown status";
+}
+
+int xtn_version(void) { return 10000; }
+
+int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                    const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
+                    int64_t* n_out, xtn_stream_t stream) {
+  return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
+                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                    xtn_stream_t stream, xtn_index** out) {
+  return xtn::index_build_impl(seqs, offsets, n, d, reinterpret_cast<cudaStream_t>(stream), out);
+}
+
+int xtn_index_free(xtn_index* idx) {
+  if (!idx) return XTN_OK;
+  cudaFree(idx->keys);
+  cudaFree(idx->lens);
+  cudaFree(idx->rec);
+  cudaFree(idx->dir);
+  delete idx;
+  return XTN_OK;
+}
+
+int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
+                   int64_t* device_bytes) {
+  if (!idx) return XTN_ERR_INVALID_ARG;
+  if (n) *n = idx->n;
+  if (d) *d = idx->d;
+  if (n_records) *n_records = (int64_t)idx->n_rec;
+  if (device_bytes) *device_bytes = idx->bytes;
+  return XTN_OK;
+}
+
+int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
+                     int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out,
+                     xtn_stream_t stream) {
+  return xtn::search_query_impl(idx, q_seqs, q_offsets, n_q, out, cap, n_out,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                       const xtn_triple* in, int64_t n_in, int max_score, xtn_triple* out,
+                       int64_t* n_out, xtn_stream_t stream) {
+  return xtn::tcrdist_impl(seqs, offsets, n, in, n_in, max_score, out, n_out,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_profile_enable(int on) {
+  xtn::g_prof_on.store(on != 0);
+  return XTN_OK;
+}
+
+int xtn_profile_report(char* buf, int64_t buf_len) {
+  std::vector<xtn::ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> g(xtn::g_prof_mu);
+    recs.swap(xtn::g_prof);
+  }
+  struct Agg {
+    int64_t launches = 0;
+    double ms = 0, bytes = 0;
+  };
+  std::map<std::string, Agg> agg;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) cudaGetLastError();
+    Agg& a = agg[r.name];
+    a.launches++;
+    a.ms += ms;
+    a.bytes += r.bytes;
+  }
+  {
+    std::lock_guard<std::mutex> g(xtn::g_prof_mu);
+    for (auto& r : recs) {
+      xtn::g_ev_pool.push_back(r.a);
+      xtn::g_ev_pool.push_back(r.b);
+    }
+  }
+  std::string s;
+  char line[256];
+  for (auto& kv : agg) {
+    std::snprintf(line, sizeof line, "%s %lld %.6f %.0f\n", kv.first.c_str(),
+                  (long long)kv.second.launches, kv.second.ms, kv.second.bytes);
+    s += line;
+  }
+  if (buf && buf_len > 0) {
+    const size_t w = std::min<size_t>(s.size(), (size_t)buf_len - 1);
+    std::memcpy(buf, s.data(), w);
+    buf[w] = '\0';
+  }
+  return (int)agg.size();
+}
+
+}  // extern "C"

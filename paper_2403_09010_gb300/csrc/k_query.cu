@@ -1,0 +1,153 @@
+// Query-vs-reference lookup against a resident, sorted variant index: the
+// SymDel step "reuse x to look up the hash map" (Appendix A, SymDel steps 2-3)
+// with the hash map realised as the sorted record array of Sec. 2.2.
+//
+//   k_build_dir    : dir[t] = first index record whose top `dir_bits`
+//                    fingerprint bits are >= t, so a lookup starts from a
+//                    range of ~n_rec / 2^dir_bits records instead of all.
+//   k_query_lookup : one warp per query, one lane per deletion variant (same
+//                    order as the self-search expansion): binary search of the
+//                    variant's fingerprint group inside its directory range;
+//                    writes the group's start and size.
+//   k_query_emit   : candidate t finds its query variant by binary search over
+//                    the candidate offsets, reads the reference id at the
+//                    matching index position and writes (q << ref_bits) | r.
+#include <algorithm>
+
+#include "xtn_common.cuh"
+#include "xtn_kernels.h"
+
+namespace xtn {
+
+__global__ void k_build_dir(const uint64_t* __restrict__ rec, uint64_t n_rec, int dir_bits,
+                            uint32_t* __restrict__ dir) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t n_dir = 1ull << dir_bits;
+  if (t > n_dir) return;
+  if (t == n_dir) {
+    dir[t] = (uint32_t)n_rec;
+    return;
+  }
+  uint64_t lo = 0, hi = n_rec;  // first position with top bits >= t
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if ((rec[mid] >> (64 - dir_bits)) < t) lo = mid + 1; else hi = mid;
+  }
+  dir[t] = (uint32_t)lo;
+}
+
+void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_t* dir,
+                      cudaStream_t s) {
+  const uint64_t n = (1ull << dir_bits) + 1;
+  prof_begin(s, "k_build_dir", (double)n * 4.0);
+  k_build_dir<<<div_up_u32(n, 256), 256, 0, s>>>(rec, n_rec, dir_bits, dir);
+  prof_end(s);
+}
+
+__global__ void __launch_bounds__(256)
+    k_query_lookup(const Key128* __restrict__ qkeys, const uint8_t* __restrict__ qlens,
+                   const uint64_t* __restrict__ q_rec_off, int64_t n_q, uint64_t n_qv,
+                   const uint64_t* __restrict__ rec, uint64_t n_rec,
+                   const uint32_t* __restrict__ dir, int dir_bits, int gshift,
+                   uint32_t* __restrict__ qv_start, uint32_t* __restrict__ qv_cnt,
+                   uint32_t* __restrict__ qv_q, uint32_t* __restrict__ err) {
+  const uint32_t lane = lane_id();
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp0; q < n_q; q += n_warps) {
+    const Key128 k = qkeys[q];
+    const uint32_t L = qlens[q];
+    const uint64_t base = q_rec_off[q];
+    uint32_t cnt = (uint32_t)(q_rec_off[q + 1] - base);
+    if (base + cnt > n_qv) {
+      if (lane == 0) atomicOr(err, DERR_RANGE);
+      cnt = 0;
+    }
+    for (uint32_t v = lane; v < cnt; v += 32) {
+      const uint64_t fp = fingerprint(variant_of(k, L, v), 0ull);
+      const uint64_t g = fp >> gshift;
+      const uint64_t top = fp >> (64 - dir_bits);
+      uint64_t lo = dir[top], hi = dir[top + 1];
+      if (hi > n_rec || lo > hi) {
+        atomicOr(err, DERR_RANGE);
+        lo = hi = 0;
+      }
+      uint64_t a = lo, b = hi;  // lower bound of g
+      while (a < b) {
+        const uint64_t mid = (a + b) >> 1;
+        if ((rec[mid] >> gshift) < g) a = mid + 1; else b = mid;
+      }
+      uint64_t c = a, e = hi;  // upper bound of g
+      while (c < e) {
+        const uint64_t mid = (c + e) >> 1;
+        if ((rec[mid] >> gshift) <= g) c = mid + 1; else e = mid;
+      }
+      qv_start[base + v] = (uint32_t)a;
+      qv_cnt[base + v] = (uint32_t)(c - a);
+      qv_q[base + v] = (uint32_t)q;
+    }
+  }
+}
+
+void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint64_t* q_rec_off,
+                         int64_t n_q, uint64_t n_qv, const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,
+                         int dir_bits, int gshift, uint32_t* qv_start, uint32_t* qv_cnt,
+                         uint32_t* qv_q, int sms, uint32_t* err, cudaStream_t s) {
+  if (n_q <= 0) return;
+  const int blocks = (int)std::min<int64_t>((n_q + 7) / 8, (int64_t)sms * 8);
+  prof_begin(s, "k_query_lookup", (double)n_q * 30.0);
+  k_query_lookup<<<blocks, 256, 0, s>>>(qkeys, qlens, q_rec_off, n_q, n_qv, rec, n_rec, dir, dir_bits,
+                                        gshift, qv_start, qv_cnt, qv_q, err);
+  prof_end(s);
+}
+
+__global__ void __launch_bounds__(256)
+    k_query_emit(const uint64_t* __restrict__ rec, uint64_t n_rec, uint32_t ref_bits,
+                 const uint32_t* __restrict__ qv_start, const uint32_t* __restrict__ qv_q,
+                 const uint64_t* __restrict__ cand_off, uint64_t n_qv, uint64_t n_cand,
+                 uint64_t* __restrict__ out, uint32_t* __restrict__ hist, int hist_hi,
+                 uint32_t* __restrict__ err) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  const int passes = (hist_hi + 7) / 8;
+  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  __syncthreads();
+  const uint64_t idmask = (1ull << ref_bits) - 1ull;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_cand;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t lo = 0, hi = n_qv;  // largest v with cand_off[v] <= t
+    while (hi - lo > 1) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (cand_off[mid] <= t) lo = mid; else hi = mid;
+    }
+    const uint64_t pos = (uint64_t)qv_start[lo] + (t - cand_off[lo]);
+    uint64_t w = 0;
+    if (pos < n_rec) {
+      w = ((uint64_t)qv_q[lo] << ref_bits) | (rec[pos] & idmask);
+    } else {
+      atomicOr(err, DERR_RANGE);
+    }
+    out[t] = w;
+    for (int p = 0; p < passes; ++p) {
+      const int sh = 8 * p;
+      const int bits = min(8, hist_hi - sh);
+      atomicAdd(&s_hist[p * RADIX + (uint32_t)((w >> sh) & ((1u << bits) - 1u))], 1u);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+}
+
+void launch_query_emit(const uint64_t* rec, uint64_t n_rec, uint32_t ref_bits,
+                       const uint32_t* qv_start, const uint32_t* qv_q, const uint64_t* cand_off,
+                       uint64_t n_qv, uint64_t n_cand, uint64_t* out, uint32_t* hist,
+                       int hist_hi, int sms, uint32_t* err, cudaStream_t s) {
+  if (n_cand == 0) return;
+  const int blocks = (int)std::min<uint64_t>((n_cand + 255) / 256, (uint64_t)sms * 8);
+  prof_begin(s, "k_query_emit", (double)n_cand * 24.0);
+  k_query_emit<<<blocks, 256, 0, s>>>(rec, n_rec, ref_bits, qv_start, qv_q, cand_off, n_qv, n_cand,
+                                      out, hist, hist_hi, err);
+  prof_end(s);
+}
+
+}  // namespace xtn

@@ -1,0 +1,278 @@
+// Least-significant-digit radix sort of 64-bit keys on a bit range [lo, hi),
+// 8-bit digits, one read and one write of the keys per digit ("onesweep":
+// the digit offsets of a tile come from a decoupled look-back over the
+// preceding tiles instead of a separate upsweep pass; Adinets & Merrill 2022).
+// This is the grouping step of Appendix A, XTNeighbor step 4 (the paper's
+// `sortKeyValues`) and the pair sort of step 6 (`sort`).  Sorting is stable,
+// so records with equal sorted bits keep their input order.
+//
+// One tile = THREADS x ITEMS keys:
+//   1. load: warp w reads its contiguous 32*ITEMS keys, item-major, so each
+//      load instruction is a 256-byte coalesced run;
+//   2. rank: per item, the lanes holding the same digit are found with one
+//      ballot per digit bit; the lowest of them bumps the warp's private
+//      256-bin counter in shared memory (stable warp-level multi-split);
+//   3. the per-warp counts become per-digit warp offsets and tile counts;
+//      the tile count of each digit is published for the look-back;
+//   4. keys are scattered into shared memory in digit order;
+//   5. thread t looks back along digit t's chain to get the number of keys
+//      with digit t in all earlier tiles;
+//   6. keys leave shared memory in digit order: runs of one digit land on
+//      consecutive addresses.
+#include <algorithm>
+
+#include "xtn_common.cuh"
+#include "xtn_kernels.h"
+
+namespace xtn {
+
+// Global digit histograms of every pass in one read of the keys.
+__global__ void k_histogram(const uint64_t* __restrict__ keys, int64_t n, int lo, int hi,
+                            uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  const int passes = (hi - lo + 7) / 8;
+  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < passes; ++p) {
+      const int sh = lo + 8 * p;
+      const int bits = min(8, hi - sh);
+      atomicAdd(&s_hist[p * RADIX + (uint32_t)((k >> sh) & ((1u << bits) - 1u))], 1u);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+}
+
+// digit_base[p][r] = number of keys whose pass-p digit is < r.
+__global__ void k_digit_scan(const uint32_t* __restrict__ hist, uint64_t* __restrict__ digit_base) {
+  __shared__ uint64_t s_w[RADIX / 32];
+  const int p = blockIdx.x, t = threadIdx.x;
+  const uint64_t v = hist[p * RADIX + t];
+  const uint64_t inc = warp_incl_scan_u64(v);
+  if ((t & 31) == 31) s_w[t >> 5] = inc;
+  __syncthreads();
+  uint64_t off = 0;
+  for (int w = 0; w < (t >> 5); ++w) off += s_w[w];
+  digit_base[p * RADIX + t] = off + inc - v;
+}
+
+template <int THREADS, int ITEMS>
+struct OnesweepSmem {
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr size_t keys_bytes = (size_t)TILE * 8;
+  static constexpr size_t whist_bytes = (size_t)WARPS * RADIX * 4;
+  static constexpr size_t bytes = keys_bytes + whist_bytes + RADIX * 4 + RADIX * 8;
+};
+
+template <int THREADS, int ITEMS, int MIN_BLOCKS>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
+    k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
+               int bits, const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
+               uint32_t* __restrict__ ctr, uint32_t* __restrict__ err) {
+  using SM = OnesweepSmem<THREADS, ITEMS>;
+  constexpr int WARPS = SM::WARPS;
+  constexpr int TILE = SM::TILE;
+  static_assert(THREADS >= RADIX, "one thread per digit");
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
+  uint32_t* s_tstart = s_whist + WARPS * RADIX;
+  int64_t* s_obase = reinterpret_cast<int64_t*>(s_tstart + RADIX);
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wsum[THREADS / 32];
+
+  const uint32_t tile = tile_id(ctr, &s_tile);
+  const int64_t tile_base = (int64_t)tile * TILE;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t dmask = (1u << bits) - 1u;
+
+  for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) s_whist[k] = 0;
+
+  uint64_t key[ITEMS];
+  const int64_t wbase = tile_base + (int64_t)warp * 32 * ITEMS;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int64_t pos = wbase + i * 32 + lane;
+    key[i] = pos < n ? __ldcs(in + pos) : 0ull;
+  }
+  __syncthreads();
+
+  // 2. stable warp multi-split ranking
+  uint32_t* wh = s_whist + warp * RADIX;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint16_t rank[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const bool valid = wbase + i * 32 + lane < n;
+    const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
+    uint32_t peers = __ballot_sync(FULL_MASK, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b < bits) {
+        const uint32_t bal = __ballot_sync(FULL_MASK, (dig >> b) & 1u);
+        peers &= ((dig >> b) & 1u) ? bal : ~bal;
+      }
+    }
+    const uint32_t before = peers & lt_mask;
+    uint32_t base = 0;
+    if (valid) base = wh[dig];
+    __syncwarp();
+    if (valid && before == 0) wh[dig] = base + __popc(peers);
+    __syncwarp();
+    rank[i] = (uint16_t)(base + __popc(before));
+  }
+  __syncthreads();
+
+  // 3. warp offsets per digit, tile counts, publish aggregates
+  uint32_t tcount = 0;
+  if (threadIdx.x < RADIX) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = s_whist[w * RADIX + threadIdx.x];
+      s_whist[w * RADIX + threadIdx.x] = run;
+      run += c;
+    }
+    tcount = run;
+    st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], (tile == 0 ? ST_INC : ST_AGG) | run);
+  }
+  // exclusive scan of tile counts over digits
+  {
+    uint32_t v = tcount;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL_MASK, inc, o);
+      if (lane >= (uint32_t)o) inc += t;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x < RADIX) {
+      uint32_t off = 0;
+      for (uint32_t w = 0; w < warp; ++w) off += s_wsum[w];
+      s_tstart[threadIdx.x] = off + inc - v;
+    }
+    __syncthreads();
+  }
+
+  // 4. scatter into shared memory in digit order
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const bool valid = wbase + i * 32 + lane < n;
+    if (valid) {
+      const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
+      s_keys[s_tstart[dig] + wh[dig] + rank[i]] = key[i];
+    }
+  }
+
+  // 5. look-back per digit
+  if (threadIdx.x < RADIX) {
+    uint64_t excl = 0;
+    if (tile > 0) {
+      excl = thread_lookback(status + threadIdx.x, tile, RADIX, err);
+      st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], ST_INC | (excl + tcount));
+    }
+    s_obase[threadIdx.x] = (int64_t)(digit_base[threadIdx.x] + excl) - (int64_t)s_tstart[threadIdx.x];
+  }
+  __syncthreads();
+
+  // 6. write out in digit order
+  const int tile_n = (int)(n - tile_base < TILE ? n - tile_base : TILE);
+  for (int j = threadIdx.x; j < tile_n; j += THREADS) {
+    const uint64_t k = s_keys[j];
+    const uint32_t dig = (uint32_t)(k >> shift) & dmask;
+    const int64_t o = s_obase[dig] + j;
+    if (o >= 0 && o < n) out[o] = k;
+    else atomicOr(err, DERR_RANGE);
+  }
+}
+
+// Tile configurations (threads, items per thread, min blocks per SM).  The
+// big configuration sorts the variant records; the small one the pairs.
+#define XTN_ONESWEEP_CONFIGS(X) \
+  X(0, 256, 16, 3)              \
+  X(1, 256, 24, 2)              \
+  X(2, 512, 12, 2)              \
+  X(3, 256, 8, 4)
+
+int onesweep_tile(int cfg) {
+  switch (cfg) {
+#define X(id, T, I, B) \
+  case id: return T * I;
+    XTN_ONESWEEP_CONFIGS(X)
+#undef X
+  }
+  return 0;
+}
+
+static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
+                                   int shift, int bits, const uint64_t* digit_base,
+                                   uint64_t* status, uint32_t* ctr, uint32_t* err, cudaStream_t s) {
+  switch (cfg) {
+#define X(id, T, I, B)                                                                      \
+  case id: {                                                                                \
+    using SM = OnesweepSmem<T, I>;                                                          \
+    static bool attr = false;                                                               \
+    if (!attr) {                                                                            \
+      cudaFuncSetAttribute(k_onesweep<T, I, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)SM::bytes);                                                 \
+      attr = true;                                                                          \
+    }                                                                                       \
+    const uint32_t tiles = div_up_u32(n, SM::TILE);                                         \
+    k_onesweep<T, I, B><<<tiles, T, SM::bytes, s>>>(in, out, n, shift, bits, digit_base,    \
+                                                    status, ctr, err);                      \
+    return cudaGetLastError();                                                              \
+  }
+    XTN_ONESWEEP_CONFIGS(X)
+#undef X
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t radix_status_bytes(int64_t n, int cfg) {
+  const int64_t tiles = (n + onesweep_tile(cfg) - 1) / onesweep_tile(cfg);
+  return (size_t)tiles * RADIX * 8 + 16;
+}
+
+void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t* hist, int sms,
+                      cudaStream_t s) {
+  if (n <= 0) return;
+  int blocks = (int)std::min<int64_t>((n + 1023) / 1024, (int64_t)sms * 4);
+  prof_begin(s, "k_histogram", (double)n * 8.0);
+  k_histogram<<<blocks, 512, 0, s>>>(keys, n, lo, hi, hist);
+  prof_end(s);
+}
+
+cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi,
+                              const uint32_t* hist, uint64_t* digit_base, uint64_t* status,
+                              int cfg, uint32_t* err, uint64_t** sorted, const char* tag,
+                              cudaStream_t s) {
+  const int passes = (hi - lo + 7) / 8;
+  *sorted = a;
+  if (n <= 1 || passes == 0) return cudaSuccess;
+  k_digit_scan<<<passes, RADIX, 0, s>>>(hist, digit_base);
+  const size_t st_bytes = radix_status_bytes(n, cfg);
+  uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st_bytes - 16);
+  uint64_t* src = a;
+  uint64_t* dst = b;
+  for (int p = 0; p < passes; ++p) {
+    const int sh = lo + 8 * p;
+    const int bits = std::min(8, hi - sh);
+    cudaError_t e = cudaMemsetAsync(status, 0, st_bytes, s);
+    if (e != cudaSuccess) return e;
+    prof_begin(s, tag, (double)n * 16.0);
+    e = onesweep_launch(cfg, src, dst, n, sh, bits, digit_base + p * RADIX, status, ctr, err, s);
+    prof_end(s);
+    if (e != cudaSuccess) return e;
+    std::swap(src, dst);
+  }
+  *sorted = src;
+  return cudaSuccess;
+}
+
+}  // namespace xtn

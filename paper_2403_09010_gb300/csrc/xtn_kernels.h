@@ -1,0 +1,65 @@
+// Host-side launchers of the sm_103a kernels (one translation unit each) and
+// the constants they share.  All launches are asynchronous on stream `s`.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xtn.h"
+
+namespace xtn {
+
+struct Key128;
+
+constexpr int RADIX = 256;     // 8-bit digits
+constexpr int MAX_PASSES = 8;  // 64-bit keys
+
+// k_variants.cu ------------------------------------------------------------
+void launch_encode(const uint8_t* seqs, const int64_t* off, int64_t n, int d, Key128* keys,
+                   uint8_t* lens, uint32_t* vcount, uint32_t* err, cudaStream_t s);
+void launch_expand(const Key128* keys, const uint8_t* lens, const uint64_t* rec_off, int64_t n,
+                   const uint32_t* seq_rep, uint32_t id_bits, uint64_t* out, uint64_t n_rec,
+                   uint32_t* hist, int hist_lo, int hist_hi, int sms, uint32_t* err,
+                   cudaStream_t s);
+void launch_seq_rep(const int64_t* rep_off, int64_t n_rep, uint32_t* seq_rep, int64_t n,
+                    cudaStream_t s);
+
+// k_radix.cu ---------------------------------------------------------------
+int onesweep_tile(int cfg);
+size_t radix_status_bytes(int64_t n, int cfg);
+void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t* hist, int sms,
+                      cudaStream_t s);
+// Sorts a[0:n) on bits [lo, hi) using b as the second buffer; `hist` holds the
+// digit histograms of every pass.  *sorted receives a or b.
+cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi,
+                              const uint32_t* hist, uint64_t* digit_base, uint64_t* status,
+                              int cfg, uint32_t* err, uint64_t** sorted, const char* tag,
+                              cudaStream_t s);
+
+// k_pairs.cu ---------------------------------------------------------------
+size_t scan_status_bytes(int64_t n);
+size_t group_status_bytes(int64_t n);
+void launch_scan_counts(const uint32_t* counts, int64_t n, uint64_t* out, uint64_t* status,
+                        uint32_t* err, cudaStream_t s);
+void launch_scan_group_pairs(const uint32_t* S, const uint32_t* E, int64_t n_groups,
+                             uint64_t* out, uint64_t* status, uint32_t* err, cudaStream_t s);
+void launch_group_bounds(const uint64_t* keys, int64_t n, int gshift, uint32_t* S, uint32_t* E,
+                         uint64_t cap, uint64_t* status, uint32_t* err, uint64_t* n_groups,
+                         cudaStream_t s);
+void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
+                       const uint64_t* pair_off, int64_t n_groups, uint64_t n_pairs,
+                       uint32_t id_bits, uint64_t* out, uint32_t* hist, int sms, uint32_t* err,
+                       cudaStream_t s);
+
+// k_verify.cu --------------------------------------------------------------
+size_t verify_status_bytes(int64_t n);
+void launch_unique_verify(const uint64_t* pairs, int64_t n, uint32_t j_bits, const Key128* keys_i,
+                          const uint8_t* lens_i, const Key128* keys_j, const uint8_t* lens_j,
+                          uint64_t n_i, uint64_t n_j, const uint32_t* seq_rep, int self_mode,
+                          int d, xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
+                          uint64_t* total, cudaStream_t s);
+void launch_tcrdist_filter(const xtn_triple* in, int64_t n, const Key128* keys,
+                           const uint8_t* lens, int64_t n_seq, int max_score, xtn_triple* out,
+                           uint64_t* status, uint32_t* err, uint64_t* total, cudaStream_t s);
+
+}  // namespace xtn

@@ -1,0 +1,174 @@
+"""Python entry points with the names of the C ABI (include/xtn.h).
+
+Inputs may be numpy arrays (host) or CUDA ``torch.Tensor`` s (device); the
+library copies host data itself.  Results come back on the side the sequences
+came from: a ``(rows, 3)`` numpy ``uint32`` array for host input, a
+``(rows, 3)`` ``torch.int32`` CUDA tensor for device input (columns i, j,
+dist; indices < 2^31 in every supported workload).  Device work runs on the
+current torch stream of the input's device.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native
+from .native import XtnError, check
+
+_ROW = 3
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=None):
+    """(pointer, keep-alive object, on_device) for a numpy array or torch tensor."""
+    if x is None:
+        return None, None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return ctypes.c_void_p(x.data_ptr()), x, bool(x.is_cuda)
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if a.size == 0:
+        a = np.zeros(1, dtype=dtype or a.dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), a, False
+
+
+def _stream(x):
+    if x is not None and _is_torch(x) and x.is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _alloc_rows(cap: int, like):
+    cap = max(int(cap), 1)
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+        t = torch.empty((cap, _ROW), dtype=torch.int32, device=like.device)
+        return t, ctypes.c_void_p(t.data_ptr())
+    a = np.empty((cap, _ROW), dtype=np.uint32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _n_items(offsets) -> int:
+    return int(offsets.shape[0]) - 1
+
+
+def _call_with_rows(fn, cap, like, where):
+    """fn(out_ptr, cap, n_out_ref) -> status; grows the buffer once if needed."""
+    n_out = ctypes.c_int64(0)
+    out, optr = _alloc_rows(cap, like)
+    rc = fn(optr, max(int(cap), 1), ctypes.byref(n_out))
+    if rc == native.XTN_ERR_BUFFER_TOO_SMALL:
+        out, optr = _alloc_rows(n_out.value, like)
+        rc = fn(optr, max(n_out.value, 1), ctypes.byref(n_out))
+    check(rc, where)
+    return out[: n_out.value]
+
+
+def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None):
+    """All pairs (i < j) within Levenshtein distance d; see xtn_search_self."""
+    n = _n_items(offsets)
+    sp, sk, _ = _ptr(seqs, np.uint8)
+    op, ok, _ = _ptr(offsets, np.int64)
+    rp, rk, _ = _ptr(rep_offsets, np.int64)
+    n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
+    stream = _stream(seqs)
+    if cap is None:
+        cap = 4 * n + 4096
+
+    def fn(optr, c, nref):
+        return native.lib().xtn_search_self(sp, op, n, int(d), rp, n_rep, optr, c, nref, stream)
+
+    return _call_with_rows(fn, cap, seqs, "xtn_search_self")
+
+
+class Index:
+    """Device-resident deletion-variant index of a reference set."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, nr, nb = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        d = ctypes.c_int(0)
+        check(native.lib().xtn_index_info(self._h, ctypes.byref(n), ctypes.byref(d),
+                                          ctypes.byref(nr), ctypes.byref(nb)), "xtn_index_info")
+        return {"n": n.value, "d": d.value, "n_records": nr.value, "device_bytes": nb.value}
+
+    def free(self):
+        if self._h:
+            native.lib().xtn_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def index_build(seqs, offsets, d: int) -> Index:
+    n = _n_items(offsets)
+    sp, sk, _ = _ptr(seqs, np.uint8)
+    op, ok, _ = _ptr(offsets, np.int64)
+    h = ctypes.c_void_p(0)
+    check(native.lib().xtn_index_build(sp, op, n, int(d), _stream(seqs), ctypes.byref(h)),
+          "xtn_index_build")
+    return Index(h)
+
+
+def search_query(index: Index, q_seqs, q_offsets, cap: int | None = None, stream=None):
+    """All (q, r) with Lev(query q, reference r) <= d; see xtn_search_query."""
+    n_q = _n_items(q_offsets)
+    sp, sk, _ = _ptr(q_seqs, np.uint8)
+    op, ok, _ = _ptr(q_offsets, np.int64)
+    st = ctypes.c_void_p(stream) if stream is not None else _stream(q_seqs)
+    if cap is None:
+        cap = 8 * n_q + 1024
+
+    def fn(optr, c, nref):
+        return native.lib().xtn_search_query(index.handle, sp, op, n_q, optr, c, nref, st)
+
+    return _call_with_rows(fn, cap, q_seqs, "xtn_search_query")
+
+
+def tcrdist_filter(seqs, offsets, rows, max_score: int = 24):
+    """Rows of `rows` whose TCRdist score is <= max_score; see xtn_tcrdist_filter."""
+    n = _n_items(offsets)
+    n_in = int(rows.shape[0])
+    sp, sk, _ = _ptr(seqs, np.uint8)
+    op, ok, _ = _ptr(offsets, np.int64)
+    if _is_torch(rows):
+        rp, rk, _ = _ptr(rows)
+    else:
+        rp, rk, _ = _ptr(np.ascontiguousarray(rows, dtype=np.uint32).reshape(-1, 3), np.uint32)
+    out, optr = _alloc_rows(n_in, rows if _is_torch(rows) else seqs)
+    n_out = ctypes.c_int64(0)
+    check(native.lib().xtn_tcrdist_filter(sp, op, n, rp, n_in, int(max_score), optr,
+                                          ctypes.byref(n_out), _stream(seqs)),
+          "xtn_tcrdist_filter")
+    return out[: n_out.value]
+
+
+def profile_enable(on: bool = True) -> None:
+    native.lib().xtn_profile_enable(1 if on else 0)
+
+
+def profile_report() -> dict:
+    """{kernel name: (launches, total_ms, algorithmic_bytes)} since the last report."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    native.lib().xtn_profile_report(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, launches, ms, nbytes = line.split()
+        out[name] = (int(launches), float(ms), float(nbytes))
+    return out

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+include/xtn.h declares; argument checks that need no device work behave."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2403_09010_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "xtn.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xtn_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_09010_gb300 import buildlib
+    buildlib.build()
+    return native.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["xtn_search_self", "xtn_index_build", "xtn_search_query",
+                     "xtn_tcrdist_filter", "xtn_index_free", "xtn_status_string"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    exported = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH],
+                              capture_output=True, text=True, check=True).stdout.split()
+    for name in _declared():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    assert set(_declared()) == set(native.SIGNATURES)
+    # nothing but the C ABI leaks out of the library
+    public = [s for s in exported if s.startswith("xtn")]
+    assert sorted(public) == _declared()
+
+
+def test_status_strings(lib):
+    for code in range(-8, 1):
+        assert native.status_string(code)
+    assert native.status_string(native.XTN_ERR_BUFFER_TOO_SMALL) == "output buffer too small"
+    assert lib.xtn_version() >= 10000
+
+
+def test_argument_checks_before_device_work(lib):
+    n_out = ctypes.c_int64(7)
+    off = (ctypes.c_int64 * 2)(0, 3)
+    seq = ctypes.c_char_p(b"CAS")
+    # n_out missing, bad d, negative n, negative cap: rejected on the host
+    assert lib.xtn_search_self(seq, off, 1, 1, None, 0, None, 0, None, None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_self(seq, off, 1, 4, None, 0, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert n_out.value == 0
+    assert lib.xtn_search_self(seq, off, -1, 1, None, 0, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_self(seq, off, 1, 1, None, 0, None, -1, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    # batched mode needs at least one repertoire
+    assert lib.xtn_search_self(seq, off, 1, 1, off, 0, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    # empty input: nothing to do, no device needed
+    assert lib.xtn_search_self(seq, off, 0, 2, None, 0, None, 0, ctypes.byref(n_out), None) == native.XTN_OK
+    assert n_out.value == 0
+    assert lib.xtn_index_build(seq, off, 0, 1, None, None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_query(None, seq, off, 1, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_index_free(None) == native.XTN_OK
+    assert lib.xtn_index_info(None, None, None, None, None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_tcrdist_filter(seq, off, 1, None, 0, 24, None, ctypes.byref(n_out), None) == native.XTN_OK

@@ -1,0 +1,250 @@
+"""CUDA path vs the CPU oracle, element by element (bit-exact integer rows).
+
+Every case calls the C ABI through the thin binding.  Outputs are the sorted
+(i, j, dist) rows; the oracle computes the same rows from strings with full
+dynamic programming (oracle/xtn_oracle.cpp).
+"""
+import numpy as np
+import pytest
+
+import cdr3_synth as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def xtn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2403_09010_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _rows(x):
+    if isinstance(x, np.ndarray):
+        return x.astype(np.uint32)
+    return x.cpu().numpy().astype(np.uint32)
+
+
+def _dev(seqs, off):
+    return (torch.from_numpy(np.ascontiguousarray(seqs)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(off)).cuda())
+
+
+def _rand_strings(rng, n, alphabet, lmin, lmax):
+    L = rng.integers(lmin, lmax + 1, n)
+    return ["".join(rng.choice(list(alphabet), size=l)) for l in L]
+
+
+# ------------------------------------------------------------ self search ---
+def test_selfsearch_n1e4_d1_full(xtn):
+    seqs, off = gen.workload(gen.SELF_SMALL)
+    want = oracle.symdel_self(seqs, off, 1)
+    got = _rows(xtn.search_self(seqs, off, 1))
+    assert got.shape == want.shape and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_selfsearch_generator_slice(xtn, d):
+    n = {0: 20_000, 1: 20_000, 2: 20_000, 3: 3_000}[d]
+    seqs, off = gen.workload(gen.SELF_1M, n)
+    want = oracle.symdel_self(seqs, off, d)
+    got = _rows(xtn.search_self(seqs, off, d))
+    assert np.array_equal(got, want)
+
+
+def test_device_inputs_match_host_inputs(xtn):
+    seqs, off = gen.generate(30_000, 77, 0.2, 0.01)
+    host = _rows(xtn.search_self(seqs, off, 2))
+    ds, do = _dev(seqs, off)
+    dev_out = xtn.search_self(ds, do, 2)
+    assert dev_out.is_cuda
+    assert np.array_equal(_rows(dev_out), host)
+    assert np.array_equal(host, oracle.symdel_self(seqs, off, 2))
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_small_alphabet_collisions(xtn, d):
+    rng = np.random.default_rng(100 + d)
+    strs = _rand_strings(rng, 400, "AC", 0, 9)
+    seqs, off = gen.from_strings(strs)
+    want = oracle.bruteforce_self(seqs, off, d)
+    got = _rows(xtn.search_self(seqs, off, d))
+    assert np.array_equal(got, want)
+
+
+def test_edge_cases(xtn):
+    # empty input
+    seqs, off = gen.from_strings([])
+    assert xtn.search_self(seqs, off, 2).shape[0] == 0
+    # one sequence, empty strings, maximum length, repeats
+    for strs, d in [(["CASSF"], 2), (["", "", "A"], 1), (["W" * 25, "W" * 24, "Y" * 25], 1),
+                    (["AAAAAAAAAAAAAAAAAAAAAAAAA", "AAAAAAAAAAAAAAAAAAAAAAAA"], 3),
+                    (["ACDEFGHIKLMNPQRSTVWYACDEF", "CDEFGHIKLMNPQRSTVWYACDEFA"], 2)]:
+        seqs, off = gen.from_strings(strs)
+        assert np.array_equal(_rows(xtn.search_self(seqs, off, d)),
+                              oracle.bruteforce_self(seqs, off, d)), strs
+
+
+def test_identical_sequences_one_giant_bucket(xtn):
+    n = 700
+    seqs, off = gen.from_strings(["CASSLGQETQYF"] * n)
+    got = _rows(xtn.search_self(seqs, off, 2))
+    assert got.shape[0] == n * (n - 1) // 2
+    assert np.all(got[:, 2] == 0)
+    ii, jj = np.triu_indices(n, 1)
+    assert np.array_equal(got[:, 0], ii) and np.array_equal(got[:, 1], jj)
+
+
+def test_d_covers_every_length(xtn):
+    rng = np.random.default_rng(5)
+    strs = _rand_strings(rng, 150, "ACDEFG", 0, 3)
+    seqs, off = gen.from_strings(strs)
+    got = _rows(xtn.search_self(seqs, off, 3))
+    assert got.shape[0] == 150 * 149 // 2
+    assert np.array_equal(got, oracle.bruteforce_self(seqs, off, 3))
+
+
+def test_buffer_too_small_reports_count(xtn):
+    import ctypes
+    from paper_2403_09010_gb300 import native
+    seqs, off = gen.workload(gen.SELF_SMALL)
+    want = oracle.symdel_self(seqs, off, 1)
+    cap = 10
+    out = np.zeros((cap, 3), np.uint32)
+    n_out = ctypes.c_int64(0)
+    s = np.ascontiguousarray(seqs)
+    o = np.ascontiguousarray(off)
+    rc = native.lib().xtn_search_self(s.ctypes.data, o.ctypes.data, o.size - 1, 1, None, 0,
+                                      out.ctypes.data, cap, ctypes.byref(n_out), None)
+    assert rc == native.XTN_ERR_BUFFER_TOO_SMALL
+    assert n_out.value == want.shape[0]
+    assert np.array_equal(out, want[:cap])
+
+
+def test_input_errors(xtn):
+    from paper_2403_09010_gb300 import native
+    for strs, code in [(["CASSF", "CAXSF"], native.XTN_ERR_BAD_RESIDUE),
+                       (["CASSF", "cassf"], native.XTN_ERR_BAD_RESIDUE),
+                       (["A" * 26], native.XTN_ERR_SEQ_TOO_LONG)]:
+        seqs, off = gen.from_strings(strs)
+        with pytest.raises(native.XtnError) as ei:
+            xtn.search_self(seqs, off, 1)
+        assert ei.value.status == code
+        # the same checks on device-resident input run in the encode kernel
+        ds, do = _dev(seqs, off)
+        with pytest.raises(native.XtnError) as ei:
+            xtn.search_self(ds, do, 1)
+        assert ei.value.status == code
+
+
+# --------------------------------------------------------------- batched ---
+def test_batched_matches_oracle(xtn):
+    seqs, off, rep = gen.batched(n_rep=12, seed=9, size_min=1, size_max=3000)
+    want = oracle.symdel_batched(seqs, off, rep, 2)             # (rep, i_loc, j_loc, dist)
+    got = _rows(xtn.search_self(seqs, off, 2, rep_offsets=rep))  # global indices
+    rep_of = np.searchsorted(rep, got[:, 0], side="right") - 1
+    assert np.all(np.searchsorted(rep, got[:, 1], side="right") - 1 == rep_of)
+    local = np.stack([rep_of, got[:, 0] - rep[rep_of], got[:, 1] - rep[rep_of], got[:, 2]], 1)
+    assert np.array_equal(local.astype(np.uint32), want)
+
+
+def test_batched_equals_separate_calls(xtn):
+    seqs, off, rep = gen.batched(n_rep=6, seed=10, size_min=500, size_max=4000)
+    got = _rows(xtn.search_self(seqs, off, 2, rep_offsets=rep))
+    parts = []
+    for r in range(6):
+        s = seqs[off[rep[r]]:off[rep[r + 1]]]
+        o = off[rep[r]:rep[r + 1] + 1] - off[rep[r]]
+        g = _rows(xtn.search_self(s, o, 2)).astype(np.int64)
+        g[:, :2] += rep[r]
+        parts.append(g)
+    assert np.array_equal(got, np.concatenate(parts).astype(np.uint32))
+
+
+# ----------------------------------------------------------------- query ---
+@pytest.mark.parametrize("d", [1, 2])
+def test_query_matches_oracle(xtn, d):
+    rs, ro, reqs = gen.served(ref_n=40_000, n_req=6, max_req=3000)
+    idx = xtn.index_build(rs, ro, d)
+    info = idx.info()
+    assert info["n"] == 40_000 and info["d"] == d
+    for r in reqs:
+        want = oracle.symdel_query(rs, ro, r.seqs, r.offsets, d)
+        got = _rows(xtn.search_query(idx, r.seqs, r.offsets))
+        assert np.array_equal(got, want)
+    idx.free()
+
+
+def test_query_small_reference_bruteforce(xtn):
+    rng = np.random.default_rng(8)
+    ref = _rand_strings(rng, 300, "ACD", 0, 7)
+    qs = _rand_strings(rng, 120, "ACD", 0, 7)
+    rs, ro = gen.from_strings(ref)
+    q, qo = gen.from_strings(qs)
+    for d in [0, 1, 2, 3]:
+        idx = xtn.index_build(rs, ro, d)
+        assert np.array_equal(_rows(xtn.search_query(idx, q, qo)),
+                              oracle.bruteforce_query(rs, ro, q, qo, d))
+        idx.free()
+
+
+# --------------------------------------------------------------- tcrdist ---
+def test_tcrdist_filter_matches_oracle(xtn):
+    seqs, off = gen.workload(gen.TCRDIST_1M, 5000)
+    lev = _rows(xtn.search_self(seqs, off, 2))
+    got = _rows(xtn.tcrdist_filter(seqs, off, lev, 24))
+    want = oracle.tcrdist_filter(seqs, off, lev, 24)
+    assert np.array_equal(got, want)
+    allp = oracle.tcrdist_allpairs(seqs, off, 2, 24)
+    assert np.array_equal(got, allp[:, :3])
+
+
+def test_tcrdist_every_residue_pair(xtn):
+    # one pair per ordered residue pair (a, b) at the same position: covers
+    # every BLOSUM62 entry the score uses.
+    aa = gen.AA
+    strs = []
+    for a in aa:
+        for b in aa:
+            strs += ["CAS" + a + "GF", "CAS" + b + "GF"]
+    seqs, off = gen.from_strings(strs)
+    rows = np.array([[2 * k, 2 * k + 1, 1] for k in range(len(strs) // 2)], np.uint32)
+    for thr in [0, 3, 6, 9, 12, 24]:
+        got = _rows(xtn.tcrdist_filter(seqs, off, rows, thr))
+        assert np.array_equal(got, oracle.tcrdist_filter(seqs, off, rows, thr)), thr
+
+
+# ------------------------------------------------------- full-size check ---
+def test_selfsearch_n1e6_d2_sampled(xtn):
+    """The 1M-sequence d=2 workload in the benchmark's launch configuration,
+    checked on sampled rows against the plain definition, plus invariants."""
+    seqs, off = gen.workload(gen.SELF_1M)
+    ds, do = _dev(seqs, off)
+    rows = _rows(xtn.search_self(ds, do, 2))
+    n = off.size - 1
+    i, j, dist = rows[:, 0].astype(np.int64), rows[:, 1].astype(np.int64), rows[:, 2]
+    assert np.all(i < j) and np.all(dist <= 2)
+    key = i * n + j
+    assert np.all(np.diff(key) > 0)
+    rng = np.random.default_rng(0)
+    for s in rng.choice(n, 12, replace=False):
+        want = oracle.neighbors_of(seqs, off, int(s), 2)          # (j, dist) rows
+        m = (i == s) | (j == s)
+        other = np.where(i[m] == s, j[m], i[m])
+        got = np.stack([other, dist[m]], 1)
+        got = got[np.argsort(got[:, 0])].astype(np.uint32)
+        assert np.array_equal(got, want), s
+    strs = None
+    # bag-of-amino-acids bound (Appendix B) on a sample of rows
+    pick = rng.choice(rows.shape[0], min(5000, rows.shape[0]), replace=False)
+    raw = bytes(seqs)
+    for a, b, dd in rows[pick]:
+        sa, sb = raw[off[a]:off[a + 1]], raw[off[b]:off[b + 1]]
+        ca = np.bincount(np.frombuffer(sa, np.uint8), minlength=128)
+        cb = np.bincount(np.frombuffer(sb, np.uint8), minlength=128)
+        assert np.linalg.norm(ca - cb) <= np.sqrt(2) * dd + 1e-9
