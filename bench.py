@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="xtn", choices=["xtn", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="use only the first n sequences (small cases for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -209,7 +211,7 @@ def main():
     xtn.build()
     lib = native.lib()
 
-    seqs, off = gen.workload(WORKLOAD)
+    seqs, off = gen.workload(WORKLOAD, args.n)
     n = off.size - 1
     d_seqs = torch.from_numpy(seqs).cuda()
     d_off = torch.from_numpy(off).cuda()
