@@ -156,6 +156,21 @@ int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
                        int64_t* n_out, xtn_stream_t stream);
 
 /*
+ * Tuning knobs (process-wide, take effect for calls that start afterwards).
+ *   XTN_TUNE_SORT_RECORDS : tile configuration of the radix sort of variant
+ *                           records (0 .. xtn_tune_count(knob)-1)
+ *   XTN_TUNE_SORT_PAIRS   : tile configuration of the radix sort of verified
+ *                           pair words
+ * Every configuration gives the same result; they differ in threads per
+ * block, keys per thread and ranking method, hence in speed per GPU and size.
+ * xtn_tune_set returns XTN_ERR_INVALID_ARG for an unknown knob or value.
+ */
+enum { XTN_TUNE_SORT_RECORDS = 0, XTN_TUNE_SORT_PAIRS = 1 };
+int xtn_tune_set(int knob, int value);
+int xtn_tune_get(int knob);
+int xtn_tune_count(int knob);
+
+/*
  * Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by CUDA events on its stream and tagged with the algorithmic
  * bytes it must move.  xtn_profile_report() synchronises those events and

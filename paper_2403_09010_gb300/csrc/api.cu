@@ -172,8 +172,12 @@ int choose_hash_bits(uint64_t n_rec, uint32_t id_bits) {
 }
 
 // Tunables (set by the autotuner through xtn_tune_set).
-std::atomic<int> g_cfg_records{0};
-std::atomic<int> g_cfg_pairs{3};
+std::atomic<int> g_cfg_records{9};
+std::atomic<int> g_cfg_pairs{9};
+}  // namespace
+std::atomic<int>& cfg_records() { return g_cfg_records; }
+std::atomic<int>& cfg_pairs() { return g_cfg_pairs; }
+namespace {
 
 // Sequences resident on the device for one call.
 struct DevSeqs {
@@ -230,6 +234,7 @@ int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar
 struct Encoded {
   Key128* keys = nullptr;
   uint8_t* lens = nullptr;
+  uint32_t* eqprev = nullptr;
   uint64_t* rec_off = nullptr;
   uint64_t n_rec = 0;
 };
@@ -239,11 +244,12 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
   const int64_t n = in.n;
   e->keys = ar.get<Key128>(n);
   e->lens = ar.get<uint8_t>(n);
+  e->eqprev = ar.get<uint32_t>(n);
   uint32_t* vcount = ar.get<uint32_t>(n);
   e->rec_off = ar.get<uint64_t>(n + 1);
   uint64_t* status = ar.get<uint64_t>(scan_status_bytes(n) / 8 + 1);
   XTN_ALLOC_OK(ar);
-  launch_encode(in.seqs, in.off, n, d, e->keys, e->lens, vcount, err, s);
+  launch_encode(in.seqs, in.off, n, d, e->keys, e->lens, e->eqprev, vcount, err, s);
   launch_scan_counts(vcount, n, e->rec_off, status, err, s);
   XTN_CK(cudaGetLastError());
   struct {
@@ -267,8 +273,8 @@ struct Sorted {
   int hs = 0;
 };
 
-int expand_and_sort(const Encoded& e, int64_t n, const uint32_t* seq_rep, int sms, Arena& ar,
-                    uint32_t* err, cudaStream_t s, Sorted* out) {
+int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep, int sms,
+                    Arena& ar, uint32_t* err, cudaStream_t s, Sorted* out) {
   const uint64_t n_rec = e.n_rec;
   out->id_bits = bits_for((uint64_t)n);
   out->hs = choose_hash_bits(n_rec, out->id_bits);
@@ -281,8 +287,8 @@ int expand_and_sort(const Encoded& e, int64_t n, const uint32_t* seq_rep, int sm
   uint64_t* status = ar.get<uint64_t>(radix_status_bytes(n_rec, cfg) / 8 + 1);
   XTN_ALLOC_OK(ar);
   XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
-  launch_expand(e.keys, e.lens, e.rec_off, n, seq_rep, out->id_bits, A, n_rec, hist, lo, 64, sms,
-                err, s);
+  launch_expand(e.keys, e.lens, e.eqprev, e.rec_off, n, d, seq_rep, out->id_bits, A, n_rec, hist,
+                lo, 64, sms, err, s);
   XTN_CK(cudaGetLastError());
   uint64_t* sorted = nullptr;
   XTN_CK(radix_sort_passes(A, B, (int64_t)n_rec, lo, 64, hist, digit_base, status, cfg, err,
@@ -292,34 +298,50 @@ int expand_and_sort(const Encoded& e, int64_t n, const uint32_t* seq_rep, int sm
   return XTN_OK;
 }
 
-// Sort candidate pair words, drop duplicates, verify; writes result rows.
-int pairs_to_rows(uint64_t* P1, uint64_t n_pairs, uint32_t pair_bits, const uint32_t* hist2,
-                  uint32_t j_bits, const Key128* keys_i, const uint8_t* lens_i, uint64_t n_i,
-                  const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
-                  const uint32_t* seq_rep, int self_mode, int d, xtn_triple* out, int64_t cap,
-                  Arena& ar, uint32_t* err, cudaStream_t s, uint64_t* n_rows) {
+// Verify candidate pair words (P1), sort the survivors, drop duplicates and
+// write result rows.  P1 is reused as the sort's second buffer.
+int verify_sort_finalize(uint64_t* P1, uint64_t n_cand, uint32_t pair_bits, uint32_t j_bits,
+                         const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
+                         const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                         const uint32_t* seq_rep, int self_mode, int d, xtn_triple* out,
+                         int64_t cap, int sms, Arena& ar, uint32_t* err, cudaStream_t s,
+                         uint64_t* n_rows) {
+  *n_rows = 0;
   const int cfg = g_cfg_pairs.load();
-  uint64_t* P2 = ar.get<uint64_t>(n_pairs + 8);
+  uint64_t* P2 = ar.get<uint64_t>(n_cand + 8);
+  uint32_t* hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
   uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
-  const size_t st = std::max(radix_status_bytes(n_pairs, cfg), verify_status_bytes(n_pairs));
-  uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
-  uint64_t* d_total = ar.get<uint64_t>(1);
+  uint64_t* counters = ar.get<uint64_t>(2);
   XTN_ALLOC_OK(ar);
-  uint64_t* sorted = nullptr;
-  XTN_CK(radix_sort_passes(P1, P2, (int64_t)n_pairs, 0, (int)pair_bits, hist2, digit_base, status,
-                           cfg, err, &sorted, "k_onesweep_pairs", s));
-  launch_unique_verify(sorted, (int64_t)n_pairs, j_bits, keys_i, lens_i, keys_j, lens_j, n_i, n_j,
-                       seq_rep, self_mode, d, out, cap, status, err, d_total, s);
+  XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
+  XTN_CK(cudaMemsetAsync(counters, 0, 16, s));
+  launch_verify_candidates(P1, n_cand, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep,
+                           self_mode, d, P2, n_cand, counters, hist, (int)pair_bits, sms, err, s);
   XTN_CK(cudaGetLastError());
   struct {
-    uint64_t total;
+    uint64_t n;
     uint32_t err;
   } h{0, 0};
-  XTN_CK(cudaMemcpyAsync(&h.total, d_total, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.n, counters, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaStreamSynchronize(s));
   if (h.err) return map_device_err(h.err);
-  *n_rows = h.total;
+  const uint64_t n_surv = h.n;
+  if (n_surv == 0) return XTN_OK;
+  const size_t st = std::max(radix_status_bytes(n_surv, cfg), verify_status_bytes(n_surv));
+  uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
+  XTN_ALLOC_OK(ar);
+  uint64_t* sorted = nullptr;
+  XTN_CK(radix_sort_passes(P2, P1, (int64_t)n_surv, 0, (int)pair_bits, hist, digit_base, status,
+                           cfg, err, &sorted, "k_onesweep_pairs", s));
+  launch_unique_finalize(sorted, (int64_t)n_surv, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j,
+                         out, cap, status, err, counters + 1, s);
+  XTN_CK(cudaGetLastError());
+  XTN_CK(cudaMemcpyAsync(&h.n, counters + 1, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err) return map_device_err(h.err);
+  *n_rows = h.n;
   return XTN_OK;
 }
 
@@ -405,7 +427,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   rc = encode_and_count(in, d, ar, err, s, &e);
   if (rc) return rc;
   Sorted so;
-  rc = expand_and_sort(e, n, seq_rep, sms, ar, err, s, &so);
+  rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so);
   if (rc) return rc;
 
   // groups of equal fingerprints with >= 2 records, inside the spare buffer
@@ -416,9 +438,10 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   const size_t st = std::max(group_status_bytes(e.n_rec), scan_status_bytes(g_cap));
   uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
   uint64_t* counters = ar.get<uint64_t>(2);
+  uint64_t* flags = ar.get<uint64_t>(group_flag_words((int64_t)e.n_rec));
   XTN_ALLOC_OK(ar);
-  launch_group_bounds(so.rec, (int64_t)e.n_rec, 64 - so.hs, S, E, g_cap, status, err, counters,
-                      s);
+  launch_group_bounds(so.rec, (int64_t)e.n_rec, 64 - so.hs, S, E, g_cap, flags, status, err,
+                      counters, s);
   XTN_CK(cudaGetLastError());
   uint64_t n_groups = 0;
   rc = read_back(&n_groups, counters, 1, s);
@@ -437,20 +460,20 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (n_pairs == 0) return XTN_OK;
   if (n_pairs >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
 
-  // candidate pairs, then dedup + verify
+  // candidate pairs, then verify, sort, dedup
   uint64_t* P1 = ar.get<uint64_t>(n_pairs + 8);
-  uint32_t* hist2 = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(hist2, 0, MAX_PASSES * RADIX * 4, s));
-  launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)n_groups, n_pairs, so.id_bits, P1,
-                    hist2, sms, err, s);
+  launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)n_groups, n_pairs, so.id_bits, P1, sms,
+                    err, s);
+  launch_peq(e.keys, e.lens, n, peq, s);
   XTN_CK(cudaGetLastError());
   OutRows o;
   rc = prepare_out(out, cap, n_pairs, ar, &o);
   if (rc) return rc;
   uint64_t n_rows = 0;
-  rc = pairs_to_rows(P1, n_pairs, 2 * so.id_bits, hist2, so.id_bits, e.keys, e.lens, n, e.keys,
-                     e.lens, n, seq_rep, 1, d, o.dev, o.dev_cap, ar, err, s, &n_rows);
+  rc = verify_sort_finalize(P1, n_pairs, 2 * so.id_bits, so.id_bits, peq, e.lens, n, e.keys,
+                            e.lens, n, seq_rep, 1, d, o.dev, o.dev_cap, sms, ar, err, s, &n_rows);
   if (rc) return rc;
   return finish_out(o, out, cap, n_rows, s, n_out);
 }
@@ -477,17 +500,6 @@ struct xtn_index {
 };
 
 namespace xtn {
-void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_t* dir,
-                      cudaStream_t s);
-void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint64_t* q_rec_off,
-                         int64_t n_q, uint64_t n_qv, const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,
-                         int dir_bits, int gshift, uint32_t* qv_start, uint32_t* qv_cnt,
-                         uint32_t* qv_q, int sms, uint32_t* err, cudaStream_t s);
-void launch_query_emit(const uint64_t* rec, uint64_t n_rec, uint32_t ref_bits,
-                       const uint32_t* qv_start, const uint32_t* qv_q, const uint64_t* cand_off,
-                       uint64_t n_qv, uint64_t n_cand, uint64_t* out, uint32_t* hist,
-                       int hist_hi, int sms, uint32_t* err, cudaStream_t s);
-
 namespace {
 
 int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d, cudaStream_t s,
@@ -510,7 +522,7 @@ int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   rc = encode_and_count(in, d, ar, err, s, &e);
   if (rc) return rc;
   Sorted so;
-  rc = expand_and_sort(e, n, nullptr, sms, ar, err, s, &so);
+  rc = expand_and_sort(e, n, d, nullptr, sms, ar, err, s, &so);
   if (rc) return rc;
 
   xtn_index* idx = new xtn_index;
@@ -577,8 +589,9 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
   uint64_t* cand_off = ar.get<uint64_t>(n_qv + 1);
   uint64_t* status = ar.get<uint64_t>(scan_status_bytes(n_qv) / 8 + 1);
   XTN_ALLOC_OK(ar);
-  launch_query_lookup(e.keys, e.lens, e.rec_off, n_q, n_qv, idx->rec, idx->n_rec, idx->dir,
-                      idx->dir_bits, 64 - idx->hs, qv_start, qv_cnt, qv_q, sms, err, s);
+  launch_query_lookup(e.keys, e.lens, e.eqprev, e.rec_off, n_q, n_qv, idx->d, idx->rec,
+                      idx->n_rec, idx->dir, idx->dir_bits, 64 - idx->hs, qv_start, qv_cnt, qv_q,
+                      sms, err, s);
   launch_scan_counts(qv_cnt, (int64_t)n_qv, cand_off, status, err, s);
   XTN_CK(cudaGetLastError());
   uint64_t n_cand = 0;
@@ -594,19 +607,19 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
   const uint32_t pair_bits = q_bits + idx->id_bits;
   if (pair_bits > 64) return XTN_ERR_TOO_LARGE;
   uint64_t* P1 = ar.get<uint64_t>(n_cand + 8);
-  uint32_t* hist2 = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  uint32_t* peq = ar.get<uint32_t>((size_t)n_q * PEQ_STRIDE);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(hist2, 0, MAX_PASSES * RADIX * 4, s));
   launch_query_emit(idx->rec, idx->n_rec, idx->id_bits, qv_start, qv_q, cand_off, n_qv, n_cand, P1,
-                    hist2, (int)pair_bits, sms, err, s);
+                    sms, err, s);
+  launch_peq(e.keys, e.lens, n_q, peq, s);
   XTN_CK(cudaGetLastError());
   OutRows o;
   rc = prepare_out(out, cap, n_cand, ar, &o);
   if (rc) return rc;
   uint64_t n_rows = 0;
-  rc = pairs_to_rows(P1, n_cand, pair_bits, hist2, idx->id_bits, e.keys, e.lens, (uint64_t)n_q,
-                     idx->keys, idx->lens, (uint64_t)idx->n, nullptr, 0, idx->d, o.dev, o.dev_cap,
-                     ar, err, s, &n_rows);
+  rc = verify_sort_finalize(P1, n_cand, pair_bits, idx->id_bits, peq, e.lens, (uint64_t)n_q,
+                            idx->keys, idx->lens, (uint64_t)idx->n, nullptr, 0, idx->d, o.dev,
+                            o.dev_cap, sms, ar, err, s, &n_rows);
   if (rc) return rc;
   return finish_out(o, out, cap, n_rows, s, n_out);
 }
@@ -729,6 +742,28 @@ int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
                        int64_t* n_out, xtn_stream_t stream) {
   return xtn::tcrdist_impl(seqs, offsets, n, in, n_in, max_score, out, n_out,
                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_tune_set(int knob, int value) {
+  if (value < 0 || value >= xtn::onesweep_configs()) return XTN_ERR_INVALID_ARG;
+  switch (knob) {
+    case XTN_TUNE_SORT_RECORDS: xtn::cfg_records().store(value); return XTN_OK;
+    case XTN_TUNE_SORT_PAIRS: xtn::cfg_pairs().store(value); return XTN_OK;
+  }
+  return XTN_ERR_INVALID_ARG;
+}
+
+int xtn_tune_get(int knob) {
+  switch (knob) {
+    case XTN_TUNE_SORT_RECORDS: return xtn::cfg_records().load();
+    case XTN_TUNE_SORT_PAIRS: return xtn::cfg_pairs().load();
+  }
+  return XTN_ERR_INVALID_ARG;
+}
+
+int xtn_tune_count(int knob) {
+  return (knob == XTN_TUNE_SORT_RECORDS || knob == XTN_TUNE_SORT_PAIRS) ? xtn::onesweep_configs()
+                                                                          : XTN_ERR_INVALID_ARG;
 }
 
 int xtn_profile_enable(int on) {

@@ -122,87 +122,192 @@ void launch_scan_group_pairs(const uint32_t* S, const uint32_t* E, int64_t n_gro
 }
 
 // ----------------------------------------------------------- group bounds ---
-constexpr int GB_THREADS = 256;
-constexpr int GB_ITEMS = 16;
-constexpr int GB_TILE = GB_THREADS * GB_ITEMS;
+// Two kernels instead of one single-pass compaction: the per-position work is
+// too light for a decoupled look-back (the chain of tile prefixes, not the
+// memory, would set the pace), so
+//   k_group_flags : reads the records once; per 32 positions writes one word
+//                   (head ballot | tail ballot << 32) and per tile the number
+//                   of heads and tails (no inter-tile waiting);
+//   k_scan_counts : prefix over the tile counts (small);
+//   k_group_write : reads only the flag words and writes the k-th head to S[k]
+//                   and the k-th tail to E[k].
+// A multi-record group starts at p when g(p) != g(p-1) and g(p) == g(p+1) and
+// ends at p when g(p) != g(p+1) and g(p) == g(p-1), g = key >> gshift (no
+// g(-1), no g(n)).
+constexpr int GB_THREADS = 512;
+constexpr int GB_WARPS = GB_THREADS / 32;
+constexpr int GB_ITEMS = 16;   // positions per lane per chunk
+constexpr int GB_CHUNKS = 4;
+constexpr int GB_WARP_SPAN = 32 * GB_ITEMS * GB_CHUNKS;
+constexpr int GB_TILE = GB_THREADS * GB_ITEMS * GB_CHUNKS;  // 32768 positions
+constexpr int GB_WORDS = GB_TILE / 32;                       // flag words per tile
+
+// K = uint32_t when the group key (key >> gshift) fits in 32 bits.
+template <typename K>
+__global__ void __launch_bounds__(GB_THREADS)
+    k_group_flags(const uint64_t* __restrict__ keys, int64_t n, int gshift,
+                  uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts) {
+  __shared__ uint64_t s_wtot[GB_WARPS];
+  const int64_t tbase = (int64_t)blockIdx.x * GB_TILE;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const int64_t wbase = tbase + (int64_t)warp * GB_WARP_SPAN;
+  // the value before position wbase (made different from it at position 0)
+  K carry = (wbase >= 1 && wbase - 1 < n) ? (K)(keys[wbase - 1] >> gshift) : (K)0;
+  uint32_t heads = 0, tails = 0;
+#pragma unroll 1
+  for (int c = 0; c < GB_CHUNKS; ++c) {
+    const int64_t cbase = wbase + (int64_t)c * 32 * GB_ITEMS;
+    K cur[GB_ITEMS];
+#pragma unroll
+    for (int i = 0; i < GB_ITEMS; ++i) {
+      const int64_t p = cbase + i * 32 + lane;
+      cur[i] = p < n ? (K)(__ldcs(keys + p) >> gshift) : (K)0;
+    }
+    const int64_t pe = cbase + 32 * GB_ITEMS;
+    const K after = (pe < n) ? (K)(keys[pe] >> gshift) : (K)0;
+    uint64_t mine = 0;  // lane i keeps the flag word of item i
+#pragma unroll
+    for (int i = 0; i < GB_ITEMS; ++i) {
+      const int64_t p = cbase + i * 32 + lane;
+      K prev = __shfl_up_sync(FULL_MASK, cur[i], 1);
+      if (lane == 0) prev = carry;
+      K next = __shfl_down_sync(FULL_MASK, cur[i], 1);
+      const K first_next =
+          (i + 1 < GB_ITEMS) ? __shfl_sync(FULL_MASK, cur[i + 1 < GB_ITEMS ? i + 1 : i], 0) : after;
+      if (lane == 31) next = first_next;
+      carry = __shfl_sync(FULL_MASK, cur[i], 31);
+      if (p == 0) prev = cur[i] ^ (K)1;      // nothing before the first position
+      if (p == n - 1) next = cur[i] ^ (K)1;  // nothing after the last one
+      const bool valid = p < n;
+      const uint32_t hb = __ballot_sync(FULL_MASK, valid && cur[i] != prev && cur[i] == next);
+      const uint32_t tb = __ballot_sync(FULL_MASK, valid && cur[i] != next && cur[i] == prev);
+      if (lane == (uint32_t)i) mine = ((uint64_t)tb << 32) | hb;
+      heads += __popc(hb);
+      tails += __popc(tb);
+    }
+    const int64_t word = cbase / 32 + lane;  // 16 consecutive words per chunk
+    if (lane < GB_ITEMS && word * 32 < n) flags[word] = mine;
+  }
+  if (lane == 0) s_wtot[warp] = ((uint64_t)heads << 31) | tails;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t total = 0;
+#pragma unroll
+    for (int w = 0; w < GB_WARPS; ++w) total += s_wtot[w];
+    tile_counts[blockIdx.x] = total;
+  }
+}
 
 __global__ void __launch_bounds__(GB_THREADS)
-    k_group_bounds(const uint64_t* __restrict__ keys, int64_t n, int gshift,
-                   uint32_t* __restrict__ S, uint32_t* __restrict__ E, uint64_t cap,
-                   uint64_t* __restrict__ status, uint32_t* __restrict__ ctr,
-                   uint32_t* __restrict__ err, uint64_t* __restrict__ n_groups) {
-  __shared__ uint64_t s_g[GB_TILE + 2];
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_w[GB_THREADS / 32];
-  __shared__ uint64_t s_prefix;
-  const uint32_t tile = tile_id(ctr, &s_tile);
-  const int64_t tbase = (int64_t)tile * GB_TILE;
-  // s_g[j] = group key of position tbase - 1 + j; out-of-range positions get
-  // sentinels that differ from every real key (keys are >> gshift < 2^(64-gshift)).
-  const uint64_t sentinel = ~0ull;
-  for (int j = threadIdx.x; j < GB_TILE + 2; j += GB_THREADS) {
-    const int64_t p = tbase - 1 + j;
-    s_g[j] = (p >= 0 && p < n) ? (__ldcs(keys + p) >> gshift) : sentinel - (p < 0 ? 1 : 0);
-  }
-  __syncthreads();
-  // a multi-record group starts at p when g(p) != g(p-1) and g(p) == g(p+1);
-  // it ends at p when g(p) != g(p+1) and g(p) == g(p-1).
-  const int j0 = threadIdx.x * GB_ITEMS;
-  uint32_t heads = 0, tails = 0;
-  uint32_t hmask = 0, tmask = 0;
+    k_group_write(const uint64_t* __restrict__ flags, int64_t n,
+                  const uint64_t* __restrict__ tile_prefix, uint32_t* __restrict__ S,
+                  uint32_t* __restrict__ E, uint64_t cap, uint32_t* __restrict__ err) {
+  __shared__ uint64_t s_w[GB_WARPS];
+  const int64_t tbase = (int64_t)blockIdx.x * GB_TILE;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  // each warp owns GB_WARP_SPAN / 32 flag words; lane l holds words l, l+32, ...
+  constexpr int WPW = GB_WARP_SPAN / 32;  // words per warp (64)
+  const int64_t w0 = tbase / 32 + (int64_t)warp * WPW;
+  const int64_t n_words = (n + 31) / 32;
+  uint64_t fw[WPW / 32];
+  uint32_t h = 0, t = 0;
 #pragma unroll
-  for (int i = 0; i < GB_ITEMS; ++i) {
-    const int64_t p = tbase + j0 + i;
-    if (p < n) {
-      const uint64_t prev = s_g[j0 + i], cur = s_g[j0 + i + 1], next = s_g[j0 + i + 2];
-      const bool h = cur != prev && cur == next;
-      const bool t = cur != next && cur == prev;
-      hmask |= (uint32_t)h << i;
-      tmask |= (uint32_t)t << i;
-      heads += h;
-      tails += t;
-    }
+  for (int k = 0; k < WPW / 32; ++k) {
+    const int64_t wi = w0 + k * 32 + lane;
+    fw[k] = wi < n_words ? flags[wi] : 0ull;
+    h += __popc((uint32_t)fw[k]);
+    t += __popc((uint32_t)(fw[k] >> 32));
   }
-  const uint64_t packed = ((uint64_t)heads << 31) | tails;
-  uint64_t excl;
-  const uint64_t total = block_excl_scan<GB_THREADS>(packed, s_w, excl);
-  if (threadIdx.x < 32) {
-    const uint64_t pre = warp_lookback(status, tile, total, err);
-    if (threadIdx.x == 0) {
-      s_prefix = pre;
-      if (tbase + GB_TILE >= n) *n_groups = (pre + total) >> 31;  // last tile
-    }
-  }
+  // exclusive prefix of (h, t) over lanes in word order, then over warps
+  uint64_t mine = ((uint64_t)h << 31) | t;
+  const uint64_t inc = warp_incl_scan_u64(mine);
+  if (lane == 31) s_w[warp] = inc;
   __syncthreads();
-  const uint64_t start = s_prefix + excl;
-  uint64_t hk = start >> 31, tk = start & 0x7fffffffull;
+  uint64_t off = tile_prefix[blockIdx.x];
 #pragma unroll
-  for (int i = 0; i < GB_ITEMS; ++i) {
-    const uint32_t p = (uint32_t)(tbase + j0 + i);
-    if (hmask >> i & 1u) {
-      if (hk < cap) S[hk] = p; else atomicOr(err, DERR_RANGE);
-      ++hk;
+  for (int w = 0; w < GB_WARPS; ++w)
+    if (w < (int)warp) off += s_w[w];
+  uint64_t hk = off >> 31, tk = off & 0x7fffffffull;
+#pragma unroll
+  for (int k = 0; k < WPW / 32; ++k) {
+    // lane l holds word w0 + 32k + l; prefix over lanes of this round
+    const uint32_t hc = __popc((uint32_t)fw[k]), tc = __popc((uint32_t)(fw[k] >> 32));
+    uint32_t hx = hc, tx = tc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t a = __shfl_up_sync(FULL_MASK, hx, o);
+      const uint32_t b = __shfl_up_sync(FULL_MASK, tx, o);
+      if (lane >= (uint32_t)o) {
+        hx += a;
+        tx += b;
+      }
     }
-    if (tmask >> i & 1u) {
-      if (tk < cap) E[tk] = p; else atomicOr(err, DERR_RANGE);
-      ++tk;
+    const uint32_t htot = __shfl_sync(FULL_MASK, hx, 31), ttot = __shfl_sync(FULL_MASK, tx, 31);
+    uint64_t hq = hk + hx - hc, tq = tk + tx - tc;
+    const uint32_t pbase = (uint32_t)((w0 + k * 32 + lane) * 32);
+    uint32_t hb = (uint32_t)fw[k], tb = (uint32_t)(fw[k] >> 32);
+    while (hb) {
+      const int b = __ffs(hb) - 1;
+      hb &= hb - 1;
+      if (hq < cap) S[hq] = pbase + b; else atomicOr(err, DERR_RANGE);
+      ++hq;
     }
+    while (tb) {
+      const int b = __ffs(tb) - 1;
+      tb &= tb - 1;
+      if (tq < cap) E[tq] = pbase + b; else atomicOr(err, DERR_RANGE);
+      ++tq;
+    }
+    hk += htot;
+    tk += ttot;
   }
 }
+
+__global__ void k_groups_total(const uint64_t* __restrict__ total, uint64_t* __restrict__ n_groups) {
+  *n_groups = *total >> 31;
+}
+
+struct CountsU64 {
+  const uint64_t* v;
+  __device__ uint64_t operator()(int64_t k) const { return v[k]; }
+};
+
+size_t group_status_bytes(int64_t n) {
+  const int64_t tiles = (n + GB_TILE - 1) / GB_TILE;
+  return scan_status_bytes(tiles) + (size_t)tiles * 16 + 64;
+}
+
+size_t group_flag_words(int64_t n) { return (size_t)((n + 31) / 32); }
 
 void launch_group_bounds(const uint64_t* keys, int64_t n, int gshift, uint32_t* S, uint32_t* E,
-                         uint64_t cap, uint64_t* status, uint32_t* err, uint64_t* n_groups, cudaStream_t s) {
+                         uint64_t cap, uint64_t* flags, uint64_t* status, uint32_t* err,
+                         uint64_t* n_groups, cudaStream_t s) {
   if (n <= 0) return;
-  const size_t st = (size_t)((n + GB_TILE - 1) / GB_TILE) * 8 + 16;
+  const int64_t tiles = (n + GB_TILE - 1) / GB_TILE;
+  // scratch layout in `status`: [scan status][tile counts][tile prefix (tiles+1)]
+  const size_t st = scan_status_bytes(tiles);
+  uint64_t* tile_counts = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(status) + st);
+  uint64_t* tile_prefix = tile_counts + tiles;
+  prof_begin(s, "k_group_flags", (double)n * 8.0 + (double)(n / 32) * 8.0);
+  if (gshift >= 32)
+    k_group_flags<uint32_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, gshift, flags, tile_counts);
+  else
+    k_group_flags<uint64_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, gshift, flags, tile_counts);
+  prof_end(s);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
-  prof_begin(s, "k_group_bounds", (double)n * 8.0);
-  k_group_bounds<<<div_up_u32(n, GB_TILE), GB_THREADS, 0, s>>>(keys, n, gshift, S, E, cap, status,
-                                                              ctr, err, n_groups);
+  prof_begin(s, "k_scan_tiles", (double)tiles * 16.0);
+  k_scan_counts<<<div_up_u32(tiles, SCAN_TILE), SCAN_THREADS, 0, s>>>(CountsU64{tile_counts},
+                                                                     tiles, tile_prefix, status,
+                                                                     ctr, err);
   prof_end(s);
+  prof_begin(s, "k_group_write", (double)(n / 32) * 8.0);
+  k_group_write<<<(unsigned)tiles, GB_THREADS, 0, s>>>(flags, n, tile_prefix, S, E, cap, err);
+  prof_end(s);
+  // number of groups = heads in the total (high field of tile_prefix[tiles])
+  k_groups_total<<<1, 1, 0, s>>>(tile_prefix + tiles, n_groups);
 }
 
-size_t group_status_bytes(int64_t n) { return (size_t)((n + GB_TILE - 1) / GB_TILE) * 8 + 16; }
 
 // ------------------------------------------------------------ pair emit ---
 constexpr int EMIT_THREADS = 256;
@@ -230,13 +335,9 @@ __device__ __forceinline__ void unrank_pair(uint64_t l, uint64_t& a, uint64_t& b
 __global__ void __launch_bounds__(EMIT_THREADS)
     k_emit_pairs(const uint64_t* __restrict__ keys, uint64_t n_keys, const uint32_t* __restrict__ S,
                  const uint64_t* __restrict__ pair_off, int64_t n_groups, uint64_t n_pairs,
-                 uint32_t id_bits, uint64_t* __restrict__ out, uint32_t* __restrict__ hist,
-                 int hist_hi, uint32_t* __restrict__ err) {
+                 uint32_t id_bits, uint64_t* __restrict__ out, uint32_t* __restrict__ err) {
   __shared__ uint64_t s_off[EMIT_TILE + 1];
   __shared__ int64_t s_k0, s_k1;
-  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
-  const int passes = (hist_hi + 7) / 8;
-  for (int k = threadIdx.x; k < passes * RADIX; k += EMIT_THREADS) s_hist[k] = 0;
   const uint64_t idmask = (1ull << id_bits) - 1ull;
   for (uint64_t t0 = (uint64_t)blockIdx.x * EMIT_TILE; t0 < n_pairs;
        t0 += (uint64_t)gridDim.x * EMIT_TILE) {
@@ -273,29 +374,21 @@ __global__ void __launch_bounds__(EMIT_THREADS)
           atomicOr(err, DERR_RANGE);
         }
         out[t] = w;
-        for (int p = 0; p < passes; ++p) {
-          const int sh = 8 * p;
-          const int bits = min(8, hist_hi - sh);
-          atomicAdd(&s_hist[p * RADIX + (uint32_t)((w >> sh) & ((1u << bits) - 1u))], 1u);
-        }
       }
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < passes * RADIX; k += EMIT_THREADS)
-    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
 }
 
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        const uint64_t* pair_off, int64_t n_groups, uint64_t n_pairs,
-                       uint32_t id_bits, uint64_t* out, uint32_t* hist, int sms, uint32_t* err,
-                       cudaStream_t s) {
+                       uint32_t id_bits, uint64_t* out, int sms, uint32_t* err, cudaStream_t s) {
   if (n_pairs == 0) return;
   const uint64_t tiles = (n_pairs + EMIT_TILE - 1) / EMIT_TILE;
   const int blocks = (int)std::min<uint64_t>(tiles, (uint64_t)sms * 8);
   prof_begin(s, "k_emit_pairs", (double)n_pairs * (8.0 + 16.0));
   k_emit_pairs<<<blocks, EMIT_THREADS, 0, s>>>(keys, n_keys, S, pair_off, n_groups, n_pairs,
-                                               id_bits, out, hist, (int)(2 * id_bits), err);
+                                               id_bits, out, err);
   prof_end(s);
 }
 

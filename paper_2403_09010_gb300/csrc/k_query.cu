@@ -14,6 +14,7 @@
 //                    matching index position and writes (q << ref_bits) | r.
 #include <algorithm>
 
+#include "variants.cuh"
 #include "xtn_common.cuh"
 #include "xtn_kernels.h"
 
@@ -44,60 +45,109 @@ void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_
   prof_end(s);
 }
 
+// Group [lo, hi) of fingerprint fp in the sorted index (empty if absent).
+__device__ __forceinline__ void index_range(const uint64_t* __restrict__ rec, uint64_t n_rec,
+                                            const uint32_t* __restrict__ dir, int dir_bits,
+                                            int gshift, uint64_t fp, uint32_t* err, uint64_t& a,
+                                            uint64_t& c) {
+  const uint64_t g = fp >> gshift;
+  const uint64_t top = fp >> (64 - dir_bits);
+  uint64_t lo = dir[top], hi = dir[top + 1];
+  if (hi > n_rec || lo > hi) {
+    atomicOr(err, DERR_RANGE);
+    lo = hi = 0;
+  }
+  a = lo;
+  uint64_t b = hi;  // lower bound of g
+  while (a < b) {
+    const uint64_t mid = (a + b) >> 1;
+    if ((rec[mid] >> gshift) < g) a = mid + 1; else b = mid;
+  }
+  c = a;
+  uint64_t e = hi;  // upper bound of g
+  while (c < e) {
+    const uint64_t mid = (c + e) >> 1;
+    if ((rec[mid] >> gshift) <= g) c = mid + 1; else e = mid;
+  }
+}
+
 __global__ void __launch_bounds__(256)
     k_query_lookup(const Key128* __restrict__ qkeys, const uint8_t* __restrict__ qlens,
-                   const uint64_t* __restrict__ q_rec_off, int64_t n_q, uint64_t n_qv,
-                   const uint64_t* __restrict__ rec, uint64_t n_rec,
-                   const uint32_t* __restrict__ dir, int dir_bits, int gshift,
+                   const uint32_t* __restrict__ qeqprev, const uint64_t* __restrict__ q_rec_off,
+                   int64_t n_q, uint64_t n_qv, int d, const uint64_t* __restrict__ rec,
+                   uint64_t n_rec, const uint32_t* __restrict__ dir, int dir_bits, int gshift,
                    uint32_t* __restrict__ qv_start, uint32_t* __restrict__ qv_cnt,
                    uint32_t* __restrict__ qv_q, uint32_t* __restrict__ err) {
+  __shared__ VariantTables s_tab;
+  __shared__ WarpVariants s_warp[8];
+  init_variant_tables(&s_tab);
+  __syncthreads();
+  WarpVariants* w = &s_warp[threadIdx.x >> 5];
   const uint32_t lane = lane_id();
+  const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = warp0; q < n_q; q += n_warps) {
-    const Key128 k = qkeys[q];
     const uint32_t L = qlens[q];
+    const uint32_t eq = qeqprev[q];
     const uint64_t base = q_rec_off[q];
     uint32_t cnt = (uint32_t)(q_rec_off[q + 1] - base);
     if (base + cnt > n_qv) {
       if (lane == 0) atomicOr(err, DERR_RANGE);
       cnt = 0;
     }
-    for (uint32_t v = lane; v < cnt; v += 32) {
-      const uint64_t fp = fingerprint(variant_of(k, L, v), 0ull);
-      const uint64_t g = fp >> gshift;
-      const uint64_t top = fp >> (64 - dir_bits);
-      uint64_t lo = dir[top], hi = dir[top + 1];
-      if (hi > n_rec || lo > hi) {
-        atomicOr(err, DERR_RANGE);
-        lo = hi = 0;
+    const SeqShape sh = warp_prepare(w, &s_tab, qkeys[q], L, eq, lane);
+    if (d <= 2) {
+      uint32_t total = canonical_total_d2(sh, d);
+      if (total != cnt) {
+        if (lane == 0) atomicOr(err, DERR_RANGE);
+        total = 0;
       }
-      uint64_t a = lo, b = hi;  // lower bound of g
-      while (a < b) {
-        const uint64_t mid = (a + b) >> 1;
-        if ((rec[mid] >> gshift) < g) a = mid + 1; else b = mid;
+      for (uint32_t v = lane; v < total; v += 32) {
+        uint64_t a, c;
+        index_range(rec, n_rec, dir, dir_bits, gshift,
+                    canonical_fingerprint_d2(w, &s_tab, sh, v, 0ull), err, a, c);
+        qv_start[base + v] = (uint32_t)a;
+        qv_cnt[base + v] = (uint32_t)(c - a);
+        qv_q[base + v] = (uint32_t)q;
       }
-      uint64_t c = a, e = hi;  // upper bound of g
-      while (c < e) {
-        const uint64_t mid = (c + e) >> 1;
-        if ((rec[mid] >> gshift) <= g) c = mid + 1; else e = mid;
+    } else {
+      const uint32_t total = cnt ? variant_count(L, (uint32_t)d) : 0u;
+      uint32_t written = 0;
+      for (uint32_t v0 = 0; v0 < total; v0 += 32) {
+        const uint32_t v = v0 + lane;
+        bool keep = false;
+        Subset ss{0u, 0u, 0u, 0u};
+        if (v < total) {
+          ss = unrank_subset(L, v);
+          keep = is_canonical(subset_mask(ss), eq);
+        }
+        const uint32_t bal = __ballot_sync(FULL_MASK, keep);
+        const uint32_t slot = written + __popc(bal & lt_mask);
+        written += __popc(bal);
+        if (keep && slot < cnt) {
+          uint64_t a, c;
+          index_range(rec, n_rec, dir, dir_bits, gshift, subset_fingerprint(w, L, ss, 0ull), err,
+                      a, c);
+          qv_start[base + slot] = (uint32_t)a;
+          qv_cnt[base + slot] = (uint32_t)(c - a);
+          qv_q[base + slot] = (uint32_t)q;
+        }
       }
-      qv_start[base + v] = (uint32_t)a;
-      qv_cnt[base + v] = (uint32_t)(c - a);
-      qv_q[base + v] = (uint32_t)q;
     }
   }
 }
 
-void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint64_t* q_rec_off,
-                         int64_t n_q, uint64_t n_qv, const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,
+void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint32_t* qeqprev,
+                         const uint64_t* q_rec_off, int64_t n_q, uint64_t n_qv, int d,
+                         const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,
                          int dir_bits, int gshift, uint32_t* qv_start, uint32_t* qv_cnt,
                          uint32_t* qv_q, int sms, uint32_t* err, cudaStream_t s) {
   if (n_q <= 0) return;
   const int blocks = (int)std::min<int64_t>((n_q + 7) / 8, (int64_t)sms * 8);
   prof_begin(s, "k_query_lookup", (double)n_q * 30.0);
-  k_query_lookup<<<blocks, 256, 0, s>>>(qkeys, qlens, q_rec_off, n_q, n_qv, rec, n_rec, dir, dir_bits,
-                                        gshift, qv_start, qv_cnt, qv_q, err);
+  k_query_lookup<<<blocks, 256, 0, s>>>(qkeys, qlens, qeqprev, q_rec_off, n_q, n_qv, d, rec, n_rec,
+                                        dir, dir_bits, gshift, qv_start, qv_cnt, qv_q, err);
   prof_end(s);
 }
 
@@ -105,12 +155,7 @@ __global__ void __launch_bounds__(256)
     k_query_emit(const uint64_t* __restrict__ rec, uint64_t n_rec, uint32_t ref_bits,
                  const uint32_t* __restrict__ qv_start, const uint32_t* __restrict__ qv_q,
                  const uint64_t* __restrict__ cand_off, uint64_t n_qv, uint64_t n_cand,
-                 uint64_t* __restrict__ out, uint32_t* __restrict__ hist, int hist_hi,
-                 uint32_t* __restrict__ err) {
-  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
-  const int passes = (hist_hi + 7) / 8;
-  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
-  __syncthreads();
+                 uint64_t* __restrict__ out, uint32_t* __restrict__ err) {
   const uint64_t idmask = (1ull << ref_bits) - 1ull;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_cand;
        t += (uint64_t)gridDim.x * blockDim.x) {
@@ -127,26 +172,18 @@ __global__ void __launch_bounds__(256)
       atomicOr(err, DERR_RANGE);
     }
     out[t] = w;
-    for (int p = 0; p < passes; ++p) {
-      const int sh = 8 * p;
-      const int bits = min(8, hist_hi - sh);
-      atomicAdd(&s_hist[p * RADIX + (uint32_t)((w >> sh) & ((1u << bits) - 1u))], 1u);
-    }
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x)
-    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
 }
 
 void launch_query_emit(const uint64_t* rec, uint64_t n_rec, uint32_t ref_bits,
                        const uint32_t* qv_start, const uint32_t* qv_q, const uint64_t* cand_off,
-                       uint64_t n_qv, uint64_t n_cand, uint64_t* out, uint32_t* hist,
-                       int hist_hi, int sms, uint32_t* err, cudaStream_t s) {
+                       uint64_t n_qv, uint64_t n_cand, uint64_t* out, int sms, uint32_t* err,
+                       cudaStream_t s) {
   if (n_cand == 0) return;
   const int blocks = (int)std::min<uint64_t>((n_cand + 255) / 256, (uint64_t)sms * 8);
   prof_begin(s, "k_query_emit", (double)n_cand * 24.0);
   k_query_emit<<<blocks, 256, 0, s>>>(rec, n_rec, ref_bits, qv_start, qv_q, cand_off, n_qv, n_cand,
-                                      out, hist, hist_hi, err);
+                                      out, err);
   prof_end(s);
 }
 

@@ -20,6 +20,7 @@
 //   6. keys leave shared memory in digit order: runs of one digit land on
 //      consecutive addresses.
 #include <algorithm>
+#include <mutex>
 
 #include "xtn_common.cuh"
 #include "xtn_kernels.h"
@@ -60,64 +61,68 @@ __global__ void k_digit_scan(const uint32_t* __restrict__ hist, uint64_t* __rest
   digit_base[p * RADIX + t] = off + inc - v;
 }
 
-template <int THREADS, int ITEMS>
+template <int THREADS, int ITEMS, int MATCH = 0>
 struct OnesweepSmem {
   static constexpr int WARPS = THREADS / 32;
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr size_t keys_bytes = (size_t)TILE * 8;
   static constexpr size_t whist_bytes = (size_t)WARPS * RADIX * 4;
-  static constexpr size_t bytes = keys_bytes + whist_bytes + RADIX * 4 + RADIX * 8;
+  static constexpr size_t match_bytes = MATCH == 2 ? (size_t)WARPS * RADIX * 4 : 0;
+  static constexpr size_t bytes = keys_bytes + whist_bytes + RADIX * 4 + RADIX * 8 + match_bytes;
 };
 
-template <int THREADS, int ITEMS, int MIN_BLOCKS>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
-    k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
-               int bits, const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
-               uint32_t* __restrict__ ctr, uint32_t* __restrict__ err) {
-  using SM = OnesweepSmem<THREADS, ITEMS>;
-  constexpr int WARPS = SM::WARPS;
-  constexpr int TILE = SM::TILE;
-  static_assert(THREADS >= RADIX, "one thread per digit");
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
-  uint32_t* s_tstart = s_whist + WARPS * RADIX;
-  int64_t* s_obase = reinterpret_cast<int64_t*>(s_tstart + RADIX);
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_wsum[THREADS / 32];
-
-  const uint32_t tile = tile_id(ctr, &s_tile);
-  const int64_t tile_base = (int64_t)tile * TILE;
-  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  const uint32_t dmask = (1u << bits) - 1u;
-
-  for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) s_whist[k] = 0;
-
-  uint64_t key[ITEMS];
-  const int64_t wbase = tile_base + (int64_t)warp * 32 * ITEMS;
+// Lanes of the warp holding the same digit as this lane (lanes with !valid
+// excluded).  MATCH = 0: one ballot per digit bit; MATCH = 1: match.any.
+template <int MATCH>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dig, uint32_t valid_mask) {
+  if (MATCH == 1) return __match_any_sync(FULL_MASK, dig) & valid_mask;
+  uint32_t peers = valid_mask;
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int64_t pos = wbase + i * 32 + lane;
-    key[i] = pos < n ? __ldcs(in + pos) : 0ull;
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t bal = __ballot_sync(FULL_MASK, (dig >> b) & 1u);
+    peers &= ((dig >> b) & 1u) ? bal : ~bal;
   }
-  __syncthreads();
+  return peers;
+}
 
-  // 2. stable warp multi-split ranking
-  uint32_t* wh = s_whist + warp * RADIX;
+// Stable rank of every item inside its warp (warp-private 256-bin counters).
+// MATCH = 2: each lane ORs its bit into a per-warp bin of its digit and reads
+// the bin back as its peer mask; the lowest peer bumps the counter, clears
+// the bin and hands the old count to its peers with one shuffle.
+template <int ITEMS, int MATCH, bool FULL>
+__device__ __forceinline__ void rank_items(const uint64_t (&key)[ITEMS], uint16_t (&rank)[ITEMS],
+                                           uint32_t* wh, uint32_t* mb, int64_t wbase, int64_t n,
+                                           int shift, uint32_t dmask, uint32_t lane) {
   const uint32_t lt_mask = (1u << lane) - 1u;
-  uint16_t rank[ITEMS];
+  if (MATCH == 2) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool valid = FULL || (wbase + i * 32 + lane < n);
+      const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
+      if (valid) atomicOr(&mb[dig], 1u << lane);
+      __syncwarp();
+      const uint32_t peers = valid ? mb[dig] : 0u;
+      __syncwarp();
+      const uint32_t before = peers & lt_mask;
+      uint32_t old = 0;
+      if (valid && before == 0) {
+        old = wh[dig];
+        wh[dig] = old + __popc(peers);
+        mb[dig] = 0u;
+      }
+      const int leader = valid ? __ffs(peers) - 1 : (int)lane;
+      old = __shfl_sync(FULL_MASK, old, leader);
+      rank[i] = (uint16_t)(old + __popc(before));
+      __syncwarp();
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const bool valid = wbase + i * 32 + lane < n;
+    const bool valid = FULL || (wbase + i * 32 + lane < n);
     const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
-    uint32_t peers = __ballot_sync(FULL_MASK, valid);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      if (b < bits) {
-        const uint32_t bal = __ballot_sync(FULL_MASK, (dig >> b) & 1u);
-        peers &= ((dig >> b) & 1u) ? bal : ~bal;
-      }
-    }
+    const uint32_t vmask = FULL ? FULL_MASK : __ballot_sync(FULL_MASK, valid);
+    const uint32_t peers = digit_peers<MATCH>(dig, vmask);
     const uint32_t before = peers & lt_mask;
     uint32_t base = 0;
     if (valid) base = wh[dig];
@@ -126,6 +131,57 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     __syncwarp();
     rank[i] = (uint16_t)(base + __popc(before));
   }
+}
+
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int MATCH>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
+    k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
+               int bits, const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
+               uint32_t* __restrict__ ctr, uint32_t* __restrict__ err) {
+  using SM = OnesweepSmem<THREADS, ITEMS, MATCH>;
+  constexpr int WARPS = SM::WARPS;
+  constexpr int TILE = SM::TILE;
+  static_assert(THREADS >= RADIX, "one thread per digit");
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
+  uint32_t* s_tstart = s_whist + WARPS * RADIX;
+  int64_t* s_obase = reinterpret_cast<int64_t*>(s_tstart + RADIX);
+  uint32_t* s_match = reinterpret_cast<uint32_t*>(s_obase + RADIX);
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wsum[THREADS / 32];
+
+  const uint32_t tile = tile_id(ctr, &s_tile);
+  const int64_t tile_base = (int64_t)tile * TILE;
+  const bool full = tile_base + TILE <= n;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t dmask = (1u << bits) - 1u;
+
+  for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) s_whist[k] = 0;
+  if (MATCH == 2)
+    for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) s_match[k] = 0;
+
+  // 1. load: warp w reads its contiguous 32*ITEMS keys item-major
+  uint64_t key[ITEMS];
+  const int64_t wbase = tile_base + (int64_t)warp * 32 * ITEMS;
+  if (full) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) key[i] = __ldcs(in + wbase + i * 32 + lane);
+  } else {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int64_t pos = wbase + i * 32 + lane;
+      key[i] = pos < n ? __ldcs(in + pos) : 0ull;
+    }
+  }
+  __syncthreads();
+
+  // 2. stable warp multi-split ranking
+  uint32_t* wh = s_whist + warp * RADIX;
+  uint32_t* mb = s_match + warp * RADIX;
+  uint16_t rank[ITEMS];
+  if (full) rank_items<ITEMS, MATCH, true>(key, rank, wh, mb, wbase, n, shift, dmask, lane);
+  else rank_items<ITEMS, MATCH, false>(key, rank, wh, mb, wbase, n, shift, dmask, lane);
   __syncthreads();
 
   // 3. warp offsets per digit, tile counts, publish aggregates
@@ -143,7 +199,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
   // exclusive scan of tile counts over digits
   {
-    uint32_t v = tcount;
+    const uint32_t v = tcount;
     uint32_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -163,8 +219,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   // 4. scatter into shared memory in digit order
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const bool valid = wbase + i * 32 + lane < n;
-    if (valid) {
+    if (full || wbase + i * 32 + lane < n) {
       const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
       s_keys[s_tstart[dig] + wh[dig] + rank[i]] = key[i];
     }
@@ -182,7 +237,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   __syncthreads();
 
   // 6. write out in digit order
-  const int tile_n = (int)(n - tile_base < TILE ? n - tile_base : TILE);
+  const int tile_n = full ? TILE : (int)(n - tile_base);
   for (int j = threadIdx.x; j < tile_n; j += THREADS) {
     const uint64_t k = s_keys[j];
     const uint32_t dig = (uint32_t)(k >> shift) & dmask;
@@ -192,17 +247,26 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
 }
 
-// Tile configurations (threads, items per thread, min blocks per SM).  The
-// big configuration sorts the variant records; the small one the pairs.
+// Tile configurations (id, threads, items per thread, min blocks per SM,
+// ranking: 0 ballots / 1 match.any).  Both sorts use configuration 9 by
+// default; the autotuner may pick others.
 #define XTN_ONESWEEP_CONFIGS(X) \
-  X(0, 256, 16, 3)              \
-  X(1, 256, 24, 2)              \
-  X(2, 512, 12, 2)              \
-  X(3, 256, 8, 4)
+  X(0, 256, 16, 3, 0)           \
+  X(1, 256, 24, 2, 0)           \
+  X(2, 512, 12, 2, 0)           \
+  X(3, 256, 8, 4, 0)            \
+  X(4, 256, 16, 3, 1)           \
+  X(5, 256, 20, 3, 0)           \
+  X(6, 384, 16, 2, 0)           \
+  X(7, 256, 12, 4, 0)           \
+  X(8, 256, 16, 3, 2)           \
+  X(9, 256, 20, 3, 2)           \
+  X(10, 512, 16, 1, 2)          \
+  X(11, 256, 24, 2, 2)
 
 int onesweep_tile(int cfg) {
   switch (cfg) {
-#define X(id, T, I, B) \
+#define X(id, T, I, B, M) \
   case id: return T * I;
     XTN_ONESWEEP_CONFIGS(X)
 #undef X
@@ -210,23 +274,26 @@ int onesweep_tile(int cfg) {
   return 0;
 }
 
+int onesweep_configs() { return 12; }
+
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    int shift, int bits, const uint64_t* digit_base,
                                    uint64_t* status, uint32_t* ctr, uint32_t* err, cudaStream_t s) {
   switch (cfg) {
-#define X(id, T, I, B)                                                                      \
-  case id: {                                                                                \
-    using SM = OnesweepSmem<T, I>;                                                          \
-    static bool attr = false;                                                               \
-    if (!attr) {                                                                            \
-      cudaFuncSetAttribute(k_onesweep<T, I, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           (int)SM::bytes);                                                 \
-      attr = true;                                                                          \
-    }                                                                                       \
-    const uint32_t tiles = div_up_u32(n, SM::TILE);                                         \
-    k_onesweep<T, I, B><<<tiles, T, SM::bytes, s>>>(in, out, n, shift, bits, digit_base,    \
-                                                    status, ctr, err);                      \
-    return cudaGetLastError();                                                              \
+#define X(id, T, I, B, M)                                                                     \
+  case id: {                                                                                  \
+    using SM = OnesweepSmem<T, I, M>;                                                         \
+    static std::once_flag once;                                                               \
+    std::call_once(once, [] {                                                                 \
+      cudaFuncSetAttribute(k_onesweep<T, I, B, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)SM::bytes);                                                   \
+      cudaFuncSetAttribute(k_onesweep<T, I, B, M>,                                            \
+                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
+    });                                                                                       \
+    const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
+    k_onesweep<T, I, B, M><<<tiles, T, SM::bytes, s>>>(in, out, n, shift, bits, digit_base,   \
+                                                       status, ctr, err);                     \
+    return cudaGetLastError();                                                                \
   }
     XTN_ONESWEEP_CONFIGS(X)
 #undef X

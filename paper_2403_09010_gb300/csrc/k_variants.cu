@@ -3,18 +3,21 @@
 // output chunk whose size is known ahead of time).
 //
 //   k_encode : ASCII sequence -> 128-bit key of 5-bit residue codes
-//              (Appendix "Compression of TCR sequences"), its length, and its
-//              number of deletion variants sum_{k<=min(d,L)} C(L, k).
-//   k_expand : one warp per sequence; lane v builds variant v (0 deletions,
-//              then every single deletion, then every pair, then every
-//              triple, subsets in colexicographic order), fingerprints it and
-//              writes the 64-bit record  fingerprint[63:b] | id[b-1:0]  at
-//              rec_off[s] + v.  Consecutive lanes write consecutive records,
-//              so every warp store is one contiguous 256-byte run.  The same
-//              kernel accumulates the digit histograms of every radix pass
-//              that will sort these records (one read of the data saved).
+//              (Appendix "Compression of TCR sequences"), its length, the
+//              mask of positions equal to their left neighbour, and its
+//              number of canonical deletion subsets (see is_canonical).
+//   k_expand : one warp per sequence; lane v takes canonical variant v (see
+//              variants.cuh), fingerprints it from the prefix sums and writes
+//              the 64-bit record  fingerprint[63:b] | id[b-1:0]  at
+//              rec_off[s] + v, so every warp store is one contiguous run.  The
+//              kernel also accumulates the digit histograms of every radix
+//              pass that will sort the records.
+//   k_peq    : per sequence, for each residue code c, the bit mask of the
+//              positions holding c (the match vectors of the bit-parallel
+//              edit distance used in verification).
 #include <algorithm>
 
+#include "variants.cuh"
 #include "xtn_common.cuh"
 #include "xtn_kernels.h"
 
@@ -28,22 +31,26 @@ __constant__ uint8_t c_letter_code[26] = {
 
 __global__ void k_encode(const uint8_t* __restrict__ seqs, const int64_t* __restrict__ off,
                          int64_t n, int d, Key128* __restrict__ keys, uint8_t* __restrict__ lens,
-                         uint32_t* __restrict__ vcount, uint32_t* __restrict__ err) {
+                         uint32_t* __restrict__ eqprev_out, uint32_t* __restrict__ vcount,
+                         uint32_t* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t a = off[i], b = off[i + 1], total = off[n];
   Key128 k{0ull, 0ull};
-  uint32_t L = 0;
+  uint32_t L = 0, eqprev = 0;
   if (a < 0 || b < a || b > total) {
     atomicOr(err, DERR_RANGE);
   } else if (b - a > XTN_MAX_LEN) {
     atomicOr(err, DERR_TOO_LONG);
   } else {
     L = (uint32_t)(b - a);
+    uint32_t prev = 0;
     for (uint32_t p = 0; p < L; ++p) {
       const uint32_t ch = seqs[a + p];
       const uint32_t c = (ch >= 'A' && ch <= 'Z') ? c_letter_code[ch - 'A'] : 0u;
       if (c == 0) atomicOr(err, DERR_BAD_RESIDUE);
+      if (p > 0 && c == prev) eqprev |= 1u << p;
+      prev = c;
       const uint32_t m = 5 * p;
       if (m < 64) {
         k.lo |= (uint64_t)c << m;
@@ -55,48 +62,143 @@ __global__ void k_encode(const uint8_t* __restrict__ seqs, const int64_t* __rest
   }
   keys[i] = k;
   lens[i] = (uint8_t)L;
-  vcount[i] = variant_count(L, (uint32_t)d);
+  eqprev_out[i] = eqprev;
+  vcount[i] = canonical_count(eqprev, L, (uint32_t)d);
 }
 
 constexpr int EXPAND_THREADS = 256;
 
+// One count per radix pass for record `rec` (8-bit digits from bit `lo`; the
+// last digit keeps only `last_mask`).
+__device__ __forceinline__ void count_digits(uint32_t* s_hist, uint64_t rec, int lo, int passes,
+                                             uint32_t last_mask) {
+  const uint64_t r = rec >> lo;
+#pragma unroll
+  for (int p = 0; p < MAX_PASSES; ++p) {
+    if (p < passes) {
+      const uint32_t m = p == passes - 1 ? last_mask : 0xffu;
+      atomicAdd(&s_hist[p * RADIX + ((uint32_t)(r >> (8 * p)) & m)], 1u);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(EXPAND_THREADS)
     k_expand(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens,
-             const uint64_t* __restrict__ rec_off, int64_t n, const uint32_t* __restrict__ seq_rep,
-             uint32_t id_bits, uint64_t* __restrict__ out, uint64_t n_rec,
-             uint32_t* __restrict__ hist, int hist_lo, int hist_passes, int hist_hi,
-             uint32_t* __restrict__ err) {
+             const uint32_t* __restrict__ eqprev, const uint64_t* __restrict__ rec_off, int64_t n,
+             int d, const uint32_t* __restrict__ seq_rep, uint32_t id_bits,
+             uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist, int hist_lo,
+             int hist_passes, int hist_hi, uint32_t* __restrict__ err) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  __shared__ VariantTables s_tab;
+  __shared__ WarpVariants s_warp[EXPAND_THREADS / 32];
   for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  init_variant_tables(&s_tab);
   __syncthreads();
+  WarpVariants* w = &s_warp[threadIdx.x >> 5];
   const uint32_t lane = lane_id();
+  const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint64_t idmask = (id_bits >= 64) ? ~0ull : ((1ull << id_bits) - 1ull);
-  for (int64_t s = warp0; s < n; s += n_warps) {
-    const Key128 k = keys[s];
-    const uint32_t L = lens[s];
-    const uint64_t base = rec_off[s];
-    uint32_t cnt = (uint32_t)(rec_off[s + 1] - base);
-    if (base + cnt > n_rec) {
-      if (lane == 0) atomicOr(err, DERR_RANGE);
-      cnt = 0;
+  const int last_bits = hist_hi - hist_lo - 8 * (hist_passes - 1);
+  const uint32_t last_mask = (1u << last_bits) - 1u;
+  // each warp takes 32 consecutive sequences per round: their metadata is
+  // read with one coalesced load per field and handed out by shuffles
+  for (int64_t s0 = warp0 * 32; s0 < n; s0 += n_warps * 32) {
+    const int64_t my = s0 + lane;
+    Key128 mk{0ull, 0ull};
+    uint32_t mL = 0, mEq = 0, mRep = 0;
+    uint64_t mBase = 0, mEnd = 0;
+    if (my < n) {
+      mk = keys[my];
+      mL = lens[my];
+      mEq = eqprev[my];
+      mBase = rec_off[my];
+      mEnd = rec_off[my + 1];
+      if (seq_rep) mRep = seq_rep[my];
     }
-    const uint64_t salt = seq_rep ? rep_salt(seq_rep[s]) : 0ull;
-    for (uint32_t v = lane; v < cnt; v += 32) {
-      const Key128 var = variant_of(k, L, v);
-      const uint64_t rec = (fingerprint(var, salt) & ~idmask) | (uint64_t)s;
-      out[base + v] = rec;
-      for (int p = 0; p < hist_passes; ++p) {
-        const int sh = hist_lo + 8 * p;
-        const int bits = min(8, hist_hi - sh);
-        atomicAdd(&s_hist[p * RADIX + (uint32_t)((rec >> sh) & ((1u << bits) - 1u))], 1u);
+    const int m = (n - s0 < 32) ? (int)(n - s0) : 32;
+    for (int j = 0; j < m; ++j) {
+      const int64_t s = s0 + j;
+      const Key128 k{__shfl_sync(FULL_MASK, mk.lo, j), __shfl_sync(FULL_MASK, mk.hi, j)};
+      const uint32_t L = __shfl_sync(FULL_MASK, mL, j);
+      const uint32_t eq = __shfl_sync(FULL_MASK, mEq, j);
+      const uint64_t base = __shfl_sync(FULL_MASK, mBase, j);
+      uint32_t cnt = (uint32_t)(__shfl_sync(FULL_MASK, mEnd, j) - base);
+      if (base + cnt > n_rec) {
+        if (lane == 0) atomicOr(err, DERR_RANGE);
+        cnt = 0;
+      }
+      const uint64_t salt = seq_rep ? rep_salt(__shfl_sync(FULL_MASK, mRep, j)) : 0ull;
+      const SeqShape sh = warp_prepare(w, &s_tab, k, L, eq, lane);
+      if (d <= 2) {
+        uint32_t total = canonical_total_d2(sh, d);
+        if (total != cnt) {
+          if (lane == 0) atomicOr(err, DERR_RANGE);
+          total = 0;
+        }
+        for (uint32_t v = lane; v < total; v += 32) {
+          const uint64_t rec =
+              (canonical_fingerprint_d2(w, &s_tab, sh, v, salt) & ~idmask) | (uint64_t)s;
+          out[base + v] = rec;
+          count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+        }
+      } else {
+        // every subset with <= d deletions, canonical ones kept (ballot compaction)
+        const uint32_t total = cnt ? variant_count(L, (uint32_t)d) : 0u;
+        uint32_t written = 0;
+        for (uint32_t v0 = 0; v0 < total; v0 += 32) {
+          const uint32_t v = v0 + lane;
+          bool keep = false;
+          Subset ss{0u, 0u, 0u, 0u};
+          if (v < total) {
+            ss = unrank_subset(L, v);
+            keep = is_canonical(subset_mask(ss), eq);
+          }
+          const uint32_t bal = __ballot_sync(FULL_MASK, keep);
+          const uint32_t slot = written + __popc(bal & lt_mask);
+          if (keep && slot < cnt) {
+            const uint64_t rec = (subset_fingerprint(w, L, ss, salt) & ~idmask) | (uint64_t)s;
+            out[base + slot] = rec;
+            count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+          }
+          written += __popc(bal);
+        }
+        if (written != cnt && lane == 0) atomicOr(err, DERR_RANGE);
       }
     }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x)
     if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+}
+
+// Match vectors: peq[i * PEQ_STRIDE + c - 1] = {positions p of sequence i with code c}.
+constexpr int PEQ_THREADS = 128;
+
+__global__ void __launch_bounds__(PEQ_THREADS)
+    k_peq(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens, int64_t n,
+          uint32_t* __restrict__ peq) {
+  __shared__ uint32_t s_peq[PEQ_THREADS * PEQ_STRIDE];
+  const int64_t first = (int64_t)blockIdx.x * PEQ_THREADS;
+  for (int k = threadIdx.x; k < PEQ_THREADS * PEQ_STRIDE; k += PEQ_THREADS) s_peq[k] = 0;
+  __syncthreads();
+  const int64_t i = first + threadIdx.x;
+  if (i < n) {
+    Key128 k = keys[i];
+    const uint32_t L = lens[i];
+    uint32_t* row = s_peq + threadIdx.x * PEQ_STRIDE;
+    for (uint32_t p = 0; p < L; ++p) {
+      const uint32_t c = (uint32_t)(k.lo & 31u);
+      k.lo = (k.lo >> 5) | (k.hi << 59);
+      k.hi >>= 5;
+      if (c >= 1 && c <= 20) row[c - 1] |= 1u << p;
+    }
+  }
+  __syncthreads();
+  const int64_t rows = (n - first < PEQ_THREADS) ? (n - first) : PEQ_THREADS;
+  for (int64_t k = threadIdx.x; k < rows * PEQ_STRIDE; k += PEQ_THREADS)
+    peq[first * PEQ_STRIDE + k] = s_peq[k];
 }
 
 // seq_rep[i] = repertoire of sequence i: the last r with rep_off[r] <= i.
@@ -121,25 +223,33 @@ void launch_seq_rep(const int64_t* rep_off, int64_t n_rep, uint32_t* seq_rep, in
 }
 
 void launch_encode(const uint8_t* seqs, const int64_t* off, int64_t n, int d, Key128* keys,
-                   uint8_t* lens, uint32_t* vcount, uint32_t* err, cudaStream_t s) {
+                   uint8_t* lens, uint32_t* eqprev, uint32_t* vcount, uint32_t* err,
+                   cudaStream_t s) {
   if (n <= 0) return;
-  prof_begin(s, "k_encode", (double)n * (16 + 16 + 1 + 4 + 8));
-  k_encode<<<div_up_u32(n, 256), 256, 0, s>>>(seqs, off, n, d, keys, lens, vcount, err);
+  prof_begin(s, "k_encode", (double)n * (16 + 16 + 1 + 4 + 4 + 8));
+  k_encode<<<div_up_u32(n, 256), 256, 0, s>>>(seqs, off, n, d, keys, lens, eqprev, vcount, err);
   prof_end(s);
 }
 
-void launch_expand(const Key128* keys, const uint8_t* lens, const uint64_t* rec_off, int64_t n,
-                   const uint32_t* seq_rep, uint32_t id_bits, uint64_t* out, uint64_t n_rec,
-                   uint32_t* hist, int hist_lo, int hist_hi, int sms, uint32_t* err,
-                   cudaStream_t s) {
+void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
+                   const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
+                   uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
+                   int hist_hi, int sms, uint32_t* err, cudaStream_t s) {
   if (n <= 0) return;
   const int passes = (hist_hi - hist_lo + 7) / 8;
-  const int64_t warps_needed = n;
-  int blocks = (int)std::min<int64_t>((warps_needed + 7) / 8, (int64_t)sms * 8);
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   if (blocks < 1) blocks = 1;
-  prof_begin(s, "k_expand", (double)n_rec * 8.0 + (double)n * 25.0);
-  k_expand<<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, rec_off, n, seq_rep, id_bits, out, n_rec,
-                                             hist, hist_lo, passes, hist_hi, err);
+  prof_begin(s, "k_expand", (double)n_rec * 8.0 + (double)n * 29.0);
+  k_expand<<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits,
+                                             out, n_rec, hist, hist_lo, passes, hist_hi, err);
+  prof_end(s);
+}
+
+void launch_peq(const Key128* keys, const uint8_t* lens, int64_t n, uint32_t* peq,
+                cudaStream_t s) {
+  if (n <= 0) return;
+  prof_begin(s, "k_peq", (double)n * (17.0 + 4.0 * PEQ_STRIDE));
+  k_peq<<<div_up_u32(n, PEQ_THREADS), PEQ_THREADS, 0, s>>>(keys, lens, n, peq);
   prof_end(s);
 }
 

@@ -1,17 +1,29 @@
-// Duplicate removal and exact verification (Appendix A, XTNeighbor steps 6-7:
-// `unique` after the pair sort, then `map` + `if` with the edit distance),
-// and the TCRdist post-filter (Results, "SymDel lookup can be combined with
-// more advanced similarity metrics").
+// Exact verification and duplicate removal (Appendix A, XTNeighbor steps 6-7:
+// `map` + `if` with the edit distance, `sort` + `unique`), and the TCRdist
+// post-filter (Results, "SymDel lookup can be combined with more advanced
+// similarity metrics").
 //
-// k_unique_verify reads the sorted pair words, drops a word equal to its
-// predecessor (the duplicates of Fig. 1C), drops i == j (one sequence sharing
-// a variant with itself through repeated residues) and pairs from different
-// repertoires, and computes the Levenshtein distance with a band of 2d+1
-// diagonals: only cells with |x - y| <= d can lie on a path of cost <= d, and
-// values are capped at d+1, so the band decides "<= d" exactly and returns
-// the exact distance when it is <= d.  Survivors are compacted in input
-// order (single-pass prefix sum with decoupled look-back), so the output
-// stays sorted by (i, j).
+// The paper removes duplicate pairs first and verifies after; here every
+// candidate is verified first and only the survivors are sorted: the
+// duplicates of Fig. 1C are cheap to verify but costly to sort, and the
+// output is the same set either way.
+//
+//   k_verify_candidates : per candidate (i, j): drop i == j (one sequence
+//                         sharing a variant with itself through repeated
+//                         residues) and pairs from different repertoires,
+//                         reject |len_i - len_j| > d, compute the edit
+//                         distance bit-parallel, keep it if <= d.  Survivors
+//                         are appended with one atomic per warp; their radix
+//                         histograms are accumulated on the way.
+//   k_unique_finalize   : over the sorted survivors, drop a word equal to its
+//                         predecessor (the duplicates of Fig. 1C) and write
+//                         {i, j, dist} rows in order (single-pass compaction
+//                         with decoupled look-back).
+//
+// Edit distance: the bit-vector algorithm of Myers (1999) in the global-
+// distance form of Hyyro (2001).  Pattern i (<= 25 residues) lives in one
+// 32-bit word; its match vectors come from the per-sequence table built by
+// k_peq; the text j is streamed from its packed key, 5 bits per step.
 #include <algorithm>
 
 #include "xtn_common.cuh"
@@ -23,45 +35,32 @@ constexpr int VER_THREADS = 256;
 constexpr int VER_ITEMS = 8;
 constexpr int VER_TILE = VER_THREADS * VER_ITEMS;
 
-// Exact edit distance of a (length la) and b (length lb) if it is <= d,
-// otherwise d + 1.  Band index k holds cell (x, y = x + k - d).
-__device__ __forceinline__ uint32_t lev_banded(const Key128& a, int la, const Key128& b, int lb,
-                                               int d) {
-  const int INF = d + 1;
-  if (la - lb > d || lb - la > d) return (uint32_t)INF;
-  constexpr int W = 2 * XTN_MAX_D + 1;
-  int band[W];
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    const int y = k - d;
-    band[k] = (k <= 2 * d && y >= 0 && y <= lb) ? y : INF;
+// Levenshtein distance between pattern (match vectors peq, length m) and the
+// text held in packed key t (length n).
+__device__ __forceinline__ uint32_t edit_distance(const uint32_t* __restrict__ peq, uint32_t m,
+                                                  Key128 t, uint32_t n) {
+  if (m == 0) return n;
+  uint32_t pv = (m >= 32) ? ~0u : ((1u << m) - 1u);
+  uint32_t mv = 0;
+  uint32_t score = m;
+  const uint32_t hb = 1u << (m - 1);
+  for (uint32_t j = 0; j < n; ++j) {
+    const uint32_t c = (uint32_t)(t.lo & 31u);
+    t.lo = (t.lo >> 5) | (t.hi << 59);
+    t.hi >>= 5;
+    const uint32_t eq = (c - 1u < 20u) ? __ldg(peq + (c - 1u)) : 0u;
+    const uint32_t xv = eq | mv;
+    const uint32_t xh = (((eq & pv) + pv) ^ pv) | eq;
+    uint32_t ph = mv | ~(xh | pv);
+    uint32_t mh = pv & xh;
+    score += (ph & hb) ? 1u : 0u;
+    score -= (mh & hb) ? 1u : 0u;
+    ph = (ph << 1) | 1u;
+    mh <<= 1;
+    pv = mh | ~(xv | ph);
+    mv = ph & xv;
   }
-  for (int x = 1; x <= la; ++x) {
-    const uint32_t ca = code_at(a, x - 1);
-    int left = INF, rowmin = INF;
-    int nb[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      int v = INF;
-      const int y = x + k - d;
-      if (k <= 2 * d) {
-        if (y == 0) {
-          v = min(x, INF);
-        } else if (y >= 1 && y <= lb) {
-          const int diag = band[k] + (ca != code_at(b, y - 1) ? 1 : 0);
-          const int up = (k + 1 <= 2 * d) ? band[k + 1] + 1 : INF;
-          v = min(min(diag, up), min(left + 1, INF));
-        }
-      }
-      nb[k] = v;
-      left = v;
-      rowmin = min(rowmin, v);
-    }
-#pragma unroll
-    for (int k = 0; k < W; ++k) band[k] = nb[k];
-    if (rowmin > d) return (uint32_t)INF;
-  }
-  return (uint32_t)min(band[lb - la + d], INF);
+  return score;
 }
 
 template <int THREADS>
@@ -86,15 +85,90 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_
   return total;
 }
 
+__global__ void __launch_bounds__(256)
+    k_verify_candidates(const uint64_t* __restrict__ cand, uint64_t n, uint32_t j_bits,
+                        const uint32_t* __restrict__ peq_i, const uint8_t* __restrict__ lens_i,
+                        uint64_t n_i, const Key128* __restrict__ keys_j,
+                        const uint8_t* __restrict__ lens_j, uint64_t n_j,
+                        const uint32_t* __restrict__ seq_rep, int self_mode, int d,
+                        uint64_t* __restrict__ surv, uint64_t surv_cap,
+                        unsigned long long* __restrict__ n_surv, uint32_t* __restrict__ hist,
+                        int hist_hi, uint32_t* __restrict__ err) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  const int passes = (hist_hi + 7) / 8;
+  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  __syncthreads();
+  const uint32_t lane = lane_id();
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t jmask = (1ull << j_bits) - 1ull;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < n;
+       t0 += stride) {
+    const uint64_t t = t0 + lane;
+    bool ok = false;
+    uint64_t w = 0;
+    if (t < n) {
+      w = cand[t];
+      const uint64_t i = w >> j_bits, j = w & jmask;
+      ok = i < n_i && j < n_j;
+      if (!ok) atomicOr(err, DERR_RANGE);
+      if (self_mode) ok = ok && i != j;
+      if (ok && seq_rep) ok = seq_rep[i] == seq_rep[j];
+      if (ok) {
+        const uint32_t la = lens_i[i], lb = lens_j[j];
+        ok = (la > lb ? la - lb : lb - la) <= (uint32_t)d &&
+             edit_distance(peq_i + i * PEQ_STRIDE, la, keys_j[j], lb) <= (uint32_t)d;
+      }
+    }
+    const uint32_t bal = __ballot_sync(FULL_MASK, ok);
+    if (bal) {
+      const uint32_t leader = (uint32_t)(__ffs(bal) - 1);
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(n_surv, (unsigned long long)__popc(bal));
+      base = __shfl_sync(FULL_MASK, base, leader);
+      if (ok) {
+        const uint64_t slot = base + __popc(bal & lt_mask);
+        if (slot < surv_cap) {
+          surv[slot] = w;
+          for (int p = 0; p < passes; ++p) {
+            const int sh = 8 * p;
+            const int bits = min(8, hist_hi - sh);
+            atomicAdd(&s_hist[p * RADIX + (uint32_t)((w >> sh) & ((1u << bits) - 1u))], 1u);
+          }
+        } else {
+          atomicOr(err, DERR_RANGE);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+}
+
+void launch_verify_candidates(const uint64_t* cand, uint64_t n, uint32_t j_bits,
+                              const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
+                              const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                              const uint32_t* seq_rep, int self_mode, int d, uint64_t* surv,
+                              uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist, int hist_hi,
+                              int sms, uint32_t* err, cudaStream_t s) {
+  if (n == 0) return;
+  const int blocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
+  prof_begin(s, "k_verify_candidates", (double)n * (8.0 + 2 * 17.0 + 4.0 * 4));
+  k_verify_candidates<<<blocks, 256, 0, s>>>(
+      cand, n, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep, self_mode, d, surv,
+      surv_cap, reinterpret_cast<unsigned long long*>(n_surv), hist, hist_hi, err);
+  prof_end(s);
+}
+
 __global__ void __launch_bounds__(VER_THREADS)
-    k_unique_verify(const uint64_t* __restrict__ pairs, int64_t n, uint32_t j_bits,
-                    const Key128* __restrict__ keys_i, const uint8_t* __restrict__ lens_i,
-                    const Key128* __restrict__ keys_j, const uint8_t* __restrict__ lens_j,
-                    uint64_t n_i, uint64_t n_j, const uint32_t* __restrict__ seq_rep,
-                    int self_mode, int d,
-                    xtn_triple* __restrict__ out, int64_t cap, uint64_t* __restrict__ status,
-                    uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
-                    uint64_t* __restrict__ total_out) {
+    k_unique_finalize(const uint64_t* __restrict__ pairs, int64_t n, uint32_t j_bits,
+                      const uint32_t* __restrict__ peq_i, const uint8_t* __restrict__ lens_i,
+                      uint64_t n_i, const Key128* __restrict__ keys_j,
+                      const uint8_t* __restrict__ lens_j, uint64_t n_j,
+                      xtn_triple* __restrict__ out, int64_t cap, uint64_t* __restrict__ status,
+                      uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
+                      uint64_t* __restrict__ total_out) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_w[VER_THREADS / 32];
   __shared__ uint64_t s_prefix;
@@ -103,28 +177,21 @@ __global__ void __launch_bounds__(VER_THREADS)
   const int64_t base = tbase + (int64_t)threadIdx.x * VER_ITEMS;
   const uint64_t jmask = (1ull << j_bits) - 1ull;
   uint64_t prev = (base > 0 && base - 1 < n) ? pairs[base - 1] : ~0ull;
-  uint32_t keep = 0;
+  uint32_t keep = 0, cnt = 0;
   uint32_t dist[VER_ITEMS];
-  uint32_t cnt = 0;
 #pragma unroll
   for (int it = 0; it < VER_ITEMS; ++it) {
     dist[it] = 0;
     const int64_t p = base + it;
     if (p < n) {
       const uint64_t w = pairs[p];
-      const uint32_t i = (uint32_t)(w >> j_bits), j = (uint32_t)(w & jmask);
+      const uint64_t i = w >> j_bits, j = w & jmask;
       bool ok = w != prev;
       if (i >= n_i || j >= n_j) {
         atomicOr(err, DERR_RANGE);
         ok = false;
       }
-      if (self_mode) ok = ok && i != j;
-      if (ok && seq_rep) ok = seq_rep[i] == seq_rep[j];
-      if (ok) {
-        const uint32_t dd = lev_banded(keys_i[i], lens_i[i], keys_j[j], lens_j[j], d);
-        ok = dd <= (uint32_t)d;
-        dist[it] = dd;
-      }
+      if (ok) dist[it] = edit_distance(peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]);
       keep |= (uint32_t)ok << it;
       cnt += ok;
       prev = w;
@@ -159,20 +226,19 @@ __global__ void __launch_bounds__(VER_THREADS)
 
 size_t verify_status_bytes(int64_t n) { return (size_t)((n + VER_TILE - 1) / VER_TILE) * 8 + 16; }
 
-void launch_unique_verify(const uint64_t* pairs, int64_t n, uint32_t j_bits, const Key128* keys_i,
-                          const uint8_t* lens_i, const Key128* keys_j, const uint8_t* lens_j,
-                          uint64_t n_i, uint64_t n_j, const uint32_t* seq_rep, int self_mode,
-                          int d, xtn_triple* out,
-                          int64_t cap, uint64_t* status, uint32_t* err, uint64_t* total,
-                          cudaStream_t s) {
+void launch_unique_finalize(const uint64_t* pairs, int64_t n, uint32_t j_bits,
+                            const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
+                            const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                            xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
+                            uint64_t* total, cudaStream_t s) {
   if (n <= 0) return;
   const size_t st = verify_status_bytes(n);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
-  prof_begin(s, "k_unique_verify", (double)n * (8.0 + 2 * 17.0));
-  k_unique_verify<<<div_up_u32(n, VER_TILE), VER_THREADS, 0, s>>>(
-      pairs, n, j_bits, keys_i, lens_i, keys_j, lens_j, n_i, n_j, seq_rep, self_mode, d, out, cap,
-      status, ctr, err, total);
+  prof_begin(s, "k_unique_finalize", (double)n * 8.0);
+  k_unique_finalize<<<div_up_u32(n, VER_TILE), VER_THREADS, 0, s>>>(
+      pairs, n, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, out, cap, status, ctr, err,
+      total);
   prof_end(s);
 }
 

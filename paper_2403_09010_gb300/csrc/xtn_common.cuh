@@ -152,37 +152,39 @@ __device__ __forceinline__ uint32_t code_at(const Key128& k, int p) {
   return (uint32_t)(v & 31u);
 }
 
-// Delete residue p: residues above p move down one field.
-__device__ __forceinline__ Key128 delete_at(const Key128& k, int p) {
-  const int m = 5 * p;
-  const uint64_t sh_lo = (k.lo >> 5) | (k.hi << 59);
-  const uint64_t sh_hi = k.hi >> 5;
-  Key128 r;
-  if (m < 64) {
-    const uint64_t low = m == 0 ? 0ull : ((1ull << m) - 1ull);
-    r.lo = (k.lo & low) | (sh_lo & ~low);
-    r.hi = sh_hi;
-  } else {
-    const uint64_t low = m == 64 ? 0ull : ((1ull << (m - 64)) - 1ull);
-    r.lo = k.lo;
-    r.hi = (k.hi & low) | (sh_hi & ~low);
-  }
-  return r;
-}
+// ------------------------------------------------------- fingerprints ---
+// A residue string s_0..s_{L-1} (codes 1..20) is fingerprinted through the
+// polynomial H(s) = sum_k s_k B^k mod 2^64 (B odd, so B is invertible mod
+// 2^64), finished by mix64, a bijection that spreads every input bit over the
+// top bits used for grouping.
+// With prefix sums P[x] = sum_{k<x} s_k B^k, deleting positions
+// p1 < p2 < p3 gives
+//   H = P[p1] + (P[p2] - P[p1+1]) B^-1 + (P[p3] - P[p2+1]) B^-2 + (P[L] - P[p3+1]) B^-3,
+// (fewer deletions: the missing positions are L, L+1, L+2 and P[x] = P[L]
+// for x >= L), so a variant costs four table reads and three multiplies.
+// Equal strings give equal fingerprints whatever they were derived from, so
+// grouping by fingerprint finds every shared variant; unequal strings that
+// collide only add candidate pairs, which the exact distance check removes.
+constexpr uint64_t HASH_B = 0x9E3779B97F4A7C15ull;
 
-// 64-bit fingerprint of a packed variant.  Equal variants give equal
-// fingerprints, so grouping by fingerprint finds every shared variant; the
-// rare unequal variants that collide only add candidate pairs, which the
-// exact distance check removes.  `salt` separates repertoires.
-// Mixing: odd-constant multiplies of both halves, then the SplitMix64
-// finaliser (Steele, Lea & Flood 2014), a bijection on 64 bits.
-__device__ __forceinline__ uint64_t fingerprint(const Key128& k, uint64_t salt) {
-  uint64_t h = (k.lo * 0x9E3779B97F4A7C15ull) ^ ((k.hi + salt) * 0xD6E8FEB86659FD93ull);
-  h ^= h >> 30;
-  h *= 0xBF58476D1CE4E5B9ull;
-  h ^= h >> 27;
-  h *= 0x94D049BB133111EBull;
-  h ^= h >> 31;
+__host__ __device__ constexpr uint64_t inverse_mod_2_64(uint64_t b) {
+  uint64_t x = b;  // Newton iteration x <- x (2 - b x) doubles the valid low bits
+  for (int i = 0; i < 6; ++i) x *= 2ull - b * x;
+  return x;
+}
+constexpr uint64_t HASH_BINV = inverse_mod_2_64(HASH_B);
+constexpr uint64_t HASH_BINV2 = HASH_BINV * HASH_BINV;
+constexpr uint64_t HASH_BINV3 = HASH_BINV2 * HASH_BINV;
+static_assert(HASH_B * HASH_BINV == 1ull, "B must be invertible mod 2^64");
+
+// Xorshift-multiply-xorshift finaliser (a bijection on 64 bits).  The raw
+// polynomial's top bits are far from uniform on residue strings; after this
+// step the top-32-bit collision rate of real variant strings matches the
+// ideal rate.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
+  h ^= h >> 32;
+  h *= 0xD6E8FEB86659FD93ull;
+  h ^= h >> 32;
   return h;
 }
 
@@ -209,31 +211,84 @@ __host__ __device__ __forceinline__ uint32_t variant_count(uint32_t L, uint32_t 
   return c;
 }
 
-// Deletion variant v of key k (length L): v = 0 is k itself, then every single
-// deletion, every pair, every triple; subsets in colexicographic order.
-// sum_{j<=d} C(L, j) variants in all (variant_count).
-__device__ __forceinline__ Key128 variant_of(const Key128& k, uint32_t L, uint32_t v) {
-  if (v == 0) return k;
-  if (v <= L) return delete_at(k, (int)(v - 1));
+// Deletion subsets of the positions {0..L-1} with at most d elements, ranked
+// v = 0 (empty set), then every single position, every pair, every triple;
+// each size in colexicographic order ({p<q} has rank C(q,2)+p among pairs,
+// {p<q<r} has rank C(r,3)+C(q,2)+p among triples).  sum_{k<=d} C(L,k)
+// subsets in all (variant_count).
+struct Subset {
+  uint32_t k, p, q, r;  // size and positions (p < q < r, unused ones 0)
+};
+
+__device__ __forceinline__ Subset unrank_subset(uint32_t L, uint32_t v) {
+  Subset s{0u, 0u, 0u, 0u};
+  if (v == 0) return s;
+  if (v <= L) {
+    s.k = 1;
+    s.p = v - 1;
+    return s;
+  }
   uint32_t t = v - 1 - L;
   const uint32_t c2 = L * (L - 1) / 2;
   if (t < c2) {
-    // {p < q} has colex rank q(q-1)/2 + p
     uint32_t q = (uint32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
     while (q * (q - 1) / 2 > t) --q;
     while ((q + 1) * q / 2 <= t) ++q;
-    const uint32_t p = t - q * (q - 1) / 2;
-    return delete_at(delete_at(k, (int)q), (int)p);
+    s.k = 2;
+    s.q = q;
+    s.p = t - q * (q - 1) / 2;
+    return s;
   }
   t -= c2;
-  // {p < q < r} has colex rank C(r,3) + C(q,2) + p
   uint32_t r = 2;
   while (binom_small(r + 1, 3) <= t) ++r;
   t -= binom_small(r, 3);
   uint32_t q = 1;
   while (binom_small(q + 1, 2) <= t) ++q;
   t -= binom_small(q, 2);
-  return delete_at(delete_at(delete_at(k, (int)r), (int)q), (int)t);
+  s.k = 3;
+  s.r = r;
+  s.q = q;
+  s.p = t;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t subset_mask(const Subset& s) {
+  uint32_t m = 0;
+  if (s.k >= 1) m |= 1u << s.p;
+  if (s.k >= 2) m |= 1u << s.q;
+  if (s.k >= 3) m |= 1u << s.r;
+  return m;
+}
+
+// Within a run of equal residues, deleting any c of its positions leaves the
+// same string, so only the leftmost-c choice is kept: a subset is canonical
+// when every deleted position p whose left neighbour holds the same residue
+// (bit p of `eqprev`) has that neighbour deleted too.  Every deletion variant
+// string still arises from exactly one canonical subset per run pattern.
+__device__ __forceinline__ bool is_canonical(uint32_t mask, uint32_t eqprev) {
+  return (eqprev & mask & ~(mask << 1)) == 0;
+}
+
+// Number of canonical subsets with at most d elements: a canonical subset
+// deletes a prefix of c_i positions from each run i, so the count is the sum
+// of the coefficients of x^0..x^d in prod_i (1 + x + ... + x^{len_i}).
+__host__ __device__ __forceinline__ uint32_t canonical_count(uint32_t eqprev, uint32_t L,
+                                                             uint32_t d) {
+  uint32_t poly[4] = {1u, 0u, 0u, 0u};
+  uint32_t p = 0;
+  while (p < L) {
+    uint32_t run = 1;
+    while (p + run < L && ((eqprev >> (p + run)) & 1u)) ++run;
+    uint32_t next[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t k = 0; k <= d; ++k)
+      for (uint32_t c = 0; c <= k && c <= run; ++c) next[k] += poly[k - c];
+    for (uint32_t k = 0; k <= d; ++k) poly[k] = next[k];
+    p += run;
+  }
+  uint32_t total = 0;
+  for (uint32_t k = 0; k <= d; ++k) total += poly[k];
+  return total;
 }
 
 // ------------------------------------------------------------ host side ---

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include "xtn.h"
@@ -11,21 +13,30 @@ namespace xtn {
 
 struct Key128;
 
-constexpr int RADIX = 256;     // 8-bit digits
-constexpr int MAX_PASSES = 8;  // 64-bit keys
+constexpr int RADIX = 256;       // 8-bit digits
+constexpr int MAX_PASSES = 8;    // 64-bit keys
+constexpr int PEQ_STRIDE = 20;   // match vectors per sequence (one per residue code)
+
+// api.cu: tuning knobs
+std::atomic<int>& cfg_records();
+std::atomic<int>& cfg_pairs();
 
 // k_variants.cu ------------------------------------------------------------
 void launch_encode(const uint8_t* seqs, const int64_t* off, int64_t n, int d, Key128* keys,
-                   uint8_t* lens, uint32_t* vcount, uint32_t* err, cudaStream_t s);
-void launch_expand(const Key128* keys, const uint8_t* lens, const uint64_t* rec_off, int64_t n,
-                   const uint32_t* seq_rep, uint32_t id_bits, uint64_t* out, uint64_t n_rec,
-                   uint32_t* hist, int hist_lo, int hist_hi, int sms, uint32_t* err,
+                   uint8_t* lens, uint32_t* eqprev, uint32_t* vcount, uint32_t* err,
                    cudaStream_t s);
+void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
+                   const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
+                   uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
+                   int hist_hi, int sms, uint32_t* err, cudaStream_t s);
+void launch_peq(const Key128* keys, const uint8_t* lens, int64_t n, uint32_t* peq,
+                cudaStream_t s);
 void launch_seq_rep(const int64_t* rep_off, int64_t n_rep, uint32_t* seq_rep, int64_t n,
                     cudaStream_t s);
 
 // k_radix.cu ---------------------------------------------------------------
 int onesweep_tile(int cfg);
+int onesweep_configs();
 size_t radix_status_bytes(int64_t n, int cfg);
 void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t* hist, int sms,
                       cudaStream_t s);
@@ -43,23 +54,42 @@ void launch_scan_counts(const uint32_t* counts, int64_t n, uint64_t* out, uint64
                         uint32_t* err, cudaStream_t s);
 void launch_scan_group_pairs(const uint32_t* S, const uint32_t* E, int64_t n_groups,
                              uint64_t* out, uint64_t* status, uint32_t* err, cudaStream_t s);
+size_t group_flag_words(int64_t n);
 void launch_group_bounds(const uint64_t* keys, int64_t n, int gshift, uint32_t* S, uint32_t* E,
-                         uint64_t cap, uint64_t* status, uint32_t* err, uint64_t* n_groups,
-                         cudaStream_t s);
+                         uint64_t cap, uint64_t* flags, uint64_t* status, uint32_t* err,
+                         uint64_t* n_groups, cudaStream_t s);
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        const uint64_t* pair_off, int64_t n_groups, uint64_t n_pairs,
-                       uint32_t id_bits, uint64_t* out, uint32_t* hist, int sms, uint32_t* err,
-                       cudaStream_t s);
+                       uint32_t id_bits, uint64_t* out, int sms, uint32_t* err, cudaStream_t s);
 
 // k_verify.cu --------------------------------------------------------------
 size_t verify_status_bytes(int64_t n);
-void launch_unique_verify(const uint64_t* pairs, int64_t n, uint32_t j_bits, const Key128* keys_i,
-                          const uint8_t* lens_i, const Key128* keys_j, const uint8_t* lens_j,
-                          uint64_t n_i, uint64_t n_j, const uint32_t* seq_rep, int self_mode,
-                          int d, xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
-                          uint64_t* total, cudaStream_t s);
+void launch_verify_candidates(const uint64_t* cand, uint64_t n, uint32_t j_bits,
+                              const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
+                              const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                              const uint32_t* seq_rep, int self_mode, int d, uint64_t* surv,
+                              uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist, int hist_hi,
+                              int sms, uint32_t* err, cudaStream_t s);
+void launch_unique_finalize(const uint64_t* pairs, int64_t n, uint32_t j_bits,
+                            const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
+                            const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                            xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
+                            uint64_t* total, cudaStream_t s);
 void launch_tcrdist_filter(const xtn_triple* in, int64_t n, const Key128* keys,
                            const uint8_t* lens, int64_t n_seq, int max_score, xtn_triple* out,
                            uint64_t* status, uint32_t* err, uint64_t* total, cudaStream_t s);
+
+// k_query.cu ---------------------------------------------------------------
+void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_t* dir,
+                      cudaStream_t s);
+void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint32_t* qeqprev,
+                         const uint64_t* q_rec_off, int64_t n_q, uint64_t n_qv, int d,
+                         const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,
+                         int dir_bits, int gshift, uint32_t* qv_start, uint32_t* qv_cnt,
+                         uint32_t* qv_q, int sms, uint32_t* err, cudaStream_t s);
+void launch_query_emit(const uint64_t* rec, uint64_t n_rec, uint32_t ref_bits,
+                       const uint32_t* qv_start, const uint32_t* qv_q, const uint64_t* cand_off,
+                       uint64_t n_qv, uint64_t n_cand, uint64_t* out, int sms, uint32_t* err,
+                       cudaStream_t s);
 
 }  // namespace xtn

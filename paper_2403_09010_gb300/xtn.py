@@ -172,3 +172,16 @@ def profile_report() -> dict:
         name, launches, ms, nbytes = line.split()
         out[name] = (int(launches), float(ms), float(nbytes))
     return out
+
+
+def tune_set(knob: int, value: int) -> None:
+    """Select a tile configuration for one of the radix sorts (see xtn_tune_set)."""
+    check(native.lib().xtn_tune_set(int(knob), int(value)), "xtn_tune_set")
+
+
+def tune_get(knob: int) -> int:
+    return int(native.lib().xtn_tune_get(int(knob)))
+
+
+def tune_count(knob: int) -> int:
+    return int(native.lib().xtn_tune_count(int(knob)))

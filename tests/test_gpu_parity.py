@@ -142,6 +142,24 @@ def test_input_errors(xtn):
         assert ei.value.status == code
 
 
+def test_every_sort_configuration(xtn):
+    R, P = xtn.XTN_TUNE_SORT_RECORDS, xtn.XTN_TUNE_SORT_PAIRS
+    default = (xtn.tune_get(R), xtn.tune_get(P))
+    seqs, off = gen.workload(gen.SELF_1M, 60_000)
+    want = oracle.symdel_self(seqs, off, 2)
+    small_s, small_o = gen.generate(777, 4, 0.5, 0.1)
+    small_want = oracle.symdel_self(small_s, small_o, 2)
+    try:
+        for cfg in range(xtn.tune_count(R)):
+            xtn.tune_set(R, cfg)
+            xtn.tune_set(P, cfg)
+            assert np.array_equal(_rows(xtn.search_self(seqs, off, 2)), want), cfg
+            assert np.array_equal(_rows(xtn.search_self(small_s, small_o, 2)), small_want), cfg
+    finally:
+        xtn.tune_set(R, default[0])
+        xtn.tune_set(P, default[1])
+
+
 # --------------------------------------------------------------- batched ---
 def test_batched_matches_oracle(xtn):
     seqs, off, rep = gen.batched(n_rep=12, seed=9, size_min=1, size_max=3000)
