@@ -287,12 +287,13 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
   uint64_t* status = ar.get<uint64_t>(radix_status_bytes(n_rec, cfg) / 8 + 1);
   XTN_ALLOC_OK(ar);
   XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
+  // expand counts the first pass's digits; each sort pass counts the next
   launch_expand(e.keys, e.lens, e.eqprev, e.rec_off, n, d, seq_rep, out->id_bits, A, n_rec, hist,
-                lo, 64, sms, err, s);
+                lo, std::min(64, lo + 8), sms, err, s);
   XTN_CK(cudaGetLastError());
   uint64_t* sorted = nullptr;
   XTN_CK(radix_sort_passes(A, B, (int64_t)n_rec, lo, 64, hist, digit_base, status, cfg, err,
-                           &sorted, "k_onesweep_records", s));
+                           &sorted, "k_onesweep_records", s, true));
   out->rec = sorted;
   out->spare = sorted == A ? B : A;
   return XTN_OK;

@@ -61,13 +61,13 @@ __global__ void k_digit_scan(const uint32_t* __restrict__ hist, uint64_t* __rest
   digit_base[p * RADIX + t] = off + inc - v;
 }
 
-template <int THREADS, int ITEMS, int MATCH = 0>
+template <int THREADS, int ITEMS, int MATCH = 0, int NCHAIN = 1>
 struct OnesweepSmem {
   static constexpr int WARPS = THREADS / 32;
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr size_t keys_bytes = (size_t)TILE * 8;
-  static constexpr size_t whist_bytes = (size_t)WARPS * RADIX * 4;
-  static constexpr size_t match_bytes = MATCH == 2 ? (size_t)WARPS * RADIX * 4 : 0;
+  static constexpr size_t whist_bytes = (size_t)NCHAIN * WARPS * RADIX * 4;
+  static constexpr size_t match_bytes = MATCH == 2 ? (size_t)NCHAIN * WARPS * RADIX * 4 : 0;
   static constexpr size_t bytes = keys_bytes + whist_bytes + RADIX * 4 + RADIX * 8 + match_bytes;
 };
 
@@ -133,33 +133,89 @@ __device__ __forceinline__ void rank_items(const uint64_t (&key)[ITEMS], uint16_
   }
 }
 
-template <int THREADS, int ITEMS, int MIN_BLOCKS, int MATCH>
+// Two ranking chains per warp: items [0, H) use counters whA / bins mbA and
+// items [H, ITEMS) use whB / mbB, one item of each per step, so the shared-
+// memory round trips of the two chains overlap.  The halves stay in item
+// order; the scatter offsets second-half ranks by the first half's counts.
+template <int ITEMS, int MATCH, bool FULL>
+__device__ __forceinline__ void rank_items2(const uint64_t (&key)[ITEMS], uint16_t (&rank)[ITEMS],
+                                            uint32_t* whA, uint32_t* whB, uint32_t* mbA,
+                                            uint32_t* mbB, int64_t wbase, int64_t n, int shift,
+                                            uint32_t dmask, uint32_t lane) {
+  constexpr int H = ITEMS / 2;
+  static_assert(ITEMS % 2 == 0, "two equal halves");
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const bool va = FULL || (wbase + k * 32 + lane < n);
+    const bool vb = FULL || (wbase + (H + k) * 32 + lane < n);
+    const uint32_t da = (uint32_t)(key[k] >> shift) & dmask;
+    const uint32_t db = (uint32_t)(key[H + k] >> shift) & dmask;
+    uint32_t pa, pb;
+    if (MATCH == 2) {
+      if (va) atomicOr(&mbA[da], 1u << lane);
+      if (vb) atomicOr(&mbB[db], 1u << lane);
+      __syncwarp();
+      pa = va ? mbA[da] : 0u;
+      pb = vb ? mbB[db] : 0u;
+      __syncwarp();
+    } else {
+      const uint32_t vma = FULL ? FULL_MASK : __ballot_sync(FULL_MASK, va);
+      const uint32_t vmb = FULL ? FULL_MASK : __ballot_sync(FULL_MASK, vb);
+      pa = digit_peers<0>(da, vma);
+      pb = digit_peers<0>(db, vmb);
+    }
+    const uint32_t ba = pa & lt_mask, bb = pb & lt_mask;
+    uint32_t oa = 0, ob = 0;
+    if (va && ba == 0) {
+      oa = whA[da];
+      whA[da] = oa + __popc(pa);
+      if (MATCH == 2) mbA[da] = 0u;
+    }
+    if (vb && bb == 0) {
+      ob = whB[db];
+      whB[db] = ob + __popc(pb);
+      if (MATCH == 2) mbB[db] = 0u;
+    }
+    oa = __shfl_sync(FULL_MASK, oa, va ? __ffs(pa) - 1 : (int)lane);
+    ob = __shfl_sync(FULL_MASK, ob, vb ? __ffs(pb) - 1 : (int)lane);
+    rank[k] = (uint16_t)(oa + __popc(ba));
+    rank[H + k] = (uint16_t)(ob + __popc(bb));
+    __syncwarp();
+  }
+}
+
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int MATCH, int NCHAIN = 1>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
                int bits, const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
-               uint32_t* __restrict__ ctr, uint32_t* __restrict__ err) {
-  using SM = OnesweepSmem<THREADS, ITEMS, MATCH>;
+               uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
+               uint32_t* __restrict__ next_hist, int next_bits) {
+  using SM = OnesweepSmem<THREADS, ITEMS, MATCH, NCHAIN>;
   constexpr int WARPS = SM::WARPS;
   constexpr int TILE = SM::TILE;
   static_assert(THREADS >= RADIX, "one thread per digit");
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
   uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
-  uint32_t* s_tstart = s_whist + WARPS * RADIX;
+  uint32_t* s_tstart = s_whist + NCHAIN * WARPS * RADIX;
   int64_t* s_obase = reinterpret_cast<int64_t*>(s_tstart + RADIX);
   uint32_t* s_match = reinterpret_cast<uint32_t*>(s_obase + RADIX);
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wsum[THREADS / 32];
+  __shared__ uint32_t s_next[RADIX];  // digit counts of the next pass (when next_hist)
 
+  if (next_hist)
+    for (int k = threadIdx.x; k < RADIX; k += THREADS) s_next[k] = 0;
   const uint32_t tile = tile_id(ctr, &s_tile);
   const int64_t tile_base = (int64_t)tile * TILE;
   const bool full = tile_base + TILE <= n;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t dmask = (1u << bits) - 1u;
 
-  for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) s_whist[k] = 0;
+  for (int k = threadIdx.x; k < NCHAIN * WARPS * RADIX; k += THREADS) s_whist[k] = 0;
   if (MATCH == 2)
-    for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) s_match[k] = 0;
+    for (int k = threadIdx.x; k < NCHAIN * WARPS * RADIX; k += THREADS) s_match[k] = 0;
 
   // 1. load: warp w reads its contiguous 32*ITEMS keys item-major
   uint64_t key[ITEMS];
@@ -177,11 +233,19 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   __syncthreads();
 
   // 2. stable warp multi-split ranking
+  // chain c of warp w keeps its counters at s_whist[(c * WARPS + w) * RADIX]
   uint32_t* wh = s_whist + warp * RADIX;
+  uint32_t* whB = s_whist + (WARPS + warp) * RADIX;
   uint32_t* mb = s_match + warp * RADIX;
+  uint32_t* mbB = s_match + (WARPS + warp) * RADIX;
   uint16_t rank[ITEMS];
-  if (full) rank_items<ITEMS, MATCH, true>(key, rank, wh, mb, wbase, n, shift, dmask, lane);
-  else rank_items<ITEMS, MATCH, false>(key, rank, wh, mb, wbase, n, shift, dmask, lane);
+  if (NCHAIN == 2) {
+    if (full) rank_items2<ITEMS, MATCH, true>(key, rank, wh, whB, mb, mbB, wbase, n, shift, dmask, lane);
+    else rank_items2<ITEMS, MATCH, false>(key, rank, wh, whB, mb, mbB, wbase, n, shift, dmask, lane);
+  } else {
+    if (full) rank_items<ITEMS, MATCH, true>(key, rank, wh, mb, wbase, n, shift, dmask, lane);
+    else rank_items<ITEMS, MATCH, false>(key, rank, wh, mb, wbase, n, shift, dmask, lane);
+  }
   __syncthreads();
 
   // 3. warp offsets per digit, tile counts, publish aggregates
@@ -193,6 +257,11 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
       const uint32_t c = s_whist[w * RADIX + threadIdx.x];
       s_whist[w * RADIX + threadIdx.x] = run;
       run += c;
+      if (NCHAIN == 2) {
+        const uint32_t c2 = s_whist[(WARPS + w) * RADIX + threadIdx.x];
+        s_whist[(WARPS + w) * RADIX + threadIdx.x] = run;
+        run += c2;
+      }
     }
     tcount = run;
     st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], (tile == 0 ? ST_INC : ST_AGG) | run);
@@ -216,12 +285,15 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     __syncthreads();
   }
 
-  // 4. scatter into shared memory in digit order
+  // 4. scatter into shared memory in digit order (and count the next digit)
+  const uint32_t nmask = (1u << next_bits) - 1u;
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     if (full || wbase + i * 32 + lane < n) {
       const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
-      s_keys[s_tstart[dig] + wh[dig] + rank[i]] = key[i];
+      if (next_hist) atomicAdd(&s_next[(uint32_t)(key[i] >> (shift + 8)) & nmask], 1u);
+      const uint32_t* whi = (NCHAIN == 2 && i >= ITEMS / 2) ? whB : wh;
+      s_keys[s_tstart[dig] + whi[dig] + rank[i]] = key[i];
     }
   }
 
@@ -236,6 +308,9 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
   __syncthreads();
 
+  if (next_hist && threadIdx.x < RADIX && s_next[threadIdx.x])
+    atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
+
   // 6. write out in digit order
   const int tile_n = full ? TILE : (int)(n - tile_base);
   for (int j = threadIdx.x; j < tile_n; j += THREADS) {
@@ -248,25 +323,29 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 }
 
 // Tile configurations (id, threads, items per thread, min blocks per SM,
-// ranking: 0 ballots / 1 match.any).  Both sorts use configuration 9 by
+// ranking: 0 ballots / 1 match.any / 2 atomic-OR bins, ranking chains).  Both sorts use configuration 9 by
 // default; the autotuner may pick others.
 #define XTN_ONESWEEP_CONFIGS(X) \
-  X(0, 256, 16, 3, 0)           \
-  X(1, 256, 24, 2, 0)           \
-  X(2, 512, 12, 2, 0)           \
-  X(3, 256, 8, 4, 0)            \
-  X(4, 256, 16, 3, 1)           \
-  X(5, 256, 20, 3, 0)           \
-  X(6, 384, 16, 2, 0)           \
-  X(7, 256, 12, 4, 0)           \
-  X(8, 256, 16, 3, 2)           \
-  X(9, 256, 20, 3, 2)           \
-  X(10, 512, 16, 1, 2)          \
-  X(11, 256, 24, 2, 2)
+  X(0, 256, 16, 3, 0, 1)           \
+  X(1, 256, 24, 2, 0, 1)           \
+  X(2, 512, 12, 2, 0, 1)           \
+  X(3, 256, 8, 4, 0, 1)            \
+  X(4, 256, 16, 3, 1, 1)           \
+  X(5, 256, 20, 3, 0, 1)           \
+  X(6, 384, 16, 2, 0, 1)           \
+  X(7, 256, 12, 4, 0, 1)           \
+  X(8, 256, 16, 3, 2, 1)           \
+  X(9, 256, 20, 3, 2, 1)           \
+  X(10, 512, 16, 1, 2, 1)          \
+  X(11, 256, 24, 2, 2, 1)          \
+  X(12, 256, 20, 3, 2, 2)       \
+  X(13, 256, 16, 3, 2, 2)       \
+  X(14, 256, 20, 3, 0, 2)       \
+  X(15, 256, 12, 4, 0, 2)
 
 int onesweep_tile(int cfg) {
   switch (cfg) {
-#define X(id, T, I, B, M) \
+#define X(id, T, I, B, M, C) \
   case id: return T * I;
     XTN_ONESWEEP_CONFIGS(X)
 #undef X
@@ -274,25 +353,27 @@ int onesweep_tile(int cfg) {
   return 0;
 }
 
-int onesweep_configs() { return 12; }
+int onesweep_configs() { return 16; }
 
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    int shift, int bits, const uint64_t* digit_base,
-                                   uint64_t* status, uint32_t* ctr, uint32_t* err, cudaStream_t s) {
+                                   uint64_t* status, uint32_t* ctr, uint32_t* err,
+                                   uint32_t* next_hist, int next_bits, cudaStream_t s) {
   switch (cfg) {
-#define X(id, T, I, B, M)                                                                     \
+#define X(id, T, I, B, M, C)                                                                  \
   case id: {                                                                                  \
-    using SM = OnesweepSmem<T, I, M>;                                                         \
+    using SM = OnesweepSmem<T, I, M, C>;                                                      \
     static std::once_flag once;                                                               \
     std::call_once(once, [] {                                                                 \
-      cudaFuncSetAttribute(k_onesweep<T, I, B, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+      cudaFuncSetAttribute(k_onesweep<T, I, B, M, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                            (int)SM::bytes);                                                   \
-      cudaFuncSetAttribute(k_onesweep<T, I, B, M>,                                            \
+      cudaFuncSetAttribute(k_onesweep<T, I, B, M, C>,                                            \
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
     });                                                                                       \
     const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
-    k_onesweep<T, I, B, M><<<tiles, T, SM::bytes, s>>>(in, out, n, shift, bits, digit_base,   \
-                                                       status, ctr, err);                     \
+    k_onesweep<T, I, B, M, C><<<tiles, T, SM::bytes, s>>>(in, out, n, shift, bits, digit_base,   \
+                                                       status, ctr, err, next_hist,           \
+                                                       next_bits);                            \
     return cudaGetLastError();                                                                \
   }
     XTN_ONESWEEP_CONFIGS(X)
@@ -315,14 +396,17 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
   prof_end(s);
 }
 
-cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi,
-                              const uint32_t* hist, uint64_t* digit_base, uint64_t* status,
-                              int cfg, uint32_t* err, uint64_t** sorted, const char* tag,
-                              cudaStream_t s) {
+cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
+                              uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
+                              uint64_t** sorted, const char* tag, cudaStream_t s,
+                              bool hist_in_passes) {
   const int passes = (hi - lo + 7) / 8;
   *sorted = a;
   if (n <= 1 || passes == 0) return cudaSuccess;
-  k_digit_scan<<<passes, RADIX, 0, s>>>(hist, digit_base);
+  // hist_in_passes: `hist` holds pass 0's counts on entry, pass p counts the
+  // digits of pass p+1 into hist[(p+1) * RADIX], and each pass's offsets are
+  // scanned just before it runs.
+  if (!hist_in_passes) k_digit_scan<<<passes, RADIX, 0, s>>>(hist, digit_base);
   const size_t st_bytes = radix_status_bytes(n, cfg);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st_bytes - 16);
   uint64_t* src = a;
@@ -330,10 +414,15 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
   for (int p = 0; p < passes; ++p) {
     const int sh = lo + 8 * p;
     const int bits = std::min(8, hi - sh);
+    if (hist_in_passes)
+      k_digit_scan<<<1, RADIX, 0, s>>>(hist + p * RADIX, digit_base + p * RADIX);
+    uint32_t* next = (hist_in_passes && p + 1 < passes) ? hist + (p + 1) * RADIX : nullptr;
+    const int next_bits = next ? std::min(8, hi - (sh + 8)) : 0;
     cudaError_t e = cudaMemsetAsync(status, 0, st_bytes, s);
     if (e != cudaSuccess) return e;
     prof_begin(s, tag, (double)n * 16.0);
-    e = onesweep_launch(cfg, src, dst, n, sh, bits, digit_base + p * RADIX, status, ctr, err, s);
+    e = onesweep_launch(cfg, src, dst, n, sh, bits, digit_base + p * RADIX, status, ctr, err, next,
+                        next_bits, s);
     prof_end(s);
     if (e != cudaSuccess) return e;
     std::swap(src, dst);

@@ -29,41 +29,66 @@ __constant__ uint8_t c_letter_code[26] = {
     1,  0,  2,  3,  4,  5,  6,  7,  8, 0, 9,  10, 11,   // A B C D E F G H I J K L M
     12, 0, 13, 14, 15, 16, 17, 0, 18, 19, 0, 20, 0};     // N O P Q R S T U V W X Y Z
 
-__global__ void k_encode(const uint8_t* __restrict__ seqs, const int64_t* __restrict__ off,
-                         int64_t n, int d, Key128* __restrict__ keys, uint8_t* __restrict__ lens,
-                         uint32_t* __restrict__ eqprev_out, uint32_t* __restrict__ vcount,
-                         uint32_t* __restrict__ err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t a = off[i], b = off[i + 1], total = off[n];
-  Key128 k{0ull, 0ull};
-  uint32_t L = 0, eqprev = 0;
-  if (a < 0 || b < a || b > total) {
-    atomicOr(err, DERR_RANGE);
-  } else if (b - a > XTN_MAX_LEN) {
+constexpr int ENCODE_WARPS = 8;
+
+// One warp per 32 consecutive sequences: their letters form one contiguous
+// byte span, copied to shared memory with coalesced loads; each lane then
+// encodes its own sequence.  Offsets are validated per lane first; a warp
+// with an invalid offset reads each valid lane's letters directly instead.
+__global__ void __launch_bounds__(ENCODE_WARPS * 32)
+    k_encode(const uint8_t* __restrict__ seqs, const int64_t* __restrict__ off, int64_t n, int d,
+             Key128* __restrict__ keys, uint8_t* __restrict__ lens,
+             uint32_t* __restrict__ eqprev_out, uint32_t* __restrict__ vcount,
+             uint32_t* __restrict__ err) {
+  __shared__ uint8_t s_bytes[ENCODE_WARPS][32 * XTN_MAX_LEN];
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const int64_t s0 = ((int64_t)blockIdx.x * ENCODE_WARPS + warp) * 32;
+  if (s0 >= n) return;  // whole warp
+  const int64_t i = s0 + lane;
+  const bool in = i < n;
+  const int64_t total = off[n];
+  const int64_t a = in ? off[i] : 0, b = in ? off[i + 1] : 0;
+  bool ok = in && a >= 0 && b >= a && b <= total;
+  if (in && !ok) atomicOr(err, DERR_RANGE);
+  if (ok && b - a > XTN_MAX_LEN) {
     atomicOr(err, DERR_TOO_LONG);
-  } else {
+    ok = false;
+  }
+  const bool all_ok = __all_sync(FULL_MASK, ok || !in);
+  const int last = (int)((n - s0 < 32) ? (n - s0 - 1) : 31);
+  const int64_t A = __shfl_sync(FULL_MASK, a, 0), Bend = __shfl_sync(FULL_MASK, b, last);
+  uint8_t* buf = s_bytes[warp];
+  const bool shared_span = all_ok && Bend - A <= 32 * XTN_MAX_LEN;
+  if (shared_span) {
+    for (int64_t k = lane; k < Bend - A; k += 32) buf[k] = seqs[A + k];
+  }
+  __syncwarp();
+  Key128 key{0ull, 0ull};
+  uint32_t L = 0, eqprev = 0;
+  if (ok) {
     L = (uint32_t)(b - a);
     uint32_t prev = 0;
     for (uint32_t p = 0; p < L; ++p) {
-      const uint32_t ch = seqs[a + p];
+      const uint32_t ch = shared_span ? buf[a - A + p] : seqs[a + p];
       const uint32_t c = (ch >= 'A' && ch <= 'Z') ? c_letter_code[ch - 'A'] : 0u;
       if (c == 0) atomicOr(err, DERR_BAD_RESIDUE);
       if (p > 0 && c == prev) eqprev |= 1u << p;
       prev = c;
       const uint32_t m = 5 * p;
       if (m < 64) {
-        k.lo |= (uint64_t)c << m;
-        if (m > 59) k.hi |= (uint64_t)c >> (64 - m);
+        key.lo |= (uint64_t)c << m;
+        if (m > 59) key.hi |= (uint64_t)c >> (64 - m);
       } else {
-        k.hi |= (uint64_t)c << (m - 64);
+        key.hi |= (uint64_t)c << (m - 64);
       }
     }
   }
-  keys[i] = k;
-  lens[i] = (uint8_t)L;
-  eqprev_out[i] = eqprev;
-  vcount[i] = canonical_count(eqprev, L, (uint32_t)d);
+  if (in) {
+    keys[i] = key;
+    lens[i] = (uint8_t)L;
+    eqprev_out[i] = eqprev;
+    vcount[i] = canonical_count(eqprev, L, (uint32_t)d);
+  }
 }
 
 constexpr int EXPAND_THREADS = 256;
@@ -227,7 +252,9 @@ void launch_encode(const uint8_t* seqs, const int64_t* off, int64_t n, int d, Ke
                    cudaStream_t s) {
   if (n <= 0) return;
   prof_begin(s, "k_encode", (double)n * (16 + 16 + 1 + 4 + 4 + 8));
-  k_encode<<<div_up_u32(n, 256), 256, 0, s>>>(seqs, off, n, d, keys, lens, eqprev, vcount, err);
+  k_encode<<<div_up_u32(n, ENCODE_WARPS * 32), ENCODE_WARPS * 32, 0, s>>>(seqs, off, n, d, keys,
+                                                                           lens, eqprev, vcount,
+                                                                           err);
   prof_end(s);
 }
 

@@ -36,29 +36,40 @@ constexpr int VER_ITEMS = 8;
 constexpr int VER_TILE = VER_THREADS * VER_ITEMS;
 
 // Levenshtein distance between pattern (match vectors peq, length m) and the
-// text held in packed key t (length n).
+// text held in packed key t (length n <= XTN_MAX_LEN).  All match vectors the
+// text needs are loaded first (independent loads, one latency), then the
+// bit-vector recurrence runs from registers, unrolled over XTN_MAX_LEN steps
+// with the steps past n switched off.
 __device__ __forceinline__ uint32_t edit_distance(const uint32_t* __restrict__ peq, uint32_t m,
                                                   Key128 t, uint32_t n) {
+  uint32_t eqv[XTN_MAX_LEN];
+#pragma unroll
+  for (int j = 0; j < XTN_MAX_LEN; ++j) {
+    const uint32_t c = (uint32_t)(t.lo & 31u);
+    t.lo = (t.lo >> 5) | (t.hi << 59);
+    t.hi >>= 5;
+    eqv[j] = ((uint32_t)j < n && c - 1u < 20u) ? __ldg(peq + (c - 1u)) : 0u;
+  }
   if (m == 0) return n;
   uint32_t pv = (m >= 32) ? ~0u : ((1u << m) - 1u);
   uint32_t mv = 0;
   uint32_t score = m;
   const uint32_t hb = 1u << (m - 1);
-  for (uint32_t j = 0; j < n; ++j) {
-    const uint32_t c = (uint32_t)(t.lo & 31u);
-    t.lo = (t.lo >> 5) | (t.hi << 59);
-    t.hi >>= 5;
-    const uint32_t eq = (c - 1u < 20u) ? __ldg(peq + (c - 1u)) : 0u;
-    const uint32_t xv = eq | mv;
-    const uint32_t xh = (((eq & pv) + pv) ^ pv) | eq;
-    uint32_t ph = mv | ~(xh | pv);
-    uint32_t mh = pv & xh;
-    score += (ph & hb) ? 1u : 0u;
-    score -= (mh & hb) ? 1u : 0u;
-    ph = (ph << 1) | 1u;
-    mh <<= 1;
-    pv = mh | ~(xv | ph);
-    mv = ph & xv;
+#pragma unroll
+  for (int j = 0; j < XTN_MAX_LEN; ++j) {
+    if ((uint32_t)j < n) {
+      const uint32_t eq = eqv[j];
+      const uint32_t xv = eq | mv;
+      const uint32_t xh = (((eq & pv) + pv) ^ pv) | eq;
+      uint32_t ph = mv | ~(xh | pv);
+      uint32_t mh = pv & xh;
+      score += (ph & hb) ? 1u : 0u;
+      score -= (mh & hb) ? 1u : 0u;
+      ph = (ph << 1) | 1u;
+      mh <<= 1;
+      pv = mh | ~(xv | ph);
+      mv = ph & xv;
+    }
   }
   return score;
 }

@@ -42,10 +42,12 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
                       cudaStream_t s);
 // Sorts a[0:n) on bits [lo, hi) using b as the second buffer; `hist` holds the
 // digit histograms of every pass.  *sorted receives a or b.
-cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi,
-                              const uint32_t* hist, uint64_t* digit_base, uint64_t* status,
-                              int cfg, uint32_t* err, uint64_t** sorted, const char* tag,
-                              cudaStream_t s);
+// hist_in_passes: `hist` holds only pass 0's digit counts; every pass counts
+// the next pass's digits itself (zeroed hist rows 1.. expected).
+cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
+                              uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
+                              uint64_t** sorted, const char* tag, cudaStream_t s,
+                              bool hist_in_passes = false);
 
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
