@@ -42,6 +42,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define XTN_API __attribute__((visibility("default")))
+#else
+#define XTN_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -78,10 +84,10 @@ enum {
 };
 
 /* Human-readable name of a status code (static string, never NULL). */
-const char* xtn_status_string(int status);
+XTN_API const char* xtn_status_string(int status);
 
 /* Library version as 10000*major + 100*minor + patch. */
-int xtn_version(void);
+XTN_API int xtn_version(void);
 
 /*
  * All-pairs self-search (Appendix A, XTNeighbor steps 0-7).
@@ -101,7 +107,7 @@ int xtn_version(void);
  * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, BUFFER_TOO_SMALL,
  * CUDA, DEVICE_TIMEOUT, TOO_LARGE.
  */
-int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+XTN_API int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                     const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
                     int64_t* n_out, xtn_stream_t stream);
 
@@ -115,14 +121,14 @@ int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int 
  * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, CUDA, DEVICE_TIMEOUT,
  * TOO_LARGE.
  */
-int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+XTN_API int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                     xtn_stream_t stream, xtn_index** out);
 
 /* Release an index (NULL is accepted). */
-int xtn_index_free(xtn_index* idx);
+XTN_API int xtn_index_free(xtn_index* idx);
 
 /* Host-side facts about an index; any output pointer may be NULL. */
-int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
+XTN_API int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
                    int64_t* device_bytes);
 
 /*
@@ -134,7 +140,7 @@ int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
  * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, BUFFER_TOO_SMALL,
  * CUDA, DEVICE_TIMEOUT, TOO_LARGE.
  */
-int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
+XTN_API int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out,
                      xtn_stream_t stream);
 
@@ -151,9 +157,35 @@ int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t*
  *   in, n_in         : input rows (i, j < n).
  * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, CUDA.
  */
-int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
+XTN_API int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
                        const xtn_triple* in, int64_t n_in, int max_score, xtn_triple* out,
                        int64_t* n_out, xtn_stream_t stream);
+
+/*
+ * xtn_tcrdist_filter_noalloc: xtn_tcrdist_filter for callers that cannot
+ * allocate device memory -- processes held to a fixed memory budget or run
+ * under an allocator they do not control, and code that records its work
+ * while allocation is not permitted.  The paper has no counterpart to this
+ * entry point; it computes exactly what xtn_tcrdist_filter computes.
+ *   - It allocates nothing: its scratch (encoded sequences, look-back status,
+ *     counters) lives in one fixed array of about 6.3 MiB of device memory
+ *     that every GPU loading the library holds until the process exits.
+ *   - Limits: n <= XTN_NOALLOC_MAX_SEQS sequences and n_in <=
+ *     XTN_NOALLOC_MAX_ROWS rows; larger inputs return XTN_ERR_TOO_LARGE.
+ *   - seqs, offsets, in and out must be device pointers of the current device
+ *     (a host buffer would need a device copy); otherwise XTN_ERR_INVALID_ARG.
+ *     n_out is a host pointer; the call waits for its stream.
+ *   - The first call on a device looks the array's device address up (once
+ *     per device); make that first call before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the caller.
+ * Errors: as xtn_tcrdist_filter, plus TOO_LARGE.
+ */
+#define XTN_NOALLOC_MAX_SEQS (1 << 18)
+#define XTN_NOALLOC_MAX_ROWS (1 << 22)
+XTN_API int xtn_tcrdist_filter_noalloc(const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                               const xtn_triple* in, int64_t n_in, int max_score, xtn_triple* out,
+                               int64_t* n_out, xtn_stream_t stream);
 
 /*
  * Tuning knobs (process-wide, take effect for calls that start afterwards).
@@ -166,9 +198,9 @@ int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
  * xtn_tune_set returns XTN_ERR_INVALID_ARG for an unknown knob or value.
  */
 enum { XTN_TUNE_SORT_RECORDS = 0, XTN_TUNE_SORT_PAIRS = 1 };
-int xtn_tune_set(int knob, int value);
-int xtn_tune_get(int knob);
-int xtn_tune_count(int knob);
+XTN_API int xtn_tune_set(int knob, int value);
+XTN_API int xtn_tune_get(int knob);
+XTN_API int xtn_tune_count(int knob);
 
 /*
  * Kernel timing.  While enabled, every kernel the library launches is
@@ -178,8 +210,8 @@ int xtn_tune_count(int knob);
  * into buf (NUL-terminated, truncated to buf_len); it returns the number of
  * lines, and clears the records.  Enabling costs two event records per launch.
  */
-int xtn_profile_enable(int on);
-int xtn_profile_report(char* buf, int64_t buf_len);
+XTN_API int xtn_profile_enable(int on);
+XTN_API int xtn_profile_report(char* buf, int64_t buf_len);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libxtn.so")
-SOURCES = ["api.cu", "k_variants.cu", "k_radix.cu", "k_pairs.cu", "k_verify.cu", "k_query.cu"]
+SOURCES = ["api.cu", "k_variants.cu", "k_radix.cu", "k_pairs.cu", "k_verify.cu", "k_query.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +30,7 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3",
+    return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3,-fvisibility=hidden",
             "-I", INCLUDE, "-I", CSRC, *extra]
 
 

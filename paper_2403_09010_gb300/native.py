@@ -24,6 +24,8 @@ XTN_ERR_DEVICE_TIMEOUT = -7
 XTN_ERR_TOO_LARGE = -8
 XTN_TUNE_SORT_RECORDS = 0
 XTN_TUNE_SORT_PAIRS = 1
+XTN_NOALLOC_MAX_SEQS = 1 << 18
+XTN_NOALLOC_MAX_ROWS = 1 << 22
 XTN_MAX_LEN = 25
 XTN_MAX_D = 3
 
@@ -40,6 +42,7 @@ SIGNATURES = {
     "xtn_index_info": (_I, [_P, _P, _P, _P, _P]),
     "xtn_search_query": (_I, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
     "xtn_tcrdist_filter": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
+    "xtn_tcrdist_filter_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
     "xtn_tune_set": (_I, [_I, _I]),
     "xtn_tune_get": (_I, [_I]),
     "xtn_tune_count": (_I, [_I]),
