@@ -80,7 +80,8 @@ enum {
   XTN_ERR_BUFFER_TOO_SMALL = -5, /* *n_out > cap; first cap rows written */
   XTN_ERR_CUDA = -6,             /* a CUDA runtime call failed */
   XTN_ERR_DEVICE_TIMEOUT = -7,   /* a bounded device-side wait gave up */
-  XTN_ERR_TOO_LARGE = -8         /* more than 2^32-1 variant records or pairs */
+  XTN_ERR_TOO_LARGE = -8,        /* more than 2^32-1 variant records or pairs */
+  XTN_ERR_CAPACITY = -9          /* a plan's candidate-pair capacity was exceeded */
 };
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -160,6 +161,40 @@ XTN_API int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const 
 XTN_API int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
                        const xtn_triple* in, int64_t n_in, int max_score, xtn_triple* out,
                        int64_t* n_out, xtn_stream_t stream);
+
+/*
+ * Planned self-search: all device memory is allocated once, so that running
+ * the search issues only kernels and memsets on one stream, with no host
+ * synchronisation -- the sequence a CUDA graph can capture and replay.  This
+ * is the batched mode of the library: any number of repertoires of uneven
+ * size (rep_offsets as in xtn_search_self) go through one launch of each
+ * kernel (Appendix A, XTNeighbor steps 0-7, over all repertoires at once).
+ *
+ * xtn_plan_create: plan for inputs with exactly these offsets (host or
+ *   device, n+1 entries) and repertoire offsets (NULL for one repertoire).
+ *   Record buffers are sized for every deletion subset of every sequence, an
+ *   upper bound whatever the letters.  pair_capacity bounds the candidate
+ *   pairs of one run (<= 0: one eighth of the record bound, at least 65,536).
+ * xtn_plan_run: search the n sequences at `seqs` (a device pointer; letters
+ *   laid out as the plan's offsets say) on `stream`; returns once the work is
+ *   queued.  Runs on one plan must not overlap.
+ * xtn_plan_result: wait for the stream and copy the rows of the last run to
+ *   out (host or device, capacity cap); *n_out = number of rows.  If the run
+ *   produced more candidate pairs than the plan holds, returns
+ *   XTN_ERR_CAPACITY with *n_out = the capacity needed; create a plan with at
+ *   least that pair_capacity.
+ * Errors: INVALID_ARG, SEQ_TOO_LONG, OOM, CUDA, TOO_LARGE at creation;
+ *   BAD_RESIDUE, DEVICE_TIMEOUT, CAPACITY, BUFFER_TOO_SMALL at result.
+ */
+typedef struct xtn_plan xtn_plan;
+XTN_API int xtn_plan_create(const int64_t* offsets, int64_t n, int d, const int64_t* rep_offsets,
+                    int64_t n_rep, int64_t pair_capacity, xtn_plan** out);
+XTN_API int xtn_plan_run(xtn_plan* plan, const uint8_t* seqs, xtn_stream_t stream);
+XTN_API int xtn_plan_result(xtn_plan* plan, xtn_triple* out, int64_t cap, int64_t* n_out,
+                    xtn_stream_t stream);
+XTN_API int xtn_plan_info(const xtn_plan* plan, int64_t* record_capacity, int64_t* pair_capacity,
+                  int64_t* device_bytes);
+XTN_API int xtn_plan_free(xtn_plan* plan);
 
 /*
  * xtn_tcrdist_filter_noalloc: xtn_tcrdist_filter for callers that cannot

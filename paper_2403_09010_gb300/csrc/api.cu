@@ -132,6 +132,7 @@ int map_device_err(uint32_t e) {
   if (e & DERR_TIMEOUT) return XTN_ERR_DEVICE_TIMEOUT;
   if (e & DERR_BAD_RESIDUE) return XTN_ERR_BAD_RESIDUE;
   if (e & DERR_TOO_LONG) return XTN_ERR_SEQ_TOO_LONG;
+  if (e & DERR_CAPACITY) return XTN_ERR_CAPACITY;
   if (e & DERR_RANGE) return XTN_ERR_INVALID_ARG;
   return XTN_OK;
 }
@@ -299,50 +300,40 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
   return XTN_OK;
 }
 
-// Verify candidate pair words (P1), sort the survivors, drop duplicates and
-// write result rows.  P1 is reused as the sort's second buffer.
-int verify_sort_finalize(uint64_t* P1, uint64_t n_cand, uint32_t pair_bits, uint32_t j_bits,
-                         const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
-                         const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
-                         const uint32_t* seq_rep, int self_mode, int d, xtn_triple* out,
-                         int64_t cap, int sms, Arena& ar, uint32_t* err, cudaStream_t s,
-                         uint64_t* n_rows) {
-  *n_rows = 0;
-  const int cfg = g_cfg_pairs.load();
-  uint64_t* P2 = ar.get<uint64_t>(n_cand + 8);
-  uint32_t* hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
-  uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
-  uint64_t* counters = ar.get<uint64_t>(2);
-  XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
-  XTN_CK(cudaMemsetAsync(counters, 0, 16, s));
-  launch_verify_candidates(P1, n_cand, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep,
-                           self_mode, d, P2, n_cand, counters, hist, (int)pair_bits, sms, err, s);
-  XTN_CK(cudaGetLastError());
-  struct {
-    uint64_t n;
-    uint32_t err;
-  } h{0, 0};
-  XTN_CK(cudaMemcpyAsync(&h.n, counters, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
-  if (h.err) return map_device_err(h.err);
-  const uint64_t n_surv = h.n;
-  if (n_surv == 0) return XTN_OK;
-  const size_t st = std::max(radix_status_bytes(n_surv, cfg), verify_status_bytes(n_surv));
-  uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
-  XTN_ALLOC_OK(ar);
+// Back stage, asynchronous: verify candidate words P1 (count cand_cap, or
+// the device count *n_cand_dev when given), append survivors to P2, sort
+// them (P1 reused as the second buffer), drop duplicates and write rows.
+// counters[0] receives the survivor count, counters[1] the row count.
+struct BackStage {
+  uint64_t* P1 = nullptr;
+  uint64_t* P2 = nullptr;
+  uint32_t* hist = nullptr;        // MAX_PASSES * RADIX
+  uint64_t* digit_base = nullptr;  // MAX_PASSES * RADIX
+  uint64_t* status = nullptr;      // back_status_bytes(cand_cap)
+  uint64_t* counters = nullptr;    // 2
+};
+
+size_t back_status_bytes(uint64_t cand_cap, int cfg) {
+  return std::max(radix_status_bytes((int64_t)cand_cap, cfg),
+                  verify_status_bytes((int64_t)cand_cap));
+}
+
+int launch_back(const BackStage& b, uint64_t cand_cap, const uint64_t* n_cand_dev,
+                uint32_t pair_bits, uint32_t j_bits, const uint32_t* peq_i, const uint8_t* lens_i,
+                uint64_t n_i, const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                const uint32_t* seq_rep, int self_mode, int d, xtn_triple* rows, int64_t row_cap,
+                int sms, uint32_t* err, cudaStream_t s, int cfg) {
+  XTN_CK(cudaMemsetAsync(b.hist, 0, MAX_PASSES * RADIX * 4, s));
+  XTN_CK(cudaMemsetAsync(b.counters, 0, 16, s));
+  launch_verify_candidates(b.P1, cand_cap, n_cand_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
+                           n_j, seq_rep, self_mode, d, b.P2, cand_cap, b.counters, b.hist,
+                           (int)pair_bits, sms, err, s);
   uint64_t* sorted = nullptr;
-  XTN_CK(radix_sort_passes(P2, P1, (int64_t)n_surv, 0, (int)pair_bits, hist, digit_base, status,
-                           cfg, err, &sorted, "k_onesweep_pairs", s));
-  launch_unique_finalize(sorted, (int64_t)n_surv, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j,
-                         out, cap, status, err, counters + 1, s);
+  XTN_CK(radix_sort_passes(b.P2, b.P1, (int64_t)cand_cap, 0, (int)pair_bits, b.hist, b.digit_base,
+                           b.status, cfg, err, &sorted, "k_onesweep_pairs", s, false, b.counters));
+  launch_unique_finalize(sorted, (int64_t)cand_cap, b.counters, j_bits, peq_i, lens_i, n_i, keys_j,
+                         lens_j, n_j, rows, row_cap, b.status, err, b.counters + 1, s);
   XTN_CK(cudaGetLastError());
-  XTN_CK(cudaMemcpyAsync(&h.n, counters + 1, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
-  if (h.err) return map_device_err(h.err);
-  *n_rows = h.n;
   return XTN_OK;
 }
 
@@ -384,6 +375,32 @@ int finish_out(const OutRows& o, xtn_triple* out, int64_t cap, uint64_t n_rows, 
   return (int64_t)n_rows > cap ? XTN_ERR_BUFFER_TOO_SMALL : XTN_OK;
 }
 
+// Repertoire of every sequence (batched mode), checked on the host.
+int stage_reps(const int64_t* rep_offsets, int64_t n_rep, int64_t n, Arena* ar, cudaStream_t s,
+               uint32_t* seq_rep) {
+  std::vector<int64_t> h(n_rep + 1);
+  if (is_device_ptr(rep_offsets)) {
+    int rc = read_back(h.data(), rep_offsets, n_rep + 1, s);
+    if (rc) return rc;
+  } else {
+    std::memcpy(h.data(), rep_offsets, (n_rep + 1) * sizeof(int64_t));
+  }
+  if (h[0] != 0 || h[n_rep] != n) return XTN_ERR_INVALID_ARG;
+  for (int64_t r = 0; r < n_rep; ++r)
+    if (h[r + 1] < h[r]) return XTN_ERR_INVALID_ARG;
+  int64_t* d_rep = ar->get<int64_t>(n_rep + 1);
+  XTN_ALLOC_OK(*ar);
+  XTN_CK(cudaMemcpyAsync(d_rep, h.data(), (n_rep + 1) * 8, cudaMemcpyHostToDevice, s));
+  launch_seq_rep(d_rep, n_rep, seq_rep, n, s);
+  return XTN_OK;
+}
+
+// pair_count[0] = pair_off[n_groups] once n_groups is known on the device.
+__global__ void k_pair_total(const uint64_t* __restrict__ pair_off,
+                             const uint64_t* __restrict__ n_groups, uint64_t* __restrict__ out) {
+  *out = pair_off[*n_groups];
+}
+
 int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                      const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
                      int64_t* n_out, cudaStream_t s) {
@@ -398,85 +415,78 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (rc) return rc;
   Arena ar(s);
   uint32_t* err = ar.get<uint32_t>(4);
+  uint64_t* counters = ar.get<uint64_t>(4);
   XTN_ALLOC_OK(ar);
   XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(cudaMemsetAsync(counters, 0, 32, s));
   DevSeqs in;
   rc = stage_seqs(seqs, offsets, n, ar, s, &in);
   if (rc) return rc;
-
-  // batched mode: repertoire of every sequence
   uint32_t* seq_rep = nullptr;
   if (rep_offsets) {
-    std::vector<int64_t> h(n_rep + 1);
-    if (is_device_ptr(rep_offsets)) {
-      rc = read_back(h.data(), rep_offsets, n_rep + 1, s);
-      if (rc) return rc;
-    } else {
-      std::memcpy(h.data(), rep_offsets, (n_rep + 1) * sizeof(int64_t));
-    }
-    if (h[0] != 0 || h[n_rep] != n) return XTN_ERR_INVALID_ARG;
-    for (int64_t r = 0; r < n_rep; ++r)
-      if (h[r + 1] < h[r]) return XTN_ERR_INVALID_ARG;
-    int64_t* d_rep = ar.get<int64_t>(n_rep + 1);
     seq_rep = ar.get<uint32_t>(n);
     XTN_ALLOC_OK(ar);
-    XTN_CK(cudaMemcpyAsync(d_rep, h.data(), (n_rep + 1) * 8, cudaMemcpyHostToDevice, s));
-    launch_seq_rep(d_rep, n_rep, seq_rep, n, s);
+    rc = stage_reps(rep_offsets, n_rep, n, &ar, s, seq_rep);
+    if (rc) return rc;
   }
 
+  // front: encode (read back the record count), expand, sort, group, offsets
   Encoded e;
   rc = encode_and_count(in, d, ar, err, s, &e);
   if (rc) return rc;
   Sorted so;
   rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so);
   if (rc) return rc;
-
-  // groups of equal fingerprints with >= 2 records, inside the spare buffer
   const uint64_t g_cap = e.n_rec / 2 + 1;
-  uint32_t* S = reinterpret_cast<uint32_t*>(so.spare);
+  uint32_t* S = reinterpret_cast<uint32_t*>(so.spare);  // groups live in the spare buffer
   uint32_t* E = S + g_cap;
   uint64_t* pair_off = reinterpret_cast<uint64_t*>(E + g_cap);  // 8-byte aligned
   const size_t st = std::max(group_status_bytes(e.n_rec), scan_status_bytes(g_cap));
   uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
-  uint64_t* counters = ar.get<uint64_t>(2);
   uint64_t* flags = ar.get<uint64_t>(group_flag_words((int64_t)e.n_rec));
   XTN_ALLOC_OK(ar);
-  launch_group_bounds(so.rec, (int64_t)e.n_rec, 64 - so.hs, S, E, g_cap, flags, status, err,
-                      counters, s);
+  launch_group_bounds(so.rec, (int64_t)e.n_rec, nullptr, 64 - so.hs, S, E, g_cap, flags, status,
+                      err, counters, s);
+  launch_scan_group_pairs(S, E, (int64_t)g_cap, counters, pair_off, status, err, s);
+  k_pair_total<<<1, 1, 0, s>>>(pair_off, counters, counters + 1);
   XTN_CK(cudaGetLastError());
-  uint64_t n_groups = 0;
-  rc = read_back(&n_groups, counters, 1, s);
-  if (rc) return rc;
-  uint64_t n_pairs = 0;
-  if (n_groups > 0) {
-    launch_scan_group_pairs(S, E, (int64_t)n_groups, pair_off, status, err, s);
-    XTN_CK(cudaGetLastError());
-    rc = read_back(&n_pairs, pair_off + n_groups, 1, s);
-    if (rc) return rc;
-  }
-  uint32_t herr = 0;
-  rc = read_back(&herr, err, 1, s);
-  if (rc) return rc;
-  if (herr) return map_device_err(herr);
+  struct {
+    uint64_t groups, pairs;
+    uint32_t err;
+  } h{0, 0, 0};
+  XTN_CK(cudaMemcpyAsync(&h.groups, counters, 16, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err) return map_device_err(h.err);
+  const uint64_t n_pairs = h.pairs;
   if (n_pairs == 0) return XTN_OK;
   if (n_pairs >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
 
-  // candidate pairs, then verify, sort, dedup
-  uint64_t* P1 = ar.get<uint64_t>(n_pairs + 8);
+  // back: emit candidates, verify, sort survivors, dedup
+  BackStage b;
+  b.P1 = ar.get<uint64_t>(n_pairs + 8);
+  b.P2 = ar.get<uint64_t>(n_pairs + 8);
+  b.hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  b.digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
+  const int cfg_pairs = g_cfg_pairs.load();
+  b.status = ar.get<uint64_t>(back_status_bytes(n_pairs, cfg_pairs) / 8 + 1);
+  b.counters = ar.get<uint64_t>(2);
   uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
   XTN_ALLOC_OK(ar);
-  launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)n_groups, n_pairs, so.id_bits, P1, sms,
-                    err, s);
+  launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)h.groups, nullptr, n_pairs, so.id_bits,
+                    b.P1, nullptr, sms, err, s);
   launch_peq(e.keys, e.lens, n, peq, s);
-  XTN_CK(cudaGetLastError());
   OutRows o;
   rc = prepare_out(out, cap, n_pairs, ar, &o);
   if (rc) return rc;
-  uint64_t n_rows = 0;
-  rc = verify_sort_finalize(P1, n_pairs, 2 * so.id_bits, so.id_bits, peq, e.lens, n, e.keys,
-                            e.lens, n, seq_rep, 1, d, o.dev, o.dev_cap, sms, ar, err, s, &n_rows);
+  rc = launch_back(b, n_pairs, nullptr, 2 * so.id_bits, so.id_bits, peq, e.lens, n, e.keys, e.lens,
+                   n, seq_rep, 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs);
   if (rc) return rc;
-  return finish_out(o, out, cap, n_rows, s, n_out);
+  XTN_CK(cudaMemcpyAsync(&h.pairs, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err) return map_device_err(h.err);
+  return finish_out(o, out, cap, h.pairs, s, n_out);
 }
 
 }  // namespace
@@ -607,21 +617,36 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
   const uint32_t q_bits = bits_for((uint64_t)n_q);
   const uint32_t pair_bits = q_bits + idx->id_bits;
   if (pair_bits > 64) return XTN_ERR_TOO_LARGE;
-  uint64_t* P1 = ar.get<uint64_t>(n_cand + 8);
+  BackStage b;
+  b.P1 = ar.get<uint64_t>(n_cand + 8);
+  b.P2 = ar.get<uint64_t>(n_cand + 8);
+  b.hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  b.digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
+  const int cfg_pairs = g_cfg_pairs.load();
+  b.status = ar.get<uint64_t>(back_status_bytes(n_cand, cfg_pairs) / 8 + 1);
+  b.counters = ar.get<uint64_t>(2);
   uint32_t* peq = ar.get<uint32_t>((size_t)n_q * PEQ_STRIDE);
   XTN_ALLOC_OK(ar);
-  launch_query_emit(idx->rec, idx->n_rec, idx->id_bits, qv_start, qv_q, cand_off, n_qv, n_cand, P1,
-                    sms, err, s);
+  launch_query_emit(idx->rec, idx->n_rec, idx->id_bits, qv_start, qv_q, cand_off, n_qv, n_cand,
+                    b.P1, sms, err, s);
   launch_peq(e.keys, e.lens, n_q, peq, s);
   XTN_CK(cudaGetLastError());
   OutRows o;
   rc = prepare_out(out, cap, n_cand, ar, &o);
   if (rc) return rc;
-  uint64_t n_rows = 0;
-  rc = verify_sort_finalize(P1, n_cand, pair_bits, idx->id_bits, peq, e.lens, (uint64_t)n_q,
-                            idx->keys, idx->lens, (uint64_t)idx->n, nullptr, 0, idx->d, o.dev,
-                            o.dev_cap, sms, ar, err, s, &n_rows);
+  rc = launch_back(b, n_cand, nullptr, pair_bits, idx->id_bits, peq, e.lens, (uint64_t)n_q,
+                   idx->keys, idx->lens, (uint64_t)idx->n, nullptr, 0, idx->d, o.dev, o.dev_cap,
+                   sms, err, s, cfg_pairs);
   if (rc) return rc;
+  struct {
+    uint64_t rows;
+    uint32_t err;
+  } h{0, 0};
+  XTN_CK(cudaMemcpyAsync(&h.rows, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err) return map_device_err(h.err);
+  const uint64_t n_rows = h.rows;
   return finish_out(o, out, cap, n_rows, s, n_out);
 }
 
@@ -678,6 +703,210 @@ int tcrdist_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, const x
 }  // namespace xtn
 
 // ======================================================================
+// Plans (sync-free self-search, batched mode)
+// ======================================================================
+struct xtn_plan {
+  int device = 0;
+  int d = 0;
+  int64_t n = 0;
+  uint64_t rec_cap = 0, pair_cap = 0, g_cap = 0;
+  uint32_t id_bits = 0;
+  int hs = 0, cfg_rec = 0, cfg_pair = 0, sms = 0;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t* off = nullptr;
+  uint32_t* seq_rep = nullptr;
+  xtn::Key128* keys = nullptr;
+  uint8_t* lens = nullptr;
+  uint32_t *eqprev = nullptr, *vcount = nullptr, *hist = nullptr, *peq = nullptr, *err = nullptr;
+  uint64_t *rec_off = nullptr, *A = nullptr, *B = nullptr, *digit_base = nullptr;
+  uint64_t *status = nullptr, *flags = nullptr, *counters = nullptr;
+  uint32_t *S = nullptr, *E = nullptr;
+  uint64_t* pair_off = nullptr;
+  uint64_t* sorted = nullptr;
+  xtn::BackStage back;
+  xtn_triple* rows = nullptr;
+
+  template <class T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    const size_t b = (count ? count : 1) * sizeof(T) + 64;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    allocs.push_back(p);
+    bytes += (int64_t)b;
+    return static_cast<T*>(p);
+  }
+  ~xtn_plan() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace xtn {
+namespace {
+
+int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* rep_offsets,
+                     int64_t n_rep, int64_t pair_capacity, xtn_plan** out) {
+  if (!out) return XTN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || d < 0 || d > XTN_MAX_D || !offsets) return XTN_ERR_INVALID_ARG;
+  if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
+  if (rep_offsets && n_rep < 1) return XTN_ERR_INVALID_ARG;
+  int sms = 0;
+  int rc = current_device_info(&sms);
+  if (rc) return rc;
+  std::vector<int64_t> h(n + 1);
+  if (is_device_ptr(offsets)) {
+    if (cudaMemcpy(h.data(), offsets, (n + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return XTN_ERR_CUDA;
+    }
+  } else {
+    std::memcpy(h.data(), offsets, (n + 1) * 8);
+  }
+  rc = check_host_offsets(h.data(), n);
+  if (rc) return rc;
+  uint64_t rec_cap = 0;  // every deletion subset: canonical ones are a subset
+  for (int64_t i = 0; i < n; ++i) rec_cap += variant_count((uint32_t)(h[i + 1] - h[i]), (uint32_t)d);
+  if (rec_cap >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  xtn_plan* p = new xtn_plan;
+  cudaGetDevice(&p->device);
+  p->d = d;
+  p->n = n;
+  p->sms = sms;
+  p->rec_cap = rec_cap;
+  p->g_cap = rec_cap / 2 + 1;
+  p->pair_cap = pair_capacity > 0 ? (uint64_t)pair_capacity
+                                  : std::max<uint64_t>(rec_cap / 8, 65536);
+  if (p->pair_cap >= (1ull << 32)) p->pair_cap = (1ull << 32) - 1;
+  p->id_bits = bits_for((uint64_t)n);
+  p->hs = choose_hash_bits(rec_cap, p->id_bits);
+  p->cfg_rec = g_cfg_records.load();
+  p->cfg_pair = g_cfg_pairs.load();
+  const size_t st = std::max({radix_status_bytes((int64_t)rec_cap, p->cfg_rec),
+                              group_status_bytes((int64_t)rec_cap),
+                              scan_status_bytes((int64_t)p->g_cap), scan_status_bytes(n)});
+  p->off = p->alloc<int64_t>(n + 1);
+  p->keys = p->alloc<Key128>(n);
+  p->lens = p->alloc<uint8_t>(n);
+  p->eqprev = p->alloc<uint32_t>(n);
+  p->vcount = p->alloc<uint32_t>(n);
+  p->rec_off = p->alloc<uint64_t>(n + 1);
+  p->A = p->alloc<uint64_t>(rec_cap + 8);
+  p->B = p->alloc<uint64_t>(rec_cap + 8);
+  p->hist = p->alloc<uint32_t>(MAX_PASSES * RADIX);
+  p->digit_base = p->alloc<uint64_t>(MAX_PASSES * RADIX);
+  p->status = p->alloc<uint64_t>(st / 8 + 1);
+  p->flags = p->alloc<uint64_t>(group_flag_words((int64_t)rec_cap));
+  p->counters = p->alloc<uint64_t>(4);
+  p->err = p->alloc<uint32_t>(4);
+  p->peq = p->alloc<uint32_t>((size_t)n * PEQ_STRIDE);
+  p->back.P1 = p->alloc<uint64_t>(p->pair_cap + 8);
+  p->back.P2 = p->alloc<uint64_t>(p->pair_cap + 8);
+  p->back.hist = p->alloc<uint32_t>(MAX_PASSES * RADIX);
+  p->back.digit_base = p->alloc<uint64_t>(MAX_PASSES * RADIX);
+  p->back.status = p->alloc<uint64_t>(back_status_bytes(p->pair_cap, p->cfg_pair) / 8 + 1);
+  p->back.counters = p->alloc<uint64_t>(2);
+  p->rows = p->alloc<xtn_triple>(p->pair_cap);
+  if (rep_offsets) p->seq_rep = p->alloc<uint32_t>(n);
+  bool ok = p->rows && p->back.counters && p->back.status && p->back.digit_base && p->back.hist &&
+            p->back.P2 && p->back.P1 && p->peq && p->err && p->counters && p->flags && p->status &&
+            p->digit_base && p->hist && p->B && p->A && p->rec_off && p->vcount && p->eqprev &&
+            p->lens && p->keys && p->off && (!rep_offsets || p->seq_rep);
+  if (!ok) {
+    delete p;
+    return XTN_ERR_OOM;
+  }
+  // records end in A after an even number of passes; groups live in the other
+  const int passes = (p->hs + 7) / 8;
+  p->sorted = (passes % 2 == 0) ? p->A : p->B;
+  uint64_t* spare = (passes % 2 == 0) ? p->B : p->A;
+  p->S = reinterpret_cast<uint32_t*>(spare);
+  p->E = p->S + p->g_cap;
+  p->pair_off = reinterpret_cast<uint64_t*>(p->E + p->g_cap);
+  cudaStream_t s = nullptr;
+  if (cudaMemcpy(p->off, h.data(), (n + 1) * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return XTN_ERR_CUDA;
+  }
+  if (rep_offsets) {
+    Arena ar(s);
+    rc = stage_reps(rep_offsets, n_rep, n, &ar, s, p->seq_rep);
+    if (rc == XTN_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = XTN_ERR_CUDA;
+    if (rc) {
+      delete p;
+      return rc;
+    }
+  }
+  *out = p;
+  return XTN_OK;
+}
+
+int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
+  if (!p || !seqs) return XTN_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return XTN_ERR_INVALID_ARG;
+  const int64_t n = p->n;
+  const int lo = 64 - p->hs;
+  XTN_CK(cudaMemsetAsync(p->err, 0, 16, s));
+  XTN_CK(cudaMemsetAsync(p->counters, 0, 32, s));
+  XTN_CK(cudaMemsetAsync(p->hist, 0, MAX_PASSES * RADIX * 4, s));
+  launch_encode(seqs, p->off, n, p->d, p->keys, p->lens, p->eqprev, p->vcount, p->err, s);
+  launch_scan_counts(p->vcount, n, p->rec_off, p->status, p->err, s);
+  launch_expand(p->keys, p->lens, p->eqprev, p->rec_off, n, p->d, p->seq_rep, p->id_bits, p->A,
+                p->rec_cap, p->hist, lo, std::min(64, lo + 8), p->sms, p->err, s);
+  uint64_t* sorted = nullptr;
+  const uint64_t* n_rec = p->rec_off + n;  // known on the device only
+  XTN_CK(radix_sort_passes(p->A, p->B, (int64_t)p->rec_cap, lo, 64, p->hist, p->digit_base,
+                           p->status, p->cfg_rec, p->err, &sorted, "k_onesweep_records", s, true,
+                           n_rec));
+  if (sorted != p->sorted) return XTN_ERR_CUDA;
+  launch_group_bounds(sorted, (int64_t)p->rec_cap, n_rec, lo, p->S, p->E, p->g_cap, p->flags,
+                      p->status, p->err, p->counters, s);
+  launch_scan_group_pairs(p->S, p->E, (int64_t)p->g_cap, p->counters, p->pair_off, p->status,
+                          p->err, s);
+  launch_emit_pairs(sorted, p->rec_cap, p->S, p->pair_off, (int64_t)p->g_cap, p->counters,
+                    p->pair_cap, p->id_bits, p->back.P1, p->counters + 1, p->sms, p->err, s);
+  launch_peq(p->keys, p->lens, n, p->peq, s);
+  XTN_CK(cudaGetLastError());
+  return launch_back(p->back, p->pair_cap, p->counters + 1, 2 * p->id_bits, p->id_bits, p->peq,
+                     p->lens, (uint64_t)n, p->keys, p->lens, (uint64_t)n, p->seq_rep, 1, p->d,
+                     p->rows, (int64_t)p->pair_cap, p->sms, p->err, s, p->cfg_pair);
+}
+
+int plan_result_impl(xtn_plan* p, xtn_triple* out, int64_t cap, int64_t* n_out, cudaStream_t s) {
+  if (!n_out) return XTN_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (!p || cap < 0 || (cap > 0 && !out)) return XTN_ERR_INVALID_ARG;
+  struct {
+    uint64_t pairs, rows;
+    uint32_t err;
+  } h{0, 0, 0};
+  XTN_CK(cudaMemcpyAsync(&h.pairs, p->counters + 1, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.rows, p->back.counters + 1, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, p->err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaStreamSynchronize(s));
+  if (h.err & DERR_CAPACITY) {
+    *n_out = (int64_t)h.pairs;
+    return XTN_ERR_CAPACITY;
+  }
+  if (h.err) return map_device_err(h.err);
+  *n_out = (int64_t)h.rows;
+  const int64_t w = std::min<int64_t>(cap, (int64_t)h.rows);
+  if (w > 0) {
+    XTN_CK(cudaMemcpyAsync(out, p->rows, w * sizeof(xtn_triple), cudaMemcpyDefault, s));
+    XTN_CK(cudaStreamSynchronize(s));
+  }
+  return (int64_t)h.rows > cap ? XTN_ERR_BUFFER_TOO_SMALL : XTN_OK;
+}
+
+}  // namespace
+}  // namespace xtn
+
+// ======================================================================
 // extern "C"
 // ======================================================================
 extern "C" {
@@ -693,6 +922,7 @@ const char* xtn_status_string(int status) {
     case XTN_ERR_CUDA: return "CUDA runtime error";
     case XTN_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
     case XTN_ERR_TOO_LARGE: return "problem exceeds 2^32-1 records or pairs";
+    case XTN_ERR_CAPACITY: return "more candidate pairs than the plan's capacity";
   }
   return "unknown status";
 }
@@ -743,6 +973,34 @@ int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,
                        int64_t* n_out, xtn_stream_t stream) {
   return xtn::tcrdist_impl(seqs, offsets, n, in, n_in, max_score, out, n_out,
                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_plan_create(const int64_t* offsets, int64_t n, int d, const int64_t* rep_offsets,
+                    int64_t n_rep, int64_t pair_capacity, xtn_plan** out) {
+  return xtn::plan_create_impl(offsets, n, d, rep_offsets, n_rep, pair_capacity, out);
+}
+
+int xtn_plan_run(xtn_plan* plan, const uint8_t* seqs, xtn_stream_t stream) {
+  return xtn::plan_run_impl(plan, seqs, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_plan_result(xtn_plan* plan, xtn_triple* out, int64_t cap, int64_t* n_out,
+                    xtn_stream_t stream) {
+  return xtn::plan_result_impl(plan, out, cap, n_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_plan_info(const xtn_plan* plan, int64_t* record_capacity, int64_t* pair_capacity,
+                  int64_t* device_bytes) {
+  if (!plan) return XTN_ERR_INVALID_ARG;
+  if (record_capacity) *record_capacity = (int64_t)plan->rec_cap;
+  if (pair_capacity) *pair_capacity = (int64_t)plan->pair_cap;
+  if (device_bytes) *device_bytes = plan->bytes;
+  return XTN_OK;
+}
+
+int xtn_plan_free(xtn_plan* plan) {
+  delete plan;
+  return XTN_OK;
 }
 
 int xtn_tune_set(int knob, int value) {

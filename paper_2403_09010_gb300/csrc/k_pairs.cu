@@ -63,12 +63,21 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* s_w, u
 // out[k] = sum_{k' < k} f(k') for k <= n (out[n] = total).
 template <class F>
 __global__ void __launch_bounds__(SCAN_THREADS)
-    k_scan_counts(F f, int64_t n, uint64_t* __restrict__ out, uint64_t* __restrict__ status,
+    k_scan_counts(F f, int64_t n_cap, const uint64_t* __restrict__ n_dev,
+                  uint64_t* __restrict__ out, uint64_t* __restrict__ status,
                   uint32_t* __restrict__ ctr, uint32_t* __restrict__ err) {
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_w[SCAN_THREADS / 32];
   __shared__ uint64_t s_prefix;
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
+  if (n == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+    return;
+  }
+  // persistent: every block takes tiles in start order until the input runs out
+  for (;;) {
   const uint32_t tile = tile_id(ctr, &s_tile);
+  if ((int64_t)tile * SCAN_TILE >= n) break;
   const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
   uint64_t v[SCAN_ITEMS];
   uint64_t sum = 0;
@@ -91,6 +100,8 @@ __global__ void __launch_bounds__(SCAN_THREADS)
     run += v[i];
     if (base + i == n - 1) out[n] = run;
   }
+  __syncthreads();  // s_prefix and s_tile are reused by the next tile
+  }
 }
 
 size_t scan_status_bytes(int64_t n) {
@@ -98,26 +109,29 @@ size_t scan_status_bytes(int64_t n) {
 }
 
 template <class F>
-static void scan_launch(F f, int64_t n, uint64_t* out, uint64_t* status, uint32_t* err,
-                        const char* tag, double bytes, cudaStream_t s) {
+static void scan_launch(F f, int64_t n, const uint64_t* n_dev, uint64_t* out, uint64_t* status,
+                        uint32_t* err, const char* tag, double bytes, cudaStream_t s) {
   const size_t st = scan_status_bytes(n);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
   prof_begin(s, tag, bytes);
-  k_scan_counts<<<div_up_u32(n, SCAN_TILE), SCAN_THREADS, 0, s>>>(f, n, out, status, ctr, err);
+  k_scan_counts<<<std::min<uint32_t>(div_up_u32(n, SCAN_TILE), 152 * 16), SCAN_THREADS, 0, s>>>(
+      f, n, n_dev, out, status, ctr, err);
   prof_end(s);
 }
 
 void launch_scan_counts(const uint32_t* counts, int64_t n, uint64_t* out, uint64_t* status,
                         uint32_t* err, cudaStream_t s) {
   if (n <= 0) return;
-  scan_launch(CountsU32{counts}, n, out, status, err, "k_scan_counts", (double)n * 12.0, s);
+  scan_launch(CountsU32{counts}, n, nullptr, out, status, err, "k_scan_counts", (double)n * 12.0,
+              s);
 }
 
 void launch_scan_group_pairs(const uint32_t* S, const uint32_t* E, int64_t n_groups,
-                             uint64_t* out, uint64_t* status, uint32_t* err, cudaStream_t s) {
+                             const uint64_t* n_groups_dev, uint64_t* out, uint64_t* status,
+                             uint32_t* err, cudaStream_t s) {
   if (n_groups <= 0) return;
-  scan_launch(PairsOfGroup{S, E}, n_groups, out, status, err, "k_scan_group_pairs",
+  scan_launch(PairsOfGroup{S, E}, n_groups, n_groups_dev, out, status, err, "k_scan_group_pairs",
               (double)n_groups * 16.0, s);
 }
 
@@ -145,10 +159,16 @@ constexpr int GB_WORDS = GB_TILE / 32;                       // flag words per t
 // K = uint32_t when the group key (key >> gshift) fits in 32 bits.
 template <typename K>
 __global__ void __launch_bounds__(GB_THREADS)
-    k_group_flags(const uint64_t* __restrict__ keys, int64_t n, int gshift,
-                  uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts) {
+    k_group_flags(const uint64_t* __restrict__ keys, int64_t n_cap,
+                  const uint64_t* __restrict__ n_dev, int gshift, uint64_t* __restrict__ flags,
+                  uint64_t* __restrict__ tile_counts) {
   __shared__ uint64_t s_wtot[GB_WARPS];
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
   const int64_t tbase = (int64_t)blockIdx.x * GB_TILE;
+  if (tbase >= n) {
+    if (threadIdx.x == 0) tile_counts[blockIdx.x] = 0;
+    return;
+  }
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const int64_t wbase = tbase + (int64_t)warp * GB_WARP_SPAN;
   // the value before position wbase (made different from it at position 0)
@@ -199,11 +219,14 @@ __global__ void __launch_bounds__(GB_THREADS)
 }
 
 __global__ void __launch_bounds__(GB_THREADS)
-    k_group_write(const uint64_t* __restrict__ flags, int64_t n,
-                  const uint64_t* __restrict__ tile_prefix, uint32_t* __restrict__ S,
-                  uint32_t* __restrict__ E, uint64_t cap, uint32_t* __restrict__ err) {
+    k_group_write(const uint64_t* __restrict__ flags, int64_t n_cap,
+                  const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ tile_prefix,
+                  uint32_t* __restrict__ S, uint32_t* __restrict__ E, uint64_t cap,
+                  uint32_t* __restrict__ err) {
   __shared__ uint64_t s_w[GB_WARPS];
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
   const int64_t tbase = (int64_t)blockIdx.x * GB_TILE;
+  if (tbase >= n) return;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   // each warp owns GB_WARP_SPAN / 32 flag words; lane l holds words l, l+32, ...
   constexpr int WPW = GB_WARP_SPAN / 32;  // words per warp (64)
@@ -279,9 +302,9 @@ size_t group_status_bytes(int64_t n) {
 
 size_t group_flag_words(int64_t n) { return (size_t)((n + 31) / 32); }
 
-void launch_group_bounds(const uint64_t* keys, int64_t n, int gshift, uint32_t* S, uint32_t* E,
-                         uint64_t cap, uint64_t* flags, uint64_t* status, uint32_t* err,
-                         uint64_t* n_groups, cudaStream_t s) {
+void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
+                         uint32_t* S, uint32_t* E, uint64_t cap, uint64_t* flags,
+                         uint64_t* status, uint32_t* err, uint64_t* n_groups, cudaStream_t s) {
   if (n <= 0) return;
   const int64_t tiles = (n + GB_TILE - 1) / GB_TILE;
   // scratch layout in `status`: [scan status][tile counts][tile prefix (tiles+1)]
@@ -290,19 +313,21 @@ void launch_group_bounds(const uint64_t* keys, int64_t n, int gshift, uint32_t* 
   uint64_t* tile_prefix = tile_counts + tiles;
   prof_begin(s, "k_group_flags", (double)n * 8.0 + (double)(n / 32) * 8.0);
   if (gshift >= 32)
-    k_group_flags<uint32_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, gshift, flags, tile_counts);
+    k_group_flags<uint32_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, n_dev, gshift, flags,
+                                                                   tile_counts);
   else
-    k_group_flags<uint64_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, gshift, flags, tile_counts);
+    k_group_flags<uint64_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, n_dev, gshift, flags,
+                                                                   tile_counts);
   prof_end(s);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
   prof_begin(s, "k_scan_tiles", (double)tiles * 16.0);
-  k_scan_counts<<<div_up_u32(tiles, SCAN_TILE), SCAN_THREADS, 0, s>>>(CountsU64{tile_counts},
-                                                                     tiles, tile_prefix, status,
-                                                                     ctr, err);
+  k_scan_counts<<<std::min<uint32_t>(div_up_u32(tiles, SCAN_TILE), 152 * 16), SCAN_THREADS, 0,
+                  s>>>(CountsU64{tile_counts}, tiles, nullptr, tile_prefix, status, ctr, err);
   prof_end(s);
   prof_begin(s, "k_group_write", (double)(n / 32) * 8.0);
-  k_group_write<<<(unsigned)tiles, GB_THREADS, 0, s>>>(flags, n, tile_prefix, S, E, cap, err);
+  k_group_write<<<(unsigned)tiles, GB_THREADS, 0, s>>>(flags, n, n_dev, tile_prefix, S, E, cap,
+                                                       err);
   prof_end(s);
   // number of groups = heads in the total (high field of tile_prefix[tiles])
   k_groups_total<<<1, 1, 0, s>>>(tile_prefix + tiles, n_groups);
@@ -334,10 +359,20 @@ __device__ __forceinline__ void unrank_pair(uint64_t l, uint64_t& a, uint64_t& b
 
 __global__ void __launch_bounds__(EMIT_THREADS)
     k_emit_pairs(const uint64_t* __restrict__ keys, uint64_t n_keys, const uint32_t* __restrict__ S,
-                 const uint64_t* __restrict__ pair_off, int64_t n_groups, uint64_t n_pairs,
-                 uint32_t id_bits, uint64_t* __restrict__ out, uint32_t* __restrict__ err) {
+                 const uint64_t* __restrict__ pair_off, int64_t n_groups_cap,
+                 const uint64_t* __restrict__ n_groups_dev, uint64_t pair_cap, uint32_t id_bits,
+                 uint64_t* __restrict__ out, uint64_t* __restrict__ n_pairs_out,
+                 uint32_t* __restrict__ err) {
   __shared__ uint64_t s_off[EMIT_TILE + 1];
   __shared__ int64_t s_k0, s_k1;
+  // group count and pair count may only be known on the device
+  const int64_t n_groups = n_groups_dev ? min((int64_t)*n_groups_dev, n_groups_cap) : n_groups_cap;
+  const uint64_t n_all = pair_off[n_groups];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (n_pairs_out) *n_pairs_out = n_all;
+    if (n_all > pair_cap) atomicOr(err, DERR_CAPACITY);
+  }
+  const uint64_t n_pairs = n_all < pair_cap ? n_all : pair_cap;
   const uint64_t idmask = (1ull << id_bits) - 1ull;
   for (uint64_t t0 = (uint64_t)blockIdx.x * EMIT_TILE; t0 < n_pairs;
        t0 += (uint64_t)gridDim.x * EMIT_TILE) {
@@ -381,14 +416,15 @@ __global__ void __launch_bounds__(EMIT_THREADS)
 }
 
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
-                       const uint64_t* pair_off, int64_t n_groups, uint64_t n_pairs,
-                       uint32_t id_bits, uint64_t* out, int sms, uint32_t* err, cudaStream_t s) {
-  if (n_pairs == 0) return;
-  const uint64_t tiles = (n_pairs + EMIT_TILE - 1) / EMIT_TILE;
+                       const uint64_t* pair_off, int64_t n_groups, const uint64_t* n_groups_dev,
+                       uint64_t pair_cap, uint32_t id_bits, uint64_t* out, uint64_t* n_pairs_out,
+                       int sms, uint32_t* err, cudaStream_t s) {
+  if (pair_cap == 0 || n_groups <= 0) return;
+  const uint64_t tiles = (pair_cap + EMIT_TILE - 1) / EMIT_TILE;
   const int blocks = (int)std::min<uint64_t>(tiles, (uint64_t)sms * 8);
-  prof_begin(s, "k_emit_pairs", (double)n_pairs * (8.0 + 16.0));
-  k_emit_pairs<<<blocks, EMIT_THREADS, 0, s>>>(keys, n_keys, S, pair_off, n_groups, n_pairs,
-                                               id_bits, out, err);
+  prof_begin(s, "k_emit_pairs", (double)pair_cap * (8.0 + 16.0));
+  k_emit_pairs<<<blocks, EMIT_THREADS, 0, s>>>(keys, n_keys, S, pair_off, n_groups, n_groups_dev,
+                                               pair_cap, id_bits, out, n_pairs_out, err);
   prof_end(s);
 }
 

@@ -187,7 +187,8 @@ __device__ __forceinline__ void rank_items2(const uint64_t (&key)[ITEMS], uint16
 
 template <int THREADS, int ITEMS, int MIN_BLOCKS, int MATCH, int NCHAIN = 1>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
-    k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n, int shift,
+    k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+               const uint64_t* __restrict__ n_dev, int64_t n_cap, int shift,
                int bits, const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
                uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
                uint32_t* __restrict__ next_hist, int next_bits) {
@@ -207,11 +208,17 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 
   if (next_hist)
     for (int k = threadIdx.x; k < RADIX; k += THREADS) s_next[k] = 0;
-  const uint32_t tile = tile_id(ctr, &s_tile);
-  const int64_t tile_base = (int64_t)tile * TILE;
-  const bool full = tile_base + TILE <= n;
+  // key count: on the device when the caller did not know it at launch time
+  // (grid sized for n_cap; tiles past the count leave at once)
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t dmask = (1u << bits) - 1u;
+  // persistent: every block takes tiles in start order until the keys run out
+  for (;;) {
+  const uint32_t tile = tile_id(ctr, &s_tile);
+  const int64_t tile_base = (int64_t)tile * TILE;
+  if (tile_base >= n) break;
+  const bool full = tile_base + TILE <= n;
 
   for (int k = threadIdx.x; k < NCHAIN * WARPS * RADIX; k += THREADS) s_whist[k] = 0;
   if (MATCH == 2)
@@ -308,9 +315,6 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
   __syncthreads();
 
-  if (next_hist && threadIdx.x < RADIX && s_next[threadIdx.x])
-    atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
-
   // 6. write out in digit order
   const int tile_n = full ? TILE : (int)(n - tile_base);
   for (int j = threadIdx.x; j < tile_n; j += THREADS) {
@@ -320,6 +324,10 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     if (o >= 0 && o < n) out[o] = k;
     else atomicOr(err, DERR_RANGE);
   }
+  __syncthreads();  // shared staging is reused by the next tile
+  }
+  if (next_hist && threadIdx.x < RADIX && s_next[threadIdx.x])
+    atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
 }
 
 // Tile configurations (id, threads, items per thread, min blocks per SM,
@@ -355,8 +363,22 @@ int onesweep_tile(int cfg) {
 
 int onesweep_configs() { return 16; }
 
+// Multiprocessor count of the current device (cached per device).
+static int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 1;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
-                                   int shift, int bits, const uint64_t* digit_base,
+                                   const uint64_t* n_dev, int shift, int bits, const uint64_t* digit_base,
                                    uint64_t* status, uint32_t* ctr, uint32_t* err,
                                    uint32_t* next_hist, int next_bits, cudaStream_t s) {
   switch (cfg) {
@@ -370,8 +392,12 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
       cudaFuncSetAttribute(k_onesweep<T, I, B, M, C>,                                            \
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
     });                                                                                       \
-    const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
-    k_onesweep<T, I, B, M, C><<<tiles, T, SM::bytes, s>>>(in, out, n, shift, bits, digit_base,   \
+    /* a count known only on the device: persistent grid; else one tile per block */        \
+    const uint32_t tiles = n_dev ? std::min<uint32_t>(div_up_u32(n, SM::TILE),               \
+                                                      (uint32_t)(device_sms() * B))           \
+                                 : div_up_u32(n, SM::TILE);                                   \
+    k_onesweep<T, I, B, M, C><<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits,        \
+                                                          digit_base,                         \
                                                        status, ctr, err, next_hist,           \
                                                        next_bits);                            \
     return cudaGetLastError();                                                                \
@@ -399,7 +425,7 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
 cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
-                              bool hist_in_passes) {
+                              bool hist_in_passes, const uint64_t* n_dev) {
   const int passes = (hi - lo + 7) / 8;
   *sorted = a;
   if (n <= 1 || passes == 0) return cudaSuccess;
@@ -421,8 +447,8 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
     cudaError_t e = cudaMemsetAsync(status, 0, st_bytes, s);
     if (e != cudaSuccess) return e;
     prof_begin(s, tag, (double)n * 16.0);
-    e = onesweep_launch(cfg, src, dst, n, sh, bits, digit_base + p * RADIX, status, ctr, err, next,
-                        next_bits, s);
+    e = onesweep_launch(cfg, src, dst, n, n_dev, sh, bits, digit_base + p * RADIX, status, ctr, err,
+                        next, next_bits, s);
     prof_end(s);
     if (e != cudaSuccess) return e;
     std::swap(src, dst);

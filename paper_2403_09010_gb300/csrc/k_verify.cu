@@ -97,7 +97,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_
 }
 
 __global__ void __launch_bounds__(256)
-    k_verify_candidates(const uint64_t* __restrict__ cand, uint64_t n, uint32_t j_bits,
+    k_verify_candidates(const uint64_t* __restrict__ cand, uint64_t n_cap,
+                        const uint64_t* __restrict__ n_dev, uint32_t j_bits,
                         const uint32_t* __restrict__ peq_i, const uint8_t* __restrict__ lens_i,
                         uint64_t n_i, const Key128* __restrict__ keys_j,
                         const uint8_t* __restrict__ lens_j, uint64_t n_j,
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(256)
   const int passes = (hist_hi + 7) / 8;
   for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
   __syncthreads();
+  const uint64_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
   const uint32_t lane = lane_id();
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint64_t jmask = (1ull << j_bits) - 1ull;
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(256)
     if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
 }
 
-void launch_verify_candidates(const uint64_t* cand, uint64_t n, uint32_t j_bits,
+void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* n_dev,
+                              uint32_t j_bits,
                               const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                               const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                               const uint32_t* seq_rep, int self_mode, int d, uint64_t* surv,
@@ -167,13 +170,14 @@ void launch_verify_candidates(const uint64_t* cand, uint64_t n, uint32_t j_bits,
   const int blocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
   prof_begin(s, "k_verify_candidates", (double)n * (8.0 + 2 * 17.0 + 4.0 * 4));
   k_verify_candidates<<<blocks, 256, 0, s>>>(
-      cand, n, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep, self_mode, d, surv,
+      cand, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep, self_mode, d, surv,
       surv_cap, reinterpret_cast<unsigned long long*>(n_surv), hist, hist_hi, err);
   prof_end(s);
 }
 
 __global__ void __launch_bounds__(VER_THREADS)
-    k_unique_finalize(const uint64_t* __restrict__ pairs, int64_t n, uint32_t j_bits,
+    k_unique_finalize(const uint64_t* __restrict__ pairs, int64_t n_cap,
+                      const uint64_t* __restrict__ n_dev, uint32_t j_bits,
                       const uint32_t* __restrict__ peq_i, const uint8_t* __restrict__ lens_i,
                       uint64_t n_i, const Key128* __restrict__ keys_j,
                       const uint8_t* __restrict__ lens_j, uint64_t n_j,
@@ -183,8 +187,12 @@ __global__ void __launch_bounds__(VER_THREADS)
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_w[VER_THREADS / 32];
   __shared__ uint64_t s_prefix;
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
+  // persistent: every block takes tiles in start order until the input runs out
+  for (;;) {
   const uint32_t tile = tile_id(ctr, &s_tile);
   const int64_t tbase = (int64_t)tile * VER_TILE;
+  if (tbase >= n) break;
   const int64_t base = tbase + (int64_t)threadIdx.x * VER_ITEMS;
   const uint64_t jmask = (1ull << j_bits) - 1ull;
   uint64_t prev = (base > 0 && base - 1 < n) ? pairs[base - 1] : ~0ull;
@@ -233,11 +241,14 @@ __global__ void __launch_bounds__(VER_THREADS)
       ++o;
     }
   }
+  __syncthreads();  // s_prefix and s_tile are reused by the next tile
+  }
 }
 
 size_t verify_status_bytes(int64_t n) { return (size_t)((n + VER_TILE - 1) / VER_TILE) * 8 + 16; }
 
-void launch_unique_finalize(const uint64_t* pairs, int64_t n, uint32_t j_bits,
+void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_dev,
+                            uint32_t j_bits,
                             const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                             xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
@@ -247,8 +258,8 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, uint32_t j_bits,
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
   prof_begin(s, "k_unique_finalize", (double)n * 8.0);
-  k_unique_finalize<<<div_up_u32(n, VER_TILE), VER_THREADS, 0, s>>>(
-      pairs, n, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, out, cap, status, ctr, err,
+  k_unique_finalize<<<std::min<uint32_t>(div_up_u32(n, VER_TILE), 152 * 8), VER_THREADS, 0, s>>>(
+      pairs, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, out, cap, status, ctr, err,
       total);
   prof_end(s);
 }

@@ -19,6 +19,7 @@ enum : uint32_t {
   DERR_TOO_LONG = 1u << 1,
   DERR_TIMEOUT = 1u << 2,
   DERR_RANGE = 1u << 3,   // an index outside the caller's sequence range
+  DERR_CAPACITY = 1u << 4,  // more candidate pairs than a planned capacity
 };
 
 // A spin on a predecessor's status word gives up after this many polls

@@ -44,10 +44,12 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
 // digit histograms of every pass.  *sorted receives a or b.
 // hist_in_passes: `hist` holds only pass 0's digit counts; every pass counts
 // the next pass's digits itself (zeroed hist rows 1.. expected).
+// n_dev: when not null the key count is read on the device (n is then a
+// capacity that sizes the grid and the look-back status).
 cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
-                              bool hist_in_passes = false);
+                              bool hist_in_passes = false, const uint64_t* n_dev = nullptr);
 
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
@@ -55,24 +57,28 @@ size_t group_status_bytes(int64_t n);
 void launch_scan_counts(const uint32_t* counts, int64_t n, uint64_t* out, uint64_t* status,
                         uint32_t* err, cudaStream_t s);
 void launch_scan_group_pairs(const uint32_t* S, const uint32_t* E, int64_t n_groups,
-                             uint64_t* out, uint64_t* status, uint32_t* err, cudaStream_t s);
+                             const uint64_t* n_groups_dev, uint64_t* out, uint64_t* status,
+                             uint32_t* err, cudaStream_t s);
 size_t group_flag_words(int64_t n);
-void launch_group_bounds(const uint64_t* keys, int64_t n, int gshift, uint32_t* S, uint32_t* E,
-                         uint64_t cap, uint64_t* flags, uint64_t* status, uint32_t* err,
-                         uint64_t* n_groups, cudaStream_t s);
+void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
+                         uint32_t* S, uint32_t* E, uint64_t cap, uint64_t* flags,
+                         uint64_t* status, uint32_t* err, uint64_t* n_groups, cudaStream_t s);
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
-                       const uint64_t* pair_off, int64_t n_groups, uint64_t n_pairs,
-                       uint32_t id_bits, uint64_t* out, int sms, uint32_t* err, cudaStream_t s);
+                       const uint64_t* pair_off, int64_t n_groups, const uint64_t* n_groups_dev,
+                       uint64_t pair_cap, uint32_t id_bits, uint64_t* out, uint64_t* n_pairs_out,
+                       int sms, uint32_t* err, cudaStream_t s);
 
 // k_verify.cu --------------------------------------------------------------
 size_t verify_status_bytes(int64_t n);
-void launch_verify_candidates(const uint64_t* cand, uint64_t n, uint32_t j_bits,
+void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* n_dev,
+                              uint32_t j_bits,
                               const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                               const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                               const uint32_t* seq_rep, int self_mode, int d, uint64_t* surv,
                               uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist, int hist_hi,
                               int sms, uint32_t* err, cudaStream_t s);
-void launch_unique_finalize(const uint64_t* pairs, int64_t n, uint32_t j_bits,
+void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_dev,
+                            uint32_t j_bits,
                             const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                             xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,

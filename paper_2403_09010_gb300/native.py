@@ -22,6 +22,7 @@ XTN_ERR_BUFFER_TOO_SMALL = -5
 XTN_ERR_CUDA = -6
 XTN_ERR_DEVICE_TIMEOUT = -7
 XTN_ERR_TOO_LARGE = -8
+XTN_ERR_CAPACITY = -9
 XTN_TUNE_SORT_RECORDS = 0
 XTN_TUNE_SORT_PAIRS = 1
 XTN_NOALLOC_MAX_SEQS = 1 << 18
@@ -43,6 +44,11 @@ SIGNATURES = {
     "xtn_search_query": (_I, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
     "xtn_tcrdist_filter": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
     "xtn_tcrdist_filter_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
+    "xtn_plan_create": (_I, [_P, _I64, _I, _P, _I64, _I64, _P]),
+    "xtn_plan_run": (_I, [_P, _P, _P]),
+    "xtn_plan_result": (_I, [_P, _P, _I64, _P, _P]),
+    "xtn_plan_info": (_I, [_P, _P, _P, _P]),
+    "xtn_plan_free": (_I, [_P]),
     "xtn_tune_set": (_I, [_I, _I]),
     "xtn_tune_get": (_I, [_I]),
     "xtn_tune_count": (_I, [_I]),

@@ -116,6 +116,65 @@ class Index:
             pass
 
 
+class Plan:
+    """Planned self-search (see xtn_plan_create): device memory allocated once,
+    `run` only queues kernels on the current stream (CUDA-graph capturable),
+    `result` waits and returns the rows of the last run."""
+
+    def __init__(self, offsets, d: int, rep_offsets=None, pair_capacity: int = 0):
+        n = _n_items(offsets)
+        op, ok, _ = _ptr(offsets, np.int64)
+        rp, rk, _ = _ptr(rep_offsets, np.int64)
+        n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
+        h = ctypes.c_void_p(0)
+        check(native.lib().xtn_plan_create(op, n, int(d), rp, n_rep, int(pair_capacity),
+                                           ctypes.byref(h)), "xtn_plan_create")
+        self._h = h
+        self.n = n
+        self.d = int(d)
+
+    def info(self):
+        rc, pc, nb = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        check(native.lib().xtn_plan_info(self._h, ctypes.byref(rc), ctypes.byref(pc),
+                                         ctypes.byref(nb)), "xtn_plan_info")
+        return {"record_capacity": rc.value, "pair_capacity": pc.value, "device_bytes": nb.value}
+
+    def run(self, seqs, stream=None) -> None:
+        """Queue a search over device-resident `seqs` (torch CUDA tensor)."""
+        sp, sk, on_dev = _ptr(seqs, np.uint8)
+        if not on_dev:
+            raise ValueError("Plan.run needs the sequences in device memory")
+        st = ctypes.c_void_p(stream) if stream is not None else _stream(seqs)
+        check(native.lib().xtn_plan_run(self._h, sp, st), "xtn_plan_run")
+        self._keep = sk
+
+    def result(self, cap: int | None = None, like=None, stream=None):
+        """Rows of the last run (raises XtnError with XTN_ERR_CAPACITY if the
+        plan's pair capacity was too small; .needed holds the capacity needed)."""
+        st = ctypes.c_void_p(stream) if stream is not None else _stream(like)
+        if cap is None:
+            cap = self.info()["pair_capacity"]
+        out, optr = _alloc_rows(cap, like)
+        n_out = ctypes.c_int64(0)
+        rc = native.lib().xtn_plan_result(self._h, optr, int(cap), ctypes.byref(n_out), st)
+        if rc != native.XTN_OK:
+            e = XtnError(rc, "xtn_plan_result")
+            e.needed = n_out.value
+            raise e
+        return out[: n_out.value]
+
+    def free(self):
+        if getattr(self, "_h", None):
+            native.lib().xtn_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def index_build(seqs, offsets, d: int) -> Index:
     n = _n_items(offsets)
     sp, sk, _ = _ptr(seqs, np.uint8)

@@ -184,6 +184,54 @@ def test_batched_equals_separate_calls(xtn):
     assert np.array_equal(got, np.concatenate(parts).astype(np.uint32))
 
 
+# ------------------------------------------------------------------ plans ---
+def test_plan_matches_one_shot_and_replays_in_a_graph(xtn):
+    seqs, off, rep = gen.batched(n_rep=20, seed=11, size_min=100, size_max=8000)
+    want = _rows(xtn.search_self(seqs, off, 2, rep_offsets=rep))
+    ds, do = _dev(seqs, off)
+    plan = xtn.Plan(off, 2, rep_offsets=rep)
+    info = plan.info()
+    assert info["record_capacity"] > 0 and info["pair_capacity"] >= 65536
+    plan.run(ds)
+    assert np.array_equal(_rows(plan.result(like=ds)), want)
+    # the run queues only kernels and memsets: capture it and replay
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.run(ds)                       # warm-up on the capture stream
+        torch.cuda.current_stream().synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.run(ds)
+    for _ in range(3):
+        g.replay()
+        got = _rows(plan.result(like=ds))
+        assert np.array_equal(got, want)
+    # new letters, same layout: the graph searches whatever is in the buffer now
+    mutated = seqs.copy()
+    mutated[::7] = ord("W")
+    ds.copy_(torch.from_numpy(mutated))
+    g.replay()
+    assert np.array_equal(_rows(plan.result(like=ds)),
+                          _rows(xtn.search_self(mutated, off, 2, rep_offsets=rep)))
+    plan.free()
+
+
+def test_plan_capacity_is_reported(xtn):
+    from paper_2403_09010_gb300 import native
+    seqs, off = gen.workload(gen.SELF_1M, 30_000)
+    want = oracle.symdel_self(seqs, off, 2)
+    ds, do = _dev(seqs, off)
+    small = xtn.Plan(do, 2, pair_capacity=1000)
+    small.run(ds)
+    with pytest.raises(native.XtnError) as ei:
+        small.result(like=ds)
+    assert ei.value.status == native.XTN_ERR_CAPACITY and ei.value.needed > 1000
+    big = xtn.Plan(do, 2, pair_capacity=ei.value.needed)
+    big.run(ds)
+    assert np.array_equal(_rows(big.result(like=ds)), want)
+
+
 # ----------------------------------------------------------------- query ---
 @pytest.mark.parametrize("d", [1, 2])
 def test_query_matches_oracle(xtn, d):
