@@ -185,6 +185,122 @@ def cpu_baseline():
                       f"{rows.shape[0]:,} pairs"}
 
 
+def _events_ms(fn, reps, stream):
+    import torch
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return float(np.median(times))
+
+
+def run_batched(reps: int = 5):
+    """256 repertoires (log-uniform sizes 1e3..2e5), d=2: one autotuned plan
+    replayed as a CUDA graph vs one xtn_search_self call per repertoire."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    from paper_2403_09010_gb300 import autotune
+    seqs, off, rep = gen.batched()
+    ds = torch.from_numpy(seqs).cuda()
+    do = torch.from_numpy(off).cuda()
+    tuned = autotune.tune(ds, off, gen.BATCH_D, rep_offsets=rep, use_cache=False)
+    plan = xtn.Plan(off, gen.BATCH_D, rep_offsets=rep, pair_capacity=tuned["pair_capacity"])
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        plan.run(ds)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            plan.run(ds)
+        graph_ms = _events_ms(g.replay, reps, stream)
+        rows = plan.result(like=ds)
+        eager_ms = _events_ms(lambda: plan.run(ds), reps, stream)
+    stats = plan.stats()
+    # the plain path: one call per repertoire on the same resident data
+    rep_rows = []
+
+    def per_rep():
+        rep_rows.clear()
+        for r in range(rep.size - 1):
+            a, b = int(rep[r]), int(rep[r + 1])
+            o = do[a:b + 1] - do[a]
+            part = xtn.search_self(ds[int(off[a]):int(off[b])], o, gen.BATCH_D)
+            rep_rows.append((a, part))
+    cur = torch.cuda.current_stream()
+    per_rep()
+    per_rep_ms = _events_ms(per_rep, max(1, reps // 2), cur)
+    merged = torch.cat([p + torch.tensor([a, a, 0], dtype=torch.int32, device=p.device)
+                        for a, p in rep_rows])
+    identical = bool(torch.equal(merged, rows))
+    plan.free()
+    return {"workload": "batched_256reps_d2", "n": int(off.size - 1), "repertoires": int(rep.size - 1),
+            "graph_ms": graph_ms, "plan_eager_ms": eager_ms, "per_repertoire_ms": per_rep_ms,
+            "speedup_vs_per_repertoire": per_rep_ms / graph_ms, "pairs": int(rows.shape[0]),
+            "identical_output": identical, "autotune": tuned, "counts": stats}
+
+
+def run_served(speed: float = 1.0):
+    """10M-sequence resident index (d=2), 2,000 requests of 1..10,000 queries
+    arriving as a Poisson process at 200/s: continuous batching vs a plain
+    one-request-at-a-time queue on the same arrivals."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    from paper_2403_09010_gb300 import serve
+    rs, ro, reqs = gen.served()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idx = xtn.index_build(rs, ro, 2)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = idx.info()
+    out = {"workload": "served_ref1e7_2000req_d2", "index_build_s": build_s,
+           "index_records": info["n_records"], "index_device_bytes": info["device_bytes"]}
+    # warm the query path
+    xtn.search_query(idx, reqs[0].seqs, reqs[0].offsets)
+    # the nominal arrival rate, then the same requests arriving 4x and 16x
+    # faster, and all at once (capacity): continuous batching vs a plain queue
+    ref_rows = None
+    identical = True
+    for label, sp in [("rate_200", speed), ("rate_800", 4 * speed), ("rate_3200", 16 * speed),
+                      ("all_at_once", 1e9)]:
+        res = {}
+        for name, kw in [("continuous", dict(slots=4)),
+                         ("plain_queue", dict(slots=1, max_batch_queries=1))]:
+            srv = serve.Server(idx, **kw)
+            pend = serve.replay(srv, reqs, speed=sp)
+            srv.close()
+            res[name] = srv.stats(pend)
+            rows = [p.rows for p in pend]
+            if ref_rows is None:
+                ref_rows = rows
+            else:
+                identical &= all(np.array_equal(a, b) for a, b in zip(rows, ref_rows))
+        out[label] = res
+    out["identical_output"] = bool(identical)
+    idx.free()
+    return out
+
+
+def run_tcrdist(reps: int = 10):
+    """TCRdist post-filter (score <= 24) of the d=2 neighbours of 1M sequences."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    seqs, off = gen.workload(gen.TCRDIST_1M)
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    cur = torch.cuda.current_stream()
+    rows = xtn.search_self(ds, do, 2)
+    kept = xtn.tcrdist_filter(ds, do, rows, 24)
+    search_ms = _events_ms(lambda: xtn.search_self(ds, do, 2), reps, cur)
+    filter_ms = _events_ms(lambda: xtn.tcrdist_filter(ds, do, rows, 24), reps, cur)
+    return {"workload": "tcrdist_n1e6_d2_score24", "lev2_pairs": int(rows.shape[0]),
+            "kept_pairs": int(kept.shape[0]), "search_ms": search_ms, "filter_ms": filter_ms}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +308,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="xtn", choices=["xtn", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / served / TCRdist side measurements")
     ap.add_argument("--n", type=int, default=None,
                     help="use only the first n sequences (small cases for profiling)")
     args = ap.parse_args()
@@ -324,6 +442,10 @@ def main():
         "kernels": kernels,
         "clocks": clk.summary(),
     }
+    if not args.no_extras and world == 1 and args.n is None:
+        line["batched"] = run_batched()
+        line["served"] = run_served()
+        line["tcrdist"] = run_tcrdist()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -194,6 +194,11 @@ XTN_API int xtn_plan_result(xtn_plan* plan, xtn_triple* out, int64_t cap, int64_
                     xtn_stream_t stream);
 XTN_API int xtn_plan_info(const xtn_plan* plan, int64_t* record_capacity, int64_t* pair_capacity,
                   int64_t* device_bytes);
+/* Counts of the last run (waits for `stream`): variant records, groups of
+ * two or more records, candidate pairs, verified pair words (before dedup);
+ * any output pointer may be NULL. */
+XTN_API int xtn_plan_stats(xtn_plan* plan, int64_t* records, int64_t* groups, int64_t* candidates,
+                   int64_t* survivors, xtn_stream_t stream);
 XTN_API int xtn_plan_free(xtn_plan* plan);
 
 /*

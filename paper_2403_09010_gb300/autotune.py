@@ -1,0 +1,95 @@
+"""Autotuner for the planned (batched) self-search.
+
+Picks, by timing on the caller's own data, the tile configuration of each
+radix sort (variant records and verified pairs; see xtn_tune_set) and a
+candidate-pair capacity for the plan (measured candidates x 1.25, so a plan
+holds no more pair memory than it needs).  The pipeline splits large buckets
+of shared variants at the granularity of its emit tiles whatever their size,
+so there is no bucket-split threshold to tune.  Results are cached as JSON,
+keyed by GPU name, workload size and d.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import native, xtn
+
+
+def _cache_file():
+    return os.environ.get("XTN_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "xtn_tune.json"))
+
+
+def _key(n, n_rep, d):
+    try:
+        import torch
+        gpu = torch.cuda.get_device_name()
+    except Exception:
+        gpu = "unknown"
+    return f"{gpu}|n={n}|reps={n_rep}|d={d}"
+
+
+def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int = 2,
+         use_cache: bool = True) -> dict:
+    """Time every sort configuration on this workload and apply the fastest.
+    Returns {"records_cfg", "pairs_cfg", "pair_capacity", "sort_ms": {...}}."""
+    n = int(offsets.shape[0]) - 1
+    n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
+    key = _key(n, n_rep, d)
+    path = _cache_file()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        r = cache[key]
+        xtn.tune_set(native.XTN_TUNE_SORT_RECORDS, r["records_cfg"])
+        xtn.tune_set(native.XTN_TUNE_SORT_PAIRS, r["pairs_cfg"])
+        return r
+    import torch
+    R, P = native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS
+    configs = list(range(xtn.tune_count(R))) if configs is None else list(configs)
+
+    def measure(kernel):
+        plan = xtn.Plan(offsets, d, rep_offsets=rep_offsets)
+        plan.run(seqs_dev)                       # warm-up
+        torch.cuda.synchronize()
+        xtn.profile_report()
+        xtn.profile_enable(True)
+        for _ in range(repeats):
+            plan.run(seqs_dev)
+        torch.cuda.synchronize()
+        xtn.profile_enable(False)
+        prof = xtn.profile_report()
+        stats = plan.stats()
+        plan.free()
+        launches, ms, _ = prof.get(kernel, (1, float("inf"), 0))
+        return ms / repeats, stats
+
+    rec_ms, pair_ms = {}, {}
+    cands = 0
+    for c in configs:
+        xtn.tune_set(R, c)
+        rec_ms[c], st = measure("k_onesweep_records")
+        cands = max(cands, st["candidates"])
+    best_r = min(rec_ms, key=rec_ms.get)
+    xtn.tune_set(R, best_r)
+    for c in configs:
+        xtn.tune_set(P, c)
+        pair_ms[c], _ = measure("k_onesweep_pairs")
+    best_p = min(pair_ms, key=pair_ms.get)
+    xtn.tune_set(P, best_p)
+    r = {"records_cfg": best_r, "pairs_cfg": best_p,
+         "pair_capacity": max(65536, int(cands * 1.25)),
+         "sort_ms": {"records": rec_ms[best_r], "pairs": pair_ms[best_p]}}
+    if use_cache:
+        cache[key] = r
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            json.dump(cache, open(path, "w"), indent=1)
+        except OSError:
+            pass
+    return r

@@ -998,6 +998,25 @@ int xtn_plan_info(const xtn_plan* plan, int64_t* record_capacity, int64_t* pair_
   return XTN_OK;
 }
 
+int xtn_plan_stats(xtn_plan* plan, int64_t* records, int64_t* groups, int64_t* candidates,
+                   int64_t* survivors, xtn_stream_t stream) {
+  if (!plan) return XTN_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t h[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(&h[0], plan->rec_off + plan->n, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&h[1], plan->counters, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&h[3], plan->back.counters, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return XTN_ERR_CUDA;
+  }
+  if (records) *records = (int64_t)h[0];
+  if (groups) *groups = (int64_t)h[1];
+  if (candidates) *candidates = (int64_t)h[2];
+  if (survivors) *survivors = (int64_t)h[3];
+  return XTN_OK;
+}
+
 int xtn_plan_free(xtn_plan* plan) {
   delete plan;
   return XTN_OK;

@@ -48,6 +48,7 @@ SIGNATURES = {
     "xtn_plan_run": (_I, [_P, _P, _P]),
     "xtn_plan_result": (_I, [_P, _P, _I64, _P, _P]),
     "xtn_plan_info": (_I, [_P, _P, _P, _P]),
+    "xtn_plan_stats": (_I, [_P, _P, _P, _P, _P, _P]),
     "xtn_plan_free": (_I, [_P]),
     "xtn_tune_set": (_I, [_I, _I]),
     "xtn_tune_get": (_I, [_I]),

@@ -139,6 +139,14 @@ class Plan:
                                          ctypes.byref(nb)), "xtn_plan_info")
         return {"record_capacity": rc.value, "pair_capacity": pc.value, "device_bytes": nb.value}
 
+    def stats(self, stream=None):
+        """Counts of the last run: records, groups, candidates, survivors."""
+        v = [ctypes.c_int64(0) for _ in range(4)]
+        st = ctypes.c_void_p(stream) if stream is not None else _stream(None)
+        check(native.lib().xtn_plan_stats(self._h, *[ctypes.byref(x) for x in v], st),
+              "xtn_plan_stats")
+        return dict(zip(["records", "groups", "candidates", "survivors"], [x.value for x in v]))
+
     def run(self, seqs, stream=None) -> None:
         """Queue a search over device-resident `seqs` (torch CUDA tensor)."""
         sp, sk, on_dev = _ptr(seqs, np.uint8)
