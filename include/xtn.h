@@ -233,11 +233,15 @@ XTN_API int xtn_tcrdist_filter_noalloc(const uint8_t* seqs, const int64_t* offse
  *                           records (0 .. xtn_tune_count(knob)-1)
  *   XTN_TUNE_SORT_PAIRS   : tile configuration of the radix sort of verified
  *                           pair words
- * Every configuration gives the same result; they differ in threads per
- * block, keys per thread and ranking method, hence in speed per GPU and size.
+ *   XTN_TUNE_RECORD_HISTOGRAM : where the record sort's digit counts are
+ *                           taken: 0 = the expand kernel counts the digits
+ *                           of every pass, 1 = expand counts the first pass
+ *                           and each sort pass counts the next
+ * Every value gives the same result; they differ in threads per block, keys
+ * per thread, ranking method and counting, hence in speed per GPU and size.
  * xtn_tune_set returns XTN_ERR_INVALID_ARG for an unknown knob or value.
  */
-enum { XTN_TUNE_SORT_RECORDS = 0, XTN_TUNE_SORT_PAIRS = 1 };
+enum { XTN_TUNE_SORT_RECORDS = 0, XTN_TUNE_SORT_PAIRS = 1, XTN_TUNE_RECORD_HISTOGRAM = 2 };
 XTN_API int xtn_tune_set(int knob, int value);
 XTN_API int xtn_tune_get(int knob);
 XTN_API int xtn_tune_count(int knob);

@@ -1,7 +1,9 @@
 """Autotuner for the planned (batched) self-search.
 
-Picks, by timing on the caller's own data, the tile configuration of each
-radix sort (variant records and verified pairs; see xtn_tune_set) and a
+Picks, by timing on the caller's own data, where the record sort's digit
+counts are taken (in the expand kernel, or one pass ahead in each sort pass),
+the tile configuration of each radix sort (variant records and verified
+pairs; see xtn_tune_set) and a
 candidate-pair capacity for the plan (measured candidates x 1.25, so a plan
 holds no more pair memory than it needs).  The pipeline splits large buckets
 of shared variants at the granularity of its emit tiles whatever their size,
@@ -33,7 +35,8 @@ def _key(n, n_rep, d):
 def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int = 2,
          use_cache: bool = True) -> dict:
     """Time every sort configuration on this workload and apply the fastest.
-    Returns {"records_cfg", "pairs_cfg", "pair_capacity", "sort_ms": {...}}."""
+    Returns {"record_hist", "records_cfg", "pairs_cfg", "pair_capacity",
+    "sort_ms": {...}}."""
     n = int(offsets.shape[0]) - 1
     n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
     key = _key(n, n_rep, d)
@@ -46,14 +49,16 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
             cache = {}
     if use_cache and key in cache:
         r = cache[key]
+        xtn.tune_set(native.XTN_TUNE_RECORD_HISTOGRAM, r.get("record_hist", 0))
         xtn.tune_set(native.XTN_TUNE_SORT_RECORDS, r["records_cfg"])
         xtn.tune_set(native.XTN_TUNE_SORT_PAIRS, r["pairs_cfg"])
         return r
     import torch
-    R, P = native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS
+    R, P, H = (native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS,
+               native.XTN_TUNE_RECORD_HISTOGRAM)
     configs = list(range(xtn.tune_count(R))) if configs is None else list(configs)
 
-    def measure(kernel):
+    def measure(*kernels):
         plan = xtn.Plan(offsets, d, rep_offsets=rep_offsets)
         plan.run(seqs_dev)                       # warm-up
         torch.cuda.synchronize()
@@ -66,9 +71,15 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
         prof = xtn.profile_report()
         stats = plan.stats()
         plan.free()
-        launches, ms, _ = prof.get(kernel, (1, float("inf"), 0))
+        ms = sum(prof.get(k, (1, float("inf"), 0))[1] for k in kernels)
         return ms / repeats, stats
 
+    hist_ms = {}
+    for h in range(xtn.tune_count(H)):
+        xtn.tune_set(H, h)
+        hist_ms[h], _ = measure("k_expand", "k_onesweep_records")
+    best_h = min(hist_ms, key=hist_ms.get)
+    xtn.tune_set(H, best_h)
     rec_ms, pair_ms = {}, {}
     cands = 0
     for c in configs:
@@ -82,7 +93,7 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
         pair_ms[c], _ = measure("k_onesweep_pairs")
     best_p = min(pair_ms, key=pair_ms.get)
     xtn.tune_set(P, best_p)
-    r = {"records_cfg": best_r, "pairs_cfg": best_p,
+    r = {"record_hist": best_h, "records_cfg": best_r, "pairs_cfg": best_p,
          "pair_capacity": max(65536, int(cands * 1.25)),
          "sort_ms": {"records": rec_ms[best_r], "pairs": pair_ms[best_p]}}
     if use_cache:

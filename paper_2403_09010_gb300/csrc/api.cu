@@ -175,6 +175,10 @@ int choose_hash_bits(uint64_t n_rec, uint32_t id_bits) {
 // Tunables (set by the autotuner through xtn_tune_set).
 std::atomic<int> g_cfg_records{9};
 std::atomic<int> g_cfg_pairs{9};
+// Where the record sort's digit counts come from: 0 = the expand kernel
+// counts every pass's digit, 1 = expand counts the first and each sort pass
+// counts the next one.
+std::atomic<int> g_record_hist{0};
 }  // namespace
 std::atomic<int>& cfg_records() { return g_cfg_records; }
 std::atomic<int>& cfg_pairs() { return g_cfg_pairs; }
@@ -274,6 +278,22 @@ struct Sorted {
   int hs = 0;
 };
 
+// Expand records into A and sort them by fingerprint; `hist_mode` is the
+// record histogram placement (see g_record_hist).
+int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
+                       const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
+                       int id_bits, uint64_t* A, uint64_t* B, uint64_t rec_cap, int lo,
+                       uint32_t* hist, uint64_t* digit_base, uint64_t* status, int cfg,
+                       int hist_mode, int sms, uint32_t* err, cudaStream_t s,
+                       const uint64_t* n_rec_dev, uint64_t** sorted) {
+  const bool in_passes = hist_mode == 1;
+  launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, lo,
+                in_passes ? std::min(64, lo + 8) : 64, sms, err, s);
+  XTN_CK(cudaGetLastError());
+  return radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
+                           sorted, "k_onesweep_records", s, in_passes, n_rec_dev);
+}
+
 int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep, int sms,
                     Arena& ar, uint32_t* err, cudaStream_t s, Sorted* out) {
   const uint64_t n_rec = e.n_rec;
@@ -288,13 +308,10 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
   uint64_t* status = ar.get<uint64_t>(radix_status_bytes(n_rec, cfg) / 8 + 1);
   XTN_ALLOC_OK(ar);
   XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
-  // expand counts the first pass's digits; each sort pass counts the next
-  launch_expand(e.keys, e.lens, e.eqprev, e.rec_off, n, d, seq_rep, out->id_bits, A, n_rec, hist,
-                lo, std::min(64, lo + 8), sms, err, s);
-  XTN_CK(cudaGetLastError());
   uint64_t* sorted = nullptr;
-  XTN_CK(radix_sort_passes(A, B, (int64_t)n_rec, lo, 64, hist, digit_base, status, cfg, err,
-                           &sorted, "k_onesweep_records", s, true));
+  XTN_CK(expand_sort_launch(e.keys, e.lens, e.eqprev, e.rec_off, n, d, seq_rep, out->id_bits, A,
+                            B, n_rec, lo, hist, digit_base, status, cfg, g_record_hist.load(),
+                            sms, err, s, nullptr, &sorted));
   out->rec = sorted;
   out->spare = sorted == A ? B : A;
   return XTN_OK;
@@ -711,7 +728,7 @@ struct xtn_plan {
   int64_t n = 0;
   uint64_t rec_cap = 0, pair_cap = 0, g_cap = 0;
   uint32_t id_bits = 0;
-  int hs = 0, cfg_rec = 0, cfg_pair = 0, sms = 0;
+  int hs = 0, cfg_rec = 0, cfg_pair = 0, hist_mode = 0, sms = 0;
   std::vector<void*> allocs;
   int64_t bytes = 0;
   int64_t* off = nullptr;
@@ -785,6 +802,7 @@ int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* re
   p->hs = choose_hash_bits(rec_cap, p->id_bits);
   p->cfg_rec = g_cfg_records.load();
   p->cfg_pair = g_cfg_pairs.load();
+  p->hist_mode = g_record_hist.load();
   const size_t st = std::max({radix_status_bytes((int64_t)rec_cap, p->cfg_rec),
                               group_status_bytes((int64_t)rec_cap),
                               scan_status_bytes((int64_t)p->g_cap), scan_status_bytes(n)});
@@ -856,13 +874,12 @@ int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
   XTN_CK(cudaMemsetAsync(p->hist, 0, MAX_PASSES * RADIX * 4, s));
   launch_encode(seqs, p->off, n, p->d, p->keys, p->lens, p->eqprev, p->vcount, p->err, s);
   launch_scan_counts(p->vcount, n, p->rec_off, p->status, p->err, s);
-  launch_expand(p->keys, p->lens, p->eqprev, p->rec_off, n, p->d, p->seq_rep, p->id_bits, p->A,
-                p->rec_cap, p->hist, lo, std::min(64, lo + 8), p->sms, p->err, s);
   uint64_t* sorted = nullptr;
   const uint64_t* n_rec = p->rec_off + n;  // known on the device only
-  XTN_CK(radix_sort_passes(p->A, p->B, (int64_t)p->rec_cap, lo, 64, p->hist, p->digit_base,
-                           p->status, p->cfg_rec, p->err, &sorted, "k_onesweep_records", s, true,
-                           n_rec));
+  XTN_CK(expand_sort_launch(p->keys, p->lens, p->eqprev, p->rec_off, n, p->d, p->seq_rep,
+                            p->id_bits, p->A, p->B, p->rec_cap, lo, p->hist, p->digit_base,
+                            p->status, p->cfg_rec, p->hist_mode, p->sms, p->err, s, n_rec,
+                            &sorted));
   if (sorted != p->sorted) return XTN_ERR_CUDA;
   launch_group_bounds(sorted, (int64_t)p->rec_cap, n_rec, lo, p->S, p->E, p->g_cap, p->flags,
                       p->status, p->err, p->counters, s);
@@ -1023,8 +1040,9 @@ int xtn_plan_free(xtn_plan* plan) {
 }
 
 int xtn_tune_set(int knob, int value) {
-  if (value < 0 || value >= xtn::onesweep_configs()) return XTN_ERR_INVALID_ARG;
+  if (value < 0 || value >= xtn_tune_count(knob)) return XTN_ERR_INVALID_ARG;
   switch (knob) {
+    case XTN_TUNE_RECORD_HISTOGRAM: xtn::g_record_hist.store(value); return XTN_OK;
     case XTN_TUNE_SORT_RECORDS: xtn::cfg_records().store(value); return XTN_OK;
     case XTN_TUNE_SORT_PAIRS: xtn::cfg_pairs().store(value); return XTN_OK;
   }
@@ -1035,13 +1053,18 @@ int xtn_tune_get(int knob) {
   switch (knob) {
     case XTN_TUNE_SORT_RECORDS: return xtn::cfg_records().load();
     case XTN_TUNE_SORT_PAIRS: return xtn::cfg_pairs().load();
+    case XTN_TUNE_RECORD_HISTOGRAM: return xtn::g_record_hist.load();
   }
   return XTN_ERR_INVALID_ARG;
 }
 
 int xtn_tune_count(int knob) {
-  return (knob == XTN_TUNE_SORT_RECORDS || knob == XTN_TUNE_SORT_PAIRS) ? xtn::onesweep_configs()
-                                                                          : XTN_ERR_INVALID_ARG;
+  switch (knob) {
+    case XTN_TUNE_SORT_RECORDS:
+    case XTN_TUNE_SORT_PAIRS: return xtn::onesweep_configs();
+    case XTN_TUNE_RECORD_HISTOGRAM: return 2;
+  }
+  return XTN_ERR_INVALID_ARG;
 }
 
 int xtn_profile_enable(int on) {

@@ -94,6 +94,24 @@ __device__ __forceinline__ void rank_items(const uint64_t (&key)[ITEMS], uint16_
                                            uint32_t* wh, uint32_t* mb, int64_t wbase, int64_t n,
                                            int shift, uint32_t dmask, uint32_t lane) {
   const uint32_t lt_mask = (1u << lane) - 1u;
+  if (MATCH == 3) {
+    // ballot match; the lowest peer adds the group's size to the warp counter
+    // with one shared atomic and hands the old count to its peers
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool valid = FULL || (wbase + i * 32 + lane < n);
+      const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
+      const uint32_t vmask = FULL ? FULL_MASK : __ballot_sync(FULL_MASK, valid);
+      const uint32_t peers = digit_peers<0>(dig, vmask);
+      const uint32_t before = peers & lt_mask;
+      uint32_t old = 0;
+      if (valid && before == 0) old = atomicAdd(&wh[dig], (uint32_t)__popc(peers));
+      old = __shfl_sync(FULL_MASK, old, valid ? __ffs(peers) - 1 : (int)lane);
+      rank[i] = (uint16_t)(old + __popc(before));
+      __syncwarp();  // this item's counter update is seen by the next item
+    }
+    return;
+  }
   if (MATCH == 2) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -209,16 +227,15 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   if (next_hist)
     for (int k = threadIdx.x; k < RADIX; k += THREADS) s_next[k] = 0;
   // key count: on the device when the caller did not know it at launch time
-  // (grid sized for n_cap; tiles past the count leave at once)
+  // (grid sized for n_cap; blocks whose tile starts past the count leave at
+  // once -- tiles are numbered in start order, so no live tile waits on them)
   const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
-  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  const uint32_t dmask = (1u << bits) - 1u;
-  // persistent: every block takes tiles in start order until the keys run out
-  for (;;) {
   const uint32_t tile = tile_id(ctr, &s_tile);
   const int64_t tile_base = (int64_t)tile * TILE;
-  if (tile_base >= n) break;
+  if (tile_base >= n) return;
   const bool full = tile_base + TILE <= n;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t dmask = (1u << bits) - 1u;
 
   for (int k = threadIdx.x; k < NCHAIN * WARPS * RADIX; k += THREADS) s_whist[k] = 0;
   if (MATCH == 2)
@@ -287,20 +304,22 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     if (threadIdx.x < RADIX) {
       uint32_t off = 0;
       for (uint32_t w = 0; w < warp; ++w) off += s_wsum[w];
-      s_tstart[threadIdx.x] = off + inc - v;
+      const uint32_t ts = off + inc - v;
+      s_tstart[threadIdx.x] = ts;
+      // per-warp offsets become absolute positions in the tile's digit order
+#pragma unroll
+      for (int w = 0; w < NCHAIN * WARPS; ++w) s_whist[w * RADIX + threadIdx.x] += ts;
     }
     __syncthreads();
   }
 
-  // 4. scatter into shared memory in digit order (and count the next digit)
-  const uint32_t nmask = (1u << next_bits) - 1u;
+  // 4. scatter into shared memory in digit order
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     if (full || wbase + i * 32 + lane < n) {
       const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
-      if (next_hist) atomicAdd(&s_next[(uint32_t)(key[i] >> (shift + 8)) & nmask], 1u);
       const uint32_t* whi = (NCHAIN == 2 && i >= ITEMS / 2) ? whB : wh;
-      s_keys[s_tstart[dig] + whi[dig] + rank[i]] = key[i];
+      s_keys[whi[dig] + rank[i]] = key[i];
     }
   }
 
@@ -315,23 +334,27 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
   __syncthreads();
 
-  // 6. write out in digit order
+  // 6. write out in digit order (and count the next pass's digit: the keys
+  // pass through registers here anyway, and the ranking above has none to spare)
   const int tile_n = full ? TILE : (int)(n - tile_base);
   for (int j = threadIdx.x; j < tile_n; j += THREADS) {
     const uint64_t k = s_keys[j];
     const uint32_t dig = (uint32_t)(k >> shift) & dmask;
+    if (next_hist) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
     const int64_t o = s_obase[dig] + j;
     if (o >= 0 && o < n) out[o] = k;
     else atomicOr(err, DERR_RANGE);
   }
-  __syncthreads();  // shared staging is reused by the next tile
+  if (next_hist) {  // uniform over the block
+    __syncthreads();  // every count of the write loop is in
+    if (threadIdx.x < RADIX && s_next[threadIdx.x])
+      atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
   }
-  if (next_hist && threadIdx.x < RADIX && s_next[threadIdx.x])
-    atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
 }
 
 // Tile configurations (id, threads, items per thread, min blocks per SM,
-// ranking: 0 ballots / 1 match.any / 2 atomic-OR bins, ranking chains).  Both sorts use configuration 9 by
+// ranking: 0 ballots / 1 match.any / 2 atomic-OR bins / 3 ballots with one
+// leader atomic per group, ranking chains).  Both sorts use configuration 9 by
 // default; the autotuner may pick others.
 #define XTN_ONESWEEP_CONFIGS(X) \
   X(0, 256, 16, 3, 0, 1)           \
@@ -349,7 +372,11 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   X(12, 256, 20, 3, 2, 2)       \
   X(13, 256, 16, 3, 2, 2)       \
   X(14, 256, 20, 3, 0, 2)       \
-  X(15, 256, 12, 4, 0, 2)
+  X(15, 256, 12, 4, 0, 2)       \
+  X(16, 256, 20, 3, 3, 1)       \
+  X(17, 256, 16, 3, 3, 1)       \
+  X(18, 256, 24, 2, 3, 1)       \
+  X(19, 512, 12, 2, 3, 1)
 
 int onesweep_tile(int cfg) {
   switch (cfg) {
@@ -361,21 +388,7 @@ int onesweep_tile(int cfg) {
   return 0;
 }
 
-int onesweep_configs() { return 16; }
-
-// Multiprocessor count of the current device (cached per device).
-static int device_sms() {
-  static int cache[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 1;
-  if (!cache[dev]) {
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cache[dev] = v > 0 ? v : 1;
-  }
-  return cache[dev];
-}
+int onesweep_configs() { return 20; }
 
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    const uint64_t* n_dev, int shift, int bits, const uint64_t* digit_base,
@@ -392,10 +405,8 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
       cudaFuncSetAttribute(k_onesweep<T, I, B, M, C>,                                            \
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
     });                                                                                       \
-    /* a count known only on the device: persistent grid; else one tile per block */        \
-    const uint32_t tiles = n_dev ? std::min<uint32_t>(div_up_u32(n, SM::TILE),               \
-                                                      (uint32_t)(device_sms() * B))           \
-                                 : div_up_u32(n, SM::TILE);                                   \
+    /* one tile per block; with the count on the device, n is its capacity */                \
+    const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
     k_onesweep<T, I, B, M, C><<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits,        \
                                                           digit_base,                         \
                                                        status, ctr, err, next_hist,           \

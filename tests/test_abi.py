@@ -72,3 +72,20 @@ def test_argument_checks_before_device_work(lib):
     assert lib.xtn_index_free(None) == native.XTN_OK
     assert lib.xtn_index_info(None, None, None, None, None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_tcrdist_filter(seq, off, 1, None, 0, 24, None, ctypes.byref(n_out), None) == native.XTN_OK
+
+
+def test_tuning_knobs(lib):
+    R, P, H = native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS, native.XTN_TUNE_RECORD_HISTOGRAM
+    assert lib.xtn_tune_count(H) == 2
+    assert lib.xtn_tune_count(R) == lib.xtn_tune_count(P) > 0
+    assert lib.xtn_tune_count(99) == native.XTN_ERR_INVALID_ARG
+    for knob in (R, P, H):
+        old = lib.xtn_tune_get(knob)
+        assert 0 <= old < lib.xtn_tune_count(knob)
+        assert lib.xtn_tune_set(knob, lib.xtn_tune_count(knob)) == native.XTN_ERR_INVALID_ARG
+        assert lib.xtn_tune_set(knob, -1) == native.XTN_ERR_INVALID_ARG
+        assert lib.xtn_tune_get(knob) == old
+        last = lib.xtn_tune_count(knob) - 1
+        assert lib.xtn_tune_set(knob, last) == native.XTN_OK and lib.xtn_tune_get(knob) == last
+        assert lib.xtn_tune_set(knob, old) == native.XTN_OK
+    assert lib.xtn_tune_set(99, 0) == native.XTN_ERR_INVALID_ARG

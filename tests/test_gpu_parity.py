@@ -143,21 +143,30 @@ def test_input_errors(xtn):
 
 
 def test_every_sort_configuration(xtn):
-    R, P = xtn.XTN_TUNE_SORT_RECORDS, xtn.XTN_TUNE_SORT_PAIRS
-    default = (xtn.tune_get(R), xtn.tune_get(P))
+    R, P, H = xtn.XTN_TUNE_SORT_RECORDS, xtn.XTN_TUNE_SORT_PAIRS, xtn.XTN_TUNE_RECORD_HISTOGRAM
+    default = (xtn.tune_get(R), xtn.tune_get(P), xtn.tune_get(H))
     seqs, off = gen.workload(gen.SELF_1M, 60_000)
     want = oracle.symdel_self(seqs, off, 2)
     small_s, small_o = gen.generate(777, 4, 0.5, 0.1)
     small_want = oracle.symdel_self(small_s, small_o, 2)
     try:
-        for cfg in range(xtn.tune_count(R)):
-            xtn.tune_set(R, cfg)
-            xtn.tune_set(P, cfg)
-            assert np.array_equal(_rows(xtn.search_self(seqs, off, 2)), want), cfg
-            assert np.array_equal(_rows(xtn.search_self(small_s, small_o, 2)), small_want), cfg
+        for h in range(xtn.tune_count(H)):
+            xtn.tune_set(H, h)
+            for cfg in range(xtn.tune_count(R)):
+                xtn.tune_set(R, cfg)
+                xtn.tune_set(P, cfg)
+                assert np.array_equal(_rows(xtn.search_self(seqs, off, 2)), want), (h, cfg)
+                assert np.array_equal(_rows(xtn.search_self(small_s, small_o, 2)),
+                                      small_want), (h, cfg)
+            # the planned path takes the knobs at plan creation
+            plan = xtn.Plan(off, 2)
+            plan.run(torch.from_numpy(seqs).cuda())
+            assert np.array_equal(_rows(plan.result()), want), h
+            plan.free()
     finally:
         xtn.tune_set(R, default[0])
         xtn.tune_set(P, default[1])
+        xtn.tune_set(H, default[2])
 
 
 # --------------------------------------------------------------- batched ---
