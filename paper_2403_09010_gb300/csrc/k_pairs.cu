@@ -4,13 +4,14 @@
 //                    of per-sequence variant counts -> record offsets, and of
 //                    per-group pair counts -> pair offsets (the paper's
 //                    `cumulativeSum`).
-//   k_group_bounds : on the sorted records, a group is a run of equal
+//   group bounds   : on the sorted records, a group is a run of equal
 //                    fingerprints (the paper's `uniqueCount`).  Only groups of
 //                    two or more records can yield pairs; their first and
-//                    last positions are compacted into S[] and E[] in one read
-//                    of the records.  The k-th group start and the k-th group
-//                    end describe the same group, so no thread ever walks a
-//                    group, however large.
+//                    last positions are compacted into S[] and E[] with one
+//                    read of the records (k_group_flags, k_group_write below).
+//                    The k-th group start and the k-th group end describe the
+//                    same group, so no thread ever walks a group, however
+//                    large.
 //   k_emit_pairs   : the `expand` of step 5.  Group k owns C(E-S+1, 2) output
 //                    slots; output slot t finds its group by binary search over
 //                    the pair offsets (staged in shared memory per tile), turns

@@ -6,12 +6,14 @@
 //              (Appendix "Compression of TCR sequences"), its length, the
 //              mask of positions equal to their left neighbour, and its
 //              number of canonical deletion subsets (see is_canonical).
-//   k_expand : one warp per sequence; lane v takes canonical variant v (see
-//              variants.cuh), fingerprints it from the prefix sums and writes
-//              the 64-bit record  fingerprint[63:b] | id[b-1:0]  at
-//              rec_off[s] + v, so every warp store is one contiguous run.  The
-//              kernel also accumulates the digit histograms of every radix
-//              pass that will sort the records.
+//   k_expand : one warp per sequence (metadata of 32 sequences fetched at
+//              once); lane v takes canonical variant v (see variants.cuh),
+//              fingerprints it from the prefix sums and writes the 64-bit
+//              record  fingerprint[63:b] | id[b-1:0]  at rec_off[s] + v, so
+//              every warp store is one contiguous run.  The kernel also
+//              accumulates the digit histograms of the radix passes that will
+//              sort the records (all of them, or only the first when each
+//              sort pass counts the next).
 //   k_peq    : per sequence, for each residue code c, the bit mask of the
 //              positions holding c (the match vectors of the bit-parallel
 //              edit distance used in verification).
