@@ -237,11 +237,23 @@ XTN_API int xtn_tcrdist_filter_noalloc(const uint8_t* seqs, const int64_t* offse
  *                           taken: 0 = the expand kernel counts the digits
  *                           of every pass, 1 = expand counts the first pass
  *                           and each sort pass counts the next
+ *   XTN_TUNE_GROUPING     : how records are grouped: 0 = global radix passes
+ *                           on the top bits only, then one shared-memory pass
+ *                           per block of buckets that finishes the sort and
+ *                           writes the group flags (default); 1 = global
+ *                           passes on every bit, then a flag pass; 2 = as 0
+ *                           with 512-record shared-memory segments (slower;
+ *                           more buckets take the large-bucket path)
  * Every value gives the same result; they differ in threads per block, keys
  * per thread, ranking method and counting, hence in speed per GPU and size.
  * xtn_tune_set returns XTN_ERR_INVALID_ARG for an unknown knob or value.
  */
-enum { XTN_TUNE_SORT_RECORDS = 0, XTN_TUNE_SORT_PAIRS = 1, XTN_TUNE_RECORD_HISTOGRAM = 2 };
+enum {
+  XTN_TUNE_SORT_RECORDS = 0,
+  XTN_TUNE_SORT_PAIRS = 1,
+  XTN_TUNE_RECORD_HISTOGRAM = 2,
+  XTN_TUNE_GROUPING = 3
+};
 XTN_API int xtn_tune_set(int knob, int value);
 XTN_API int xtn_tune_get(int knob);
 XTN_API int xtn_tune_count(int knob);

@@ -179,6 +179,11 @@ std::atomic<int> g_cfg_pairs{9};
 // counts every pass's digit, 1 = expand counts the first and each sort pass
 // counts the next one.
 std::atomic<int> g_record_hist{0};
+// How records are grouped: 0 = global radix passes on the top bucket bits,
+// then k_bucket_sort (shared-memory finish + group flags); 1 = global passes
+// on every group-key bit, then k_group_flags; 2 = as 0 with 512-record
+// shared-memory segments (more buckets take the large-bucket path).
+std::atomic<int> g_grouping{0};
 }  // namespace
 std::atomic<int>& cfg_records() { return g_cfg_records; }
 std::atomic<int>& cfg_pairs() { return g_cfg_pairs; }
@@ -274,28 +279,88 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
 struct Sorted {
   uint64_t* rec = nullptr;
   uint64_t* spare = nullptr;
+  uint64_t* flags = nullptr;    // group flags (when asked for)
+  uint64_t* gstatus = nullptr;  // group-bound scratch holding the flag tile counts
   uint32_t id_bits = 0;
   int hs = 0;
 };
 
-// Expand records into A and sort them by fingerprint; `hist_mode` is the
-// record histogram placement (see g_record_hist).
+// Scratch of the grouping sort.  bucket_start: 2^G + 1 entries (bucket
+// modes); flags + gstatus: group flags and group-bound scratch (when null, no
+// flags are made: the caller only wants sorted records).
+struct GroupScratch {
+  uint64_t* bucket_start = nullptr;
+  uint64_t* flags = nullptr;
+  uint64_t* gstatus = nullptr;
+};
+
+size_t bucket_start_words(uint64_t rec_cap, int hs, int mode) {
+  if (mode == 1) return 1;
+  return ((size_t)1 << choose_grouping(rec_cap, hs, true).G) + 1;
+}
+
+// Which of A / B receives the grouped records for this mode and size.
+bool sorted_in_b(uint64_t rec_cap, int hs, int mode) {
+  if (mode == 1) return ((hs + 7) / 8) % 2 == 1;
+  return ((choose_grouping(rec_cap, hs, true).G / 8) % 2) == 0;
+}
+
+// Expand records into A and group them on their hs group-key bits
+// (lo = 64 - hs).  With gs.flags (self-search) the records of each group end
+// up contiguous and the group flags are written; without (reference index)
+// the records end up sorted.  `hist_mode` is the record histogram placement
+// (see g_record_hist), `mode` the grouping mode (see g_grouping).  *sorted
+// receives A or B.
 int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
                        const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
                        int id_bits, uint64_t* A, uint64_t* B, uint64_t rec_cap, int lo,
                        uint32_t* hist, uint64_t* digit_base, uint64_t* status, int cfg,
-                       int hist_mode, int sms, uint32_t* err, cudaStream_t s,
-                       const uint64_t* n_rec_dev, uint64_t** sorted) {
-  const bool in_passes = hist_mode == 1;
-  launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, lo,
-                in_passes ? std::min(64, lo + 8) : 64, sms, err, s);
+                       int hist_mode, int mode, const GroupScratch& gs, int sms, uint32_t* err,
+                       cudaStream_t s, const uint64_t* n_rec_dev, uint64_t** sorted) {
+  if (mode == 1) {
+    const bool in_passes = hist_mode == 1;
+    launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, lo,
+                  in_passes ? std::min(64, lo + 8) : 64, sms, err, s);
+    XTN_CK(cudaGetLastError());
+    XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
+                             sorted, "k_onesweep_records", s, in_passes, n_rec_dev));
+    if (gs.flags) {
+      XTN_CK(cudaMemsetAsync(gs.gstatus, 0, group_status_bytes((int64_t)rec_cap), s));
+      launch_group_flags(*sorted, (int64_t)rec_cap, n_rec_dev, lo, gs.flags, gs.gstatus, s);
+    }
+    return XTN_OK;
+  }
+  const bool hash = gs.flags != nullptr;
+  const GroupingShape g = choose_grouping(rec_cap, 64 - lo, hash);
+  const int glo = 64 - g.G;  // global passes sort bits [glo, 64)
+  const bool in_passes = hist_mode == 1 && g.G > 8;
+  if (g.G > 0)
+    XTN_CK(cudaMemsetAsync(gs.bucket_start, 0xFF, ((size_t)1 << g.G) * 8, s));
+  launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, glo,
+                g.G == 0 ? glo : (in_passes ? glo + 8 : 64), sms, err, s);
   XTN_CK(cudaGetLastError());
-  return radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
-                           sorted, "k_onesweep_records", s, in_passes, n_rec_dev);
+  uint64_t* X = A;
+  XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, glo, 64, hist, digit_base, status, cfg, err,
+                           &X, "k_onesweep_records", s, in_passes, n_rec_dev, gs.bucket_start));
+  uint64_t* Y = X == A ? B : A;
+  uint64_t* tile_counts = nullptr;
+  if (gs.flags) {
+    XTN_CK(cudaMemsetAsync(gs.flags, 0, group_flag_words((int64_t)rec_cap) * 8, s));
+    XTN_CK(cudaMemsetAsync(gs.gstatus, 0, group_status_bytes((int64_t)rec_cap), s));
+    tile_counts = group_tile_counts(gs.gstatus, (int64_t)rec_cap);
+  }
+  launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo,
+                mode == 2 ? 512 : 0, gs.flags, tile_counts, err, s);
+  XTN_CK(cudaGetLastError());
+  *sorted = Y;
+  return XTN_OK;
 }
 
+// want_flags: also make the group flags (out->flags, out->gstatus, the latter
+// sized for the group-bound and group-pair scans of up to g_cap groups).
 int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep, int sms,
-                    Arena& ar, uint32_t* err, cudaStream_t s, Sorted* out) {
+                    Arena& ar, uint32_t* err, cudaStream_t s, Sorted* out,
+                    bool want_flags = false, uint64_t g_cap = 0) {
   const uint64_t n_rec = e.n_rec;
   out->id_bits = bits_for((uint64_t)n);
   out->hs = choose_hash_bits(n_rec, out->id_bits);
@@ -306,12 +371,22 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
   uint32_t* hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
   uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
   uint64_t* status = ar.get<uint64_t>(radix_status_bytes(n_rec, cfg) / 8 + 1);
+  const int mode = g_grouping.load();
+  GroupScratch gs;
+  gs.bucket_start = ar.get<uint64_t>(bucket_start_words(n_rec, out->hs, mode));
+  if (want_flags) {
+    gs.flags = ar.get<uint64_t>(group_flag_words((int64_t)n_rec));
+    gs.gstatus = ar.get<uint64_t>(
+        std::max(group_status_bytes((int64_t)n_rec), scan_status_bytes((int64_t)g_cap)) / 8 + 1);
+  }
   XTN_ALLOC_OK(ar);
   XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
   uint64_t* sorted = nullptr;
   XTN_CK(expand_sort_launch(e.keys, e.lens, e.eqprev, e.rec_off, n, d, seq_rep, out->id_bits, A,
-                            B, n_rec, lo, hist, digit_base, status, cfg, g_record_hist.load(),
-                            sms, err, s, nullptr, &sorted));
+                            B, n_rec, lo, hist, digit_base, status, cfg, g_record_hist.load(), mode,
+                            gs, sms, err, s, nullptr, &sorted));
+  out->flags = gs.flags;
+  out->gstatus = gs.gstatus;
   out->rec = sorted;
   out->spare = sorted == A ? B : A;
   return XTN_OK;
@@ -452,19 +527,15 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   rc = encode_and_count(in, d, ar, err, s, &e);
   if (rc) return rc;
   Sorted so;
-  rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so);
-  if (rc) return rc;
   const uint64_t g_cap = e.n_rec / 2 + 1;
+  rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so, true, g_cap);
+  if (rc) return rc;
   uint32_t* S = reinterpret_cast<uint32_t*>(so.spare);  // groups live in the spare buffer
   uint32_t* E = S + g_cap;
   uint64_t* pair_off = reinterpret_cast<uint64_t*>(E + g_cap);  // 8-byte aligned
-  const size_t st = std::max(group_status_bytes(e.n_rec), scan_status_bytes(g_cap));
-  uint64_t* status = ar.get<uint64_t>(st / 8 + 1);
-  uint64_t* flags = ar.get<uint64_t>(group_flag_words((int64_t)e.n_rec));
-  XTN_ALLOC_OK(ar);
-  launch_group_bounds(so.rec, (int64_t)e.n_rec, nullptr, 64 - so.hs, S, E, g_cap, flags, status,
-                      err, counters, s);
-  launch_scan_group_pairs(S, E, (int64_t)g_cap, counters, pair_off, status, err, s);
+  launch_group_finish(so.flags, (int64_t)e.n_rec, nullptr, S, E, g_cap, so.gstatus, err, counters,
+                      s);
+  launch_scan_group_pairs(S, E, (int64_t)g_cap, counters, pair_off, so.gstatus, err, s);
   k_pair_total<<<1, 1, 0, s>>>(pair_off, counters, counters + 1);
   XTN_CK(cudaGetLastError());
   struct {
@@ -728,7 +799,8 @@ struct xtn_plan {
   int64_t n = 0;
   uint64_t rec_cap = 0, pair_cap = 0, g_cap = 0;
   uint32_t id_bits = 0;
-  int hs = 0, cfg_rec = 0, cfg_pair = 0, hist_mode = 0, sms = 0;
+  int hs = 0, cfg_rec = 0, cfg_pair = 0, hist_mode = 0, group_mode = 0, sms = 0;
+  uint64_t* bucket_start = nullptr;
   std::vector<void*> allocs;
   int64_t bytes = 0;
   int64_t* off = nullptr;
@@ -803,6 +875,7 @@ int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* re
   p->cfg_rec = g_cfg_records.load();
   p->cfg_pair = g_cfg_pairs.load();
   p->hist_mode = g_record_hist.load();
+  p->group_mode = g_grouping.load();
   const size_t st = std::max({radix_status_bytes((int64_t)rec_cap, p->cfg_rec),
                               group_status_bytes((int64_t)rec_cap),
                               scan_status_bytes((int64_t)p->g_cap), scan_status_bytes(n)});
@@ -818,6 +891,7 @@ int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* re
   p->digit_base = p->alloc<uint64_t>(MAX_PASSES * RADIX);
   p->status = p->alloc<uint64_t>(st / 8 + 1);
   p->flags = p->alloc<uint64_t>(group_flag_words((int64_t)rec_cap));
+  p->bucket_start = p->alloc<uint64_t>(bucket_start_words(rec_cap, p->hs, p->group_mode));
   p->counters = p->alloc<uint64_t>(4);
   p->err = p->alloc<uint32_t>(4);
   p->peq = p->alloc<uint32_t>((size_t)n * PEQ_STRIDE);
@@ -831,16 +905,17 @@ int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* re
   if (rep_offsets) p->seq_rep = p->alloc<uint32_t>(n);
   bool ok = p->rows && p->back.counters && p->back.status && p->back.digit_base && p->back.hist &&
             p->back.P2 && p->back.P1 && p->peq && p->err && p->counters && p->flags && p->status &&
+            p->bucket_start &&
             p->digit_base && p->hist && p->B && p->A && p->rec_off && p->vcount && p->eqprev &&
             p->lens && p->keys && p->off && (!rep_offsets || p->seq_rep);
   if (!ok) {
     delete p;
     return XTN_ERR_OOM;
   }
-  // records end in A after an even number of passes; groups live in the other
-  const int passes = (p->hs + 7) / 8;
-  p->sorted = (passes % 2 == 0) ? p->A : p->B;
-  uint64_t* spare = (passes % 2 == 0) ? p->B : p->A;
+  // which buffer ends up sorted depends on the pass count; groups live in the other
+  const bool in_b = sorted_in_b(rec_cap, p->hs, p->group_mode);
+  p->sorted = in_b ? p->B : p->A;
+  uint64_t* spare = in_b ? p->A : p->B;
   p->S = reinterpret_cast<uint32_t*>(spare);
   p->E = p->S + p->g_cap;
   p->pair_off = reinterpret_cast<uint64_t*>(p->E + p->g_cap);
@@ -876,13 +951,17 @@ int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
   launch_scan_counts(p->vcount, n, p->rec_off, p->status, p->err, s);
   uint64_t* sorted = nullptr;
   const uint64_t* n_rec = p->rec_off + n;  // known on the device only
+  GroupScratch gs;
+  gs.bucket_start = p->bucket_start;
+  gs.flags = p->flags;
+  gs.gstatus = p->status;
   XTN_CK(expand_sort_launch(p->keys, p->lens, p->eqprev, p->rec_off, n, p->d, p->seq_rep,
                             p->id_bits, p->A, p->B, p->rec_cap, lo, p->hist, p->digit_base,
-                            p->status, p->cfg_rec, p->hist_mode, p->sms, p->err, s, n_rec,
-                            &sorted));
+                            p->status, p->cfg_rec, p->hist_mode, p->group_mode, gs, p->sms, p->err,
+                            s, n_rec, &sorted));
   if (sorted != p->sorted) return XTN_ERR_CUDA;
-  launch_group_bounds(sorted, (int64_t)p->rec_cap, n_rec, lo, p->S, p->E, p->g_cap, p->flags,
-                      p->status, p->err, p->counters, s);
+  launch_group_finish(p->flags, (int64_t)p->rec_cap, n_rec, p->S, p->E, p->g_cap, p->status,
+                      p->err, p->counters, s);
   launch_scan_group_pairs(p->S, p->E, (int64_t)p->g_cap, p->counters, p->pair_off, p->status,
                           p->err, s);
   launch_emit_pairs(sorted, p->rec_cap, p->S, p->pair_off, (int64_t)p->g_cap, p->counters,
@@ -1043,6 +1122,7 @@ int xtn_tune_set(int knob, int value) {
   if (value < 0 || value >= xtn_tune_count(knob)) return XTN_ERR_INVALID_ARG;
   switch (knob) {
     case XTN_TUNE_RECORD_HISTOGRAM: xtn::g_record_hist.store(value); return XTN_OK;
+    case XTN_TUNE_GROUPING: xtn::g_grouping.store(value); return XTN_OK;
     case XTN_TUNE_SORT_RECORDS: xtn::cfg_records().store(value); return XTN_OK;
     case XTN_TUNE_SORT_PAIRS: xtn::cfg_pairs().store(value); return XTN_OK;
   }
@@ -1054,6 +1134,7 @@ int xtn_tune_get(int knob) {
     case XTN_TUNE_SORT_RECORDS: return xtn::cfg_records().load();
     case XTN_TUNE_SORT_PAIRS: return xtn::cfg_pairs().load();
     case XTN_TUNE_RECORD_HISTOGRAM: return xtn::g_record_hist.load();
+    case XTN_TUNE_GROUPING: return xtn::g_grouping.load();
   }
   return XTN_ERR_INVALID_ARG;
 }
@@ -1063,6 +1144,7 @@ int xtn_tune_count(int knob) {
     case XTN_TUNE_SORT_RECORDS:
     case XTN_TUNE_SORT_PAIRS: return xtn::onesweep_configs();
     case XTN_TUNE_RECORD_HISTOGRAM: return 2;
+    case XTN_TUNE_GROUPING: return 3;
   }
   return XTN_ERR_INVALID_ARG;
 }

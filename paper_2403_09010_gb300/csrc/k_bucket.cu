@@ -1,0 +1,549 @@
+// Shared-memory finish of the grouping step, with the group flags (Appendix
+// A, XTNeighbor step 4: `sort` + `uniqueCount`).
+//
+// The global radix passes order the variant records by the top G bits of
+// their group key only; the records of one such value (a "bucket") are then
+// contiguous, and the last pass leaves the first position of every bucket
+// (radix_sort_passes, bucket_start).  Each block of k_bucket takes K
+// consecutive buckets -- one to two thousand records for the 1M workload --
+// and, in shared memory, brings the records of every group (equal group key)
+// together:
+//   HASH  (self-search): a hash table keyed by the composite key
+//         (bucket - first bucket of the block) << L | low L group-key bits
+//         numbers the groups; a counting scatter by table slot makes them
+//         contiguous.  Order inside a group and between groups is arbitrary:
+//         the pair emitter orders each pair itself.
+//   !HASH (reference index): stable LSD passes of 9-bit digits over the same
+//         composite key, i.e. exactly the array further global passes give.
+// Either way one read and one write of the records replace the remaining
+// global passes.  From the grouped block the kernel also writes the
+// head/tail flag words and per-tile head/tail counts that k_group_write
+// consumes, which replaces a separate flag pass over the records.
+//
+// A bucket with more records than a block holds (many copies of one
+// sequence) is sorted by the one block that owns it, in global memory: per
+// digit pass a histogram over the bucket, then stable ranking chunk by chunk,
+// alternating between the input buffer (scratch within the bucket's own
+// range) and the output.
+#include <algorithm>
+#include <mutex>
+
+#include "xtn_common.cuh"
+#include "xtn_kernels.h"
+
+namespace xtn {
+
+namespace {
+
+constexpr int BK_THREADS = 256;
+constexpr int BK_WARPS = BK_THREADS / 32;
+constexpr int BK_BITS = 9;
+constexpr int BK_BINS = 1 << BK_BITS;
+static_assert(BK_BINS == 2 * BK_THREADS, "each thread owns two digits");
+constexpr int SORT_ITEMS = 16;  // !HASH: 4096 records per segment, 2 blocks/SM
+constexpr int HASH_ITEMS = 8;   // HASH: 2048 records per segment, 4 blocks/SM
+
+template <bool HASH>
+struct Bk {
+  static constexpr int ITEMS = HASH ? HASH_ITEMS : SORT_ITEMS;
+  static constexpr int CAP = BK_THREADS * ITEMS;
+  static constexpr int MIN_BLOCKS = HASH ? 4 : 2;
+  static constexpr int HB = HASH ? 12 : 0;  // log2 of the hash slots (2 per record)
+  static constexpr int H = 1 << HB;
+  static constexpr size_t keys = (size_t)CAP * 8;
+  static constexpr size_t rank_tables = (size_t)2 * BK_WARPS * BK_BINS * 4;  // wh + mb
+  static constexpr size_t hash_tables = HASH ? (size_t)H * 4 + (size_t)H * 2 : 0;
+  static constexpr size_t region = rank_tables > hash_tables ? rank_tables : hash_tables;
+  static constexpr size_t base = (size_t)BK_BINS * 4;
+  static constexpr size_t bytes = keys + region + base;
+};
+static_assert(Bk<true>::H >= 2 * Bk<true>::CAP, "hash load factor <= 1/2");
+
+constexpr unsigned long long NO_START = ~0ull;
+constexpr uint32_t EMPTY_SLOT = 0xffffffffu;
+constexpr uint64_t NO_GROUP = ~0ull;  // above every group key (at most 40 bits)
+
+// First recorded bucket start at index >= b (bucket starts increase with the
+// bucket index), or n when no later bucket holds records.  Whole warp.
+__device__ int64_t first_start(const unsigned long long* __restrict__ bs, int64_t b, int64_t nb,
+                               int64_t n, uint32_t lane) {
+  for (int64_t base = b; base < nb; base += 32) {
+    const int64_t idx = base + lane;
+    const unsigned long long v = idx < nb ? bs[idx] : NO_START;
+    const uint32_t m = __ballot_sync(FULL_MASK, v != NO_START);
+    if (m) {
+      const unsigned long long f = __shfl_sync(FULL_MASK, v, __ffs(m) - 1);
+      return (int64_t)f < n ? (int64_t)f : n;
+    }
+  }
+  return n;
+}
+
+// Block-wide exclusive scan of one u32 per thread.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_wsum) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL_MASK, inc, o);
+    if (lane >= (uint32_t)o) inc += t;
+  }
+  if (lane == 31) s_wsum[warp] = inc;
+  __syncthreads();
+  uint32_t off = 0;
+#pragma unroll
+  for (int w = 0; w < BK_WARPS; ++w)
+    if (w < (int)warp) off += s_wsum[w];
+  __syncthreads();  // s_wsum is reused by the next scan
+  return off + inc - v;
+}
+
+// One stable ranking pass over the block's items (item i of lane l of warp w
+// is position w*32*ITEMS + i*32 + l; positions >= m are absent).  On return
+// s_wh[w*BINS + d] holds the position at which warp w's first record of
+// digit d goes: the digit's start within the block (scan of the block's
+// digit counts) or, when `running` is set, s_base[d] -- which then advances
+// by the block's count of d.  The peer bins s_mb must be zero on entry
+// (clear_mb) and are zero again on return.
+template <int ITEMS, class DigitF>
+__device__ __forceinline__ void rank_pass(const uint64_t (&key)[ITEMS], uint16_t (&rank)[ITEMS],
+                                          int m, DigitF digit, uint32_t* s_wh, uint32_t* s_mb,
+                                          uint32_t* s_base, bool running, bool clear_mb,
+                                          uint32_t* s_wsum) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int k = threadIdx.x; k < BK_WARPS * BK_BINS; k += BK_THREADS) {
+    s_wh[k] = 0;
+    if (clear_mb) s_mb[k] = 0;
+  }
+  __syncthreads();
+  uint32_t* wh = s_wh + warp * BK_BINS;
+  uint32_t* mb = s_mb + warp * BK_BINS;
+  const int wbase = (int)warp * 32 * ITEMS;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const bool valid = wbase + i * 32 + (int)lane < m;
+    const uint32_t dig = valid ? digit(key[i]) : 0u;
+    if (valid) atomicOr(&mb[dig], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = valid ? mb[dig] : 0u;
+    __syncwarp();
+    const uint32_t before = peers & lt_mask;
+    uint32_t old = 0;
+    if (valid && before == 0) {
+      old = wh[dig];
+      wh[dig] = old + __popc(peers);
+      mb[dig] = 0u;
+    }
+    old = __shfl_sync(FULL_MASK, old, valid ? __ffs(peers) - 1 : (int)lane);
+    rank[i] = (uint16_t)(old + __popc(before));
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread t owns digits 2t and 2t+1: per-warp exclusive offsets, then the
+  // digits' starts
+  const int d0 = 2 * threadIdx.x;
+  uint32_t r0 = 0, r1 = 0;
+#pragma unroll
+  for (int w = 0; w < BK_WARPS; ++w) {
+    const uint32_t c0 = s_wh[w * BK_BINS + d0], c1 = s_wh[w * BK_BINS + d0 + 1];
+    s_wh[w * BK_BINS + d0] = r0;
+    s_wh[w * BK_BINS + d0 + 1] = r1;
+    r0 += c0;
+    r1 += c1;
+  }
+  uint32_t st0, st1;
+  if (running) {
+    st0 = s_base[d0];
+    st1 = s_base[d0 + 1];
+    s_base[d0] = st0 + r0;
+    s_base[d0 + 1] = st1 + r1;
+  } else {
+    st0 = block_excl_scan(r0 + r1, s_wsum);
+    st1 = st0 + r0;
+  }
+#pragma unroll
+  for (int w = 0; w < BK_WARPS; ++w) {
+    s_wh[w * BK_BINS + d0] += st0;
+    s_wh[w * BK_BINS + d0 + 1] += st1;
+  }
+  __syncthreads();
+}
+
+// Packed head/tail counts, the layout k_group_write expects.
+__device__ __forceinline__ uint64_t pack_ht(uint32_t h, uint32_t t) {
+  return ((uint64_t)h << 31) | t;
+}
+
+// Flag words (head ballot | tail ballot << 32) of the grouped records
+// [p, p + m), whose group keys `gkey(j)` (j relative to p) differ from
+// everything outside the range.  Words wholly inside the range are stored,
+// the edge words (shared with the neighbouring ranges) are OR-ed into the
+// zeroed array.  Head/tail counts of flag tiles t0 and t0 + 1 accumulate in
+// acc0 / acc1 (packed, lane 0 of each warp), other tiles' go straight to
+// tile_counts.
+template <class GKey>
+__device__ __forceinline__ void write_flags(int64_t p, int64_t m, GKey gkey, uint64_t* flags,
+                                            uint64_t* tile_counts, int64_t t0, uint64_t& acc0,
+                                            uint64_t& acc1) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const int64_t gw0 = p >> 5, gw1 = (p + m - 1) >> 5;
+  for (int64_t gw = gw0 + warp; gw <= gw1; gw += BK_WARPS) {
+    const int64_t j = gw * 32 + lane - p;
+    const bool valid = j >= 0 && j < m;
+    const uint64_t g = valid ? gkey(j) : NO_GROUP;
+    uint64_t gp = __shfl_up_sync(FULL_MASK, g, 1);
+    uint64_t gn = __shfl_down_sync(FULL_MASK, g, 1);
+    if (lane == 0) gp = (j - 1 >= 0 && j - 1 < m) ? gkey(j - 1) : NO_GROUP;
+    if (lane == 31) gn = (j + 1 >= 0 && j + 1 < m) ? gkey(j + 1) : NO_GROUP;
+    const uint32_t hb = __ballot_sync(FULL_MASK, valid && g != gp && g == gn);
+    const uint32_t tb = __ballot_sync(FULL_MASK, valid && g == gp && g != gn);
+    if (lane == 0) {
+      const uint64_t word = ((uint64_t)tb << 32) | hb;
+      const bool whole = gw * 32 >= p && gw * 32 + 32 <= p + m;
+      if (whole) flags[gw] = word;
+      else if (word) atomicOr(reinterpret_cast<unsigned long long*>(&flags[gw]),
+                              (unsigned long long)word);
+      if (word) {
+        const uint64_t c = pack_ht(__popc(hb), __popc(tb));
+        const int64_t t = gw * 32 / GROUP_FLAG_TILE;
+        if (t == t0) acc0 += c;
+        else if (t == t0 + 1) acc1 += c;
+        else atomicAdd(reinterpret_cast<unsigned long long*>(&tile_counts[t]), (unsigned long long)c);
+      }
+    }
+  }
+}
+
+template <bool HASH>
+__global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
+    k_bucket(uint64_t* __restrict__ A, uint64_t* __restrict__ Y, int64_t n_cap,
+             const uint64_t* __restrict__ n_dev,
+             const unsigned long long* __restrict__ bucket_start, int G, int kbits, int lo, int L,
+             int cap, uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts,
+             uint32_t* __restrict__ err) {
+  using C = Bk<HASH>;
+  constexpr int ITEMS = C::ITEMS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + C::keys);  // rank tables or hash tables
+  uint32_t* s_mb = s_wh + BK_WARPS * BK_BINS;
+  uint32_t* s_base = reinterpret_cast<uint32_t*>(smem + C::keys + C::region);
+  __shared__ uint32_t s_wsum[BK_WARPS];
+  __shared__ int64_t s_range[2];
+  __shared__ unsigned long long s_acc[2];
+
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
+  const int64_t nb = 1ll << G;
+  const int64_t K = 1ll << kbits;
+  const int64_t b0 = (int64_t)blockIdx.x * K;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const int wbase = (int)warp * 32 * ITEMS;
+
+  // [s, e) of buckets [bf, bl)
+  auto bucket_range = [&](int64_t bf, int64_t bl) {
+    if (warp == 0) {
+      int64_t s = 0, e = n;
+      if (G > 0) {
+        s = first_start(bucket_start, bf, nb, n, lane);
+        e = bl >= nb ? n : first_start(bucket_start, bl, nb, n, lane);
+      }
+      if (lane == 0) {
+        s_range[0] = s;
+        s_range[1] = e < s ? s : e;
+      }
+    }
+    __syncthreads();
+  };
+  // empty hash table (composite keys all ones, counts zero), 16 bytes a store
+  auto clear_hash = [&]() {
+    uint4* t4 = reinterpret_cast<uint4*>(s_wh);
+    constexpr int KEY4 = C::H / 4, ALL4 = (C::H + C::H / 2) / 4;
+    for (int k = threadIdx.x; k < ALL4; k += BK_THREADS)
+      t4[k] = k < KEY4 ? make_uint4(EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT)
+                       : make_uint4(0u, 0u, 0u, 0u);
+  };
+  if (threadIdx.x == 0) s_acc[0] = s_acc[1] = 0;
+  if constexpr (HASH) {
+    // warp 0 finds the block's first record, warp 1 its end, the rest clear
+    if (warp < 2) {
+      int64_t v = warp == 0 ? 0 : n;
+      if (G > 0) {
+        const int64_t bf = warp == 0 ? b0 : b0 + K;
+        v = bf >= nb ? n : first_start(bucket_start, bf, nb, n, lane);
+      }
+      if (lane == 0) s_range[warp] = v;
+    } else {
+      for (int k = threadIdx.x - 64; k < (C::H + C::H / 2) / 4; k += BK_THREADS - 64)
+        reinterpret_cast<uint4*>(s_wh)[k] =
+            k < C::H / 4 ? make_uint4(EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT)
+                         : make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+  } else {
+    bucket_range(b0, b0 + K);
+  }
+  const int64_t s = s_range[0], e = s_range[1] < s_range[0] ? s_range[0] : s_range[1];
+  __syncthreads();
+  if (s >= n || s >= e) return;
+  uint64_t acc0 = 0, acc1 = 0;  // head/tail counts of this block's first two flag tiles
+  const int64_t tile_first = s / GROUP_FLAG_TILE;
+  auto gkey_of = [lo](uint64_t k) { return k >> lo; };
+
+  auto finish = [&](int64_t p, int m) {
+    for (int j = threadIdx.x; j < m; j += BK_THREADS) Y[p + j] = s_k[j];
+    if (flags)
+      write_flags(p, m, [&](int64_t j) { return gkey_of(s_k[j]); }, flags, tile_counts, tile_first,
+                  acc0, acc1);
+    __syncthreads();  // s_k and the tables are reused by the next segment
+  };
+
+  // ---- one segment [p, q) of at most `cap` records, buckets from bA ----
+  // composite key: (key >> lo) - (bA << L) = (bucket - bA) << L | low L bits
+  auto segment = [&](int64_t p, int64_t q, uint64_t bA, int kb, bool cleared) {
+    const int m = (int)(q - p);
+    const uint64_t cbase = bA << L;
+    auto comp = [&](uint64_t k) { return (uint32_t)((k >> lo) - cbase); };
+    uint64_t key[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int pos = wbase + i * 32 + (int)lane;
+      key[i] = pos < m ? __ldcs(A + p + pos) : 0ull;
+    }
+    if constexpr (HASH) {
+      uint32_t* tk = s_wh;                                   // H composite keys
+      uint32_t* tc = tk + C::H;                              // H u16 counts, two per word
+      if (!cleared) {
+        clear_hash();
+        __syncthreads();
+      }
+      uint32_t sr[ITEMS];  // slot << 16 | rank within the slot's group
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        sr[i] = 0;
+        if (wbase + i * 32 + (int)lane < m) {
+          const uint32_t c = comp(key[i]);
+          uint32_t h = (c * 0x9E3779B1u) >> (32 - C::HB);
+          bool found = false;
+          for (int probe = 0; probe < C::H; ++probe) {  // at most m <= H/2 keys: always ends
+            const uint32_t old = atomicCAS(&tk[h], EMPTY_SLOT, c);
+            if (old == EMPTY_SLOT || old == c) {
+              found = true;
+              break;
+            }
+            h = (h + 1) & (C::H - 1);
+          }
+          if (found) {
+            const uint32_t sh = (h & 1) * 16;
+            const uint32_t r = (atomicAdd(&tc[h >> 1], 1u << sh) >> sh) & 0xffffu;
+            sr[i] = (h << 16) | r;
+          } else {
+            atomicOr(err, DERR_RANGE);
+            sr[i] = 0xffffffffu;
+          }
+        }
+      }
+      __syncthreads();
+      // slot starts: exclusive scan of the counts in slot order (thread t owns
+      // H / THREADS consecutive slots), written back over the counts
+      constexpr int PER = C::H / BK_THREADS;
+      static_assert(PER % 2 == 0, "whole count words per thread");
+      uint32_t w[PER / 2];
+      uint32_t tot = 0;
+#pragma unroll
+      for (int k = 0; k < PER / 2; ++k) {
+        w[k] = tc[threadIdx.x * (PER / 2) + k];
+        tot += (w[k] & 0xffffu) + (w[k] >> 16);
+      }
+      uint32_t run = block_excl_scan(tot, s_wsum);
+#pragma unroll
+      for (int k = 0; k < PER / 2; ++k) {
+        const uint32_t a = w[k] & 0xffffu, b = w[k] >> 16;
+        tc[threadIdx.x * (PER / 2) + k] = run | ((run + a) << 16);
+        run += a + b;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        if (wbase + i * 32 + (int)lane < m && sr[i] != 0xffffffffu) {
+          const uint32_t h = sr[i] >> 16;
+          const uint32_t start = (tc[h >> 1] >> ((h & 1) * 16)) & 0xffffu;
+          const uint32_t pos = start + (sr[i] & 0xffffu);
+          if (pos < (uint32_t)m) s_k[pos] = key[i];
+          else atomicOr(err, DERR_RANGE);
+        }
+      }
+      __syncthreads();
+    } else {
+      const int passes = (L + kb + BK_BITS - 1) / BK_BITS;
+      uint16_t rank[ITEMS];
+      for (int pass = 0; pass < passes; ++pass) {
+        const int sh = BK_BITS * pass;
+        auto digit = [&](uint64_t k) { return (comp(k) >> sh) & (BK_BINS - 1); };
+        rank_pass(key, rank, m, digit, s_wh, s_mb, s_base, false, pass == 0, s_wsum);
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          if (wbase + i * 32 + (int)lane < m) {
+            const uint32_t pos = s_wh[warp * BK_BINS + digit(key[i])] + rank[i];
+            if (pos < (uint32_t)m) s_k[pos] = key[i];
+            else atomicOr(err, DERR_RANGE);
+          }
+        }
+        __syncthreads();
+        if (pass + 1 < passes) {
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i) {
+            const int pos = wbase + i * 32 + (int)lane;
+            key[i] = pos < m ? s_k[pos] : 0ull;
+          }
+          __syncthreads();  // every read done before the next pass scatters
+        }
+      }
+    }
+    finish(p, m);
+  };
+
+  // ---- one bucket [p, q) larger than `cap`, sorted in global memory ----
+  auto large = [&](int64_t p, int64_t q) {
+    const uint64_t lmask = (1ull << L) - 1ull;  // one bucket: the low L bits decide
+    const int passes = (L + BK_BITS - 1) / BK_BITS;
+    uint64_t* src = A;
+    uint64_t* dst = Y;
+    uint64_t key[ITEMS];
+    uint16_t rank[ITEMS];
+    for (int pass = 0; pass < passes; ++pass) {
+      const int sh = BK_BITS * pass;
+      auto digit = [&](uint64_t k) {
+        return (uint32_t)((((k >> lo) & lmask) >> sh) & (BK_BINS - 1));
+      };
+      for (int k = threadIdx.x; k < BK_BINS; k += BK_THREADS) s_base[k] = 0;
+      __syncthreads();
+      for (int64_t c = p; c < q; c += cap) {
+        const int cm = (int)min((int64_t)cap, q - c);
+        for (int j = threadIdx.x; j < cm; j += BK_THREADS) atomicAdd(&s_base[digit(src[c + j])], 1u);
+      }
+      __syncthreads();
+      {
+        const int d0 = 2 * threadIdx.x;
+        const uint32_t a = s_base[d0], b = s_base[d0 + 1];
+        const uint32_t x = block_excl_scan(a + b, s_wsum);
+        s_base[d0] = x;
+        s_base[d0 + 1] = x + a;
+        __syncthreads();
+      }
+      bool first = true;
+      for (int64_t c = p; c < q; c += cap) {
+        const int cm = (int)min((int64_t)cap, q - c);
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          const int pos = wbase + i * 32 + (int)lane;
+          key[i] = pos < cm ? src[c + pos] : 0ull;
+        }
+        rank_pass(key, rank, cm, digit, s_wh, s_mb, s_base, true, first, s_wsum);
+        first = false;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          if (wbase + i * 32 + (int)lane < cm) {
+            const uint64_t pos = (uint64_t)s_wh[warp * BK_BINS + digit(key[i])] + rank[i];
+            if (pos < (uint64_t)(q - p)) dst[p + pos] = key[i];
+            else atomicOr(err, DERR_RANGE);
+          }
+        }
+        __syncthreads();
+      }
+      uint64_t* t = src;
+      src = dst;
+      dst = t;
+    }
+    if (src != Y) {
+      for (int64_t j = p + threadIdx.x; j < q; j += BK_THREADS) Y[j] = src[j];
+      __syncthreads();
+    }
+    if (flags)
+      write_flags(p, q - p, [&](int64_t j) { return gkey_of(Y[p + j]); }, flags, tile_counts,
+                  tile_first, acc0, acc1);
+    __syncthreads();
+  };
+
+  if (e - s <= cap) {
+    segment(s, e, (uint64_t)b0, kbits, HASH);
+  } else {
+    // too many records for one segment: bucket by bucket
+    for (int64_t b = b0; b < b0 + K && b < nb; ++b) {
+      bucket_range(b, b + 1);
+      const int64_t p = s_range[0], q = s_range[1];
+      __syncthreads();
+      if (p >= q) continue;
+      if (q - p <= cap) segment(p, q, (uint64_t)b, 0, false);
+      else large(p, q);
+    }
+  }
+
+  // head/tail counts of the first two flag tiles this block touched
+  if (flags && lane == 0 && (acc0 | acc1)) {
+    if (acc0) atomicAdd(&s_acc[0], (unsigned long long)acc0);
+    if (acc1) atomicAdd(&s_acc[1], (unsigned long long)acc1);
+  }
+  __syncthreads();
+  if (flags && threadIdx.x == 0) {
+    if (s_acc[0])
+      atomicAdd(reinterpret_cast<unsigned long long*>(&tile_counts[tile_first]), s_acc[0]);
+    if (s_acc[1])
+      atomicAdd(reinterpret_cast<unsigned long long*>(&tile_counts[tile_first + 1]), s_acc[1]);
+  }
+}
+
+}  // namespace
+
+int bucket_capacity(bool hash) { return hash ? Bk<true>::CAP : Bk<false>::CAP; }
+
+GroupingShape choose_grouping(uint64_t n_rec, int hs, bool hash) {
+  GroupingShape g;
+  // global bits: until the average bucket holds at most ~2k records, with at
+  // least 8 and at most 24 bits left to the shared-memory step
+  int G = 0;
+  while (G + 8 <= hs - 8 && (n_rec >> G) > 2048) G += 8;
+  while (hs - G > 24) G += 8;
+  g.G = G;
+  g.L = hs - G;
+  // buckets per block: a power of two, on average at most ~80% of a segment;
+  // the composite key keeps to 31 bits
+  const uint64_t avg = std::max<uint64_t>(1, n_rec >> G);
+  const uint64_t fill = (uint64_t)bucket_capacity(hash) * 4 / 5;
+  int kb = 0;
+  while (kb < G && g.L + kb + 1 <= 31 && (avg << (kb + 1)) <= fill) ++kb;
+  g.kbits = kb;
+  return g;
+}
+
+void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
+                   const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
+                   uint64_t* flags, uint64_t* tile_counts, uint32_t* err, cudaStream_t s) {
+  if (n <= 0) return;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_bucket<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Bk<true>::bytes);
+    cudaFuncSetAttribute(k_bucket<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_bucket<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Bk<false>::bytes);
+    cudaFuncSetAttribute(k_bucket<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
+  const int full = bucket_capacity(hash);
+  if (cap <= 0 || cap > full) cap = full;
+  const uint64_t blocks = ((uint64_t)1 << g.G) >> g.kbits;
+  const double bytes = (double)n * 16.0 + (flags ? (double)n / 4.0 : 0.0);
+  const unsigned long long* bs = reinterpret_cast<const unsigned long long*>(bucket_start);
+  if (hash) {
+    prof_begin(s, "k_bucket_group", bytes);
+    k_bucket<true><<<(unsigned)blocks, BK_THREADS, Bk<true>::bytes, s>>>(
+        A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, err);
+  } else {
+    prof_begin(s, "k_bucket_sort", bytes);
+    k_bucket<false><<<(unsigned)blocks, BK_THREADS, Bk<false>::bytes, s>>>(
+        A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, err);
+  }
+  prof_end(s);
+}
+
+}  // namespace xtn

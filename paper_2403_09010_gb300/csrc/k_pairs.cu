@@ -155,7 +155,7 @@ constexpr int GB_ITEMS = 16;   // positions per lane per chunk
 constexpr int GB_CHUNKS = 4;
 constexpr int GB_WARP_SPAN = 32 * GB_ITEMS * GB_CHUNKS;
 constexpr int GB_TILE = GB_THREADS * GB_ITEMS * GB_CHUNKS;  // 32768 positions
-constexpr int GB_WORDS = GB_TILE / 32;                       // flag words per tile
+static_assert(GB_TILE == GROUP_FLAG_TILE, "flag tiles shared with k_bucket_sort");
 
 // K = uint32_t when the group key (key >> gshift) fits in 32 bits.
 template <typename K>
@@ -303,15 +303,17 @@ size_t group_status_bytes(int64_t n) {
 
 size_t group_flag_words(int64_t n) { return (size_t)((n + 31) / 32); }
 
-void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
-                         uint32_t* S, uint32_t* E, uint64_t cap, uint64_t* flags,
-                         uint64_t* status, uint32_t* err, uint64_t* n_groups, cudaStream_t s) {
+// Scratch layout in `status`: [scan status][tile counts][tile prefix (tiles+1)].
+uint64_t* group_tile_counts(uint64_t* status, int64_t n) {
+  const int64_t tiles = (n + GB_TILE - 1) / GB_TILE;
+  return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(status) + scan_status_bytes(tiles));
+}
+
+void launch_group_flags(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
+                        uint64_t* flags, uint64_t* status, cudaStream_t s) {
   if (n <= 0) return;
   const int64_t tiles = (n + GB_TILE - 1) / GB_TILE;
-  // scratch layout in `status`: [scan status][tile counts][tile prefix (tiles+1)]
-  const size_t st = scan_status_bytes(tiles);
-  uint64_t* tile_counts = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(status) + st);
-  uint64_t* tile_prefix = tile_counts + tiles;
+  uint64_t* tile_counts = group_tile_counts(status, n);
   prof_begin(s, "k_group_flags", (double)n * 8.0 + (double)(n / 32) * 8.0);
   if (gshift >= 32)
     k_group_flags<uint32_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, n_dev, gshift, flags,
@@ -320,6 +322,16 @@ void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev,
     k_group_flags<uint64_t><<<(unsigned)tiles, GB_THREADS, 0, s>>>(keys, n, n_dev, gshift, flags,
                                                                    tile_counts);
   prof_end(s);
+}
+
+void launch_group_finish(const uint64_t* flags, int64_t n, const uint64_t* n_dev, uint32_t* S,
+                         uint32_t* E, uint64_t cap, uint64_t* status, uint32_t* err,
+                         uint64_t* n_groups, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t tiles = (n + GB_TILE - 1) / GB_TILE;
+  const size_t st = scan_status_bytes(tiles);
+  uint64_t* tile_counts = group_tile_counts(status, n);
+  uint64_t* tile_prefix = tile_counts + tiles;
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
   prof_begin(s, "k_scan_tiles", (double)tiles * 16.0);
@@ -332,6 +344,13 @@ void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev,
   prof_end(s);
   // number of groups = heads in the total (high field of tile_prefix[tiles])
   k_groups_total<<<1, 1, 0, s>>>(tile_prefix + tiles, n_groups);
+}
+
+void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
+                         uint32_t* S, uint32_t* E, uint64_t cap, uint64_t* flags,
+                         uint64_t* status, uint32_t* err, uint64_t* n_groups, cudaStream_t s) {
+  launch_group_flags(keys, n, n_dev, gshift, flags, status, s);
+  launch_group_finish(flags, n, n_dev, S, E, cap, status, err, n_groups, s);
 }
 
 
@@ -405,7 +424,9 @@ __global__ void __launch_bounds__(EMIT_THREADS)
         const uint64_t s0 = S[k0 + lo];
         uint64_t w = 0;
         if (s0 + b < n_keys) {
-          w = ((keys[s0 + a] & idmask) << id_bits) | (keys[s0 + b] & idmask);
+          // members of a group need not be in id order: the word is (min, max)
+          const uint64_t ia = keys[s0 + a] & idmask, ib = keys[s0 + b] & idmask;
+          w = ((ia < ib ? ia : ib) << id_bits) | (ia < ib ? ib : ia);
         } else {
           atomicOr(err, DERR_RANGE);
         }

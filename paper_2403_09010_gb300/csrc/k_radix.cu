@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
                const uint64_t* __restrict__ n_dev, int64_t n_cap, int shift,
                int bits, const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
                uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
-               uint32_t* __restrict__ next_hist, int next_bits) {
+               uint32_t* __restrict__ next_hist, int next_bits,
+               unsigned long long* __restrict__ bucket_start, int bucket_shift) {
   using SM = OnesweepSmem<THREADS, ITEMS, MATCH, NCHAIN>;
   constexpr int WARPS = SM::WARPS;
   constexpr int TILE = SM::TILE;
@@ -344,6 +345,16 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     const int64_t o = s_obase[dig] + j;
     if (o >= 0 && o < n) out[o] = k;
     else atomicOr(err, DERR_RANGE);
+    // last pass: bucket = the bits this and the earlier passes sorted on
+    // (from bucket_shift up).  A bucket starts at o when the record before it
+    // in the output holds another bucket; for the first record of this tile's
+    // digit run that record sits in another tile, so every such candidate
+    // offers its position and the smallest one wins.
+    if (bucket_start && o >= 0 && o < n) {
+      const uint64_t b = k >> bucket_shift;
+      if (j == (int)s_tstart[dig] || b != (s_keys[j - 1] >> bucket_shift))
+        atomicMin(&bucket_start[b], (unsigned long long)o);
+    }
   }
   if (next_hist) {  // uniform over the block
     __syncthreads();  // every count of the write loop is in
@@ -393,7 +404,9 @@ int onesweep_configs() { return 20; }
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    const uint64_t* n_dev, int shift, int bits, const uint64_t* digit_base,
                                    uint64_t* status, uint32_t* ctr, uint32_t* err,
-                                   uint32_t* next_hist, int next_bits, cudaStream_t s) {
+                                   uint32_t* next_hist, int next_bits,
+                                   unsigned long long* bucket_start, int bucket_shift,
+                                   cudaStream_t s) {
   switch (cfg) {
 #define X(id, T, I, B, M, C)                                                                  \
   case id: {                                                                                  \
@@ -410,7 +423,8 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
     k_onesweep<T, I, B, M, C><<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits,        \
                                                           digit_base,                         \
                                                        status, ctr, err, next_hist,           \
-                                                       next_bits);                            \
+                                                       next_bits, bucket_start,               \
+                                                       bucket_shift);                         \
     return cudaGetLastError();                                                                \
   }
     XTN_ONESWEEP_CONFIGS(X)
@@ -436,7 +450,8 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
 cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
-                              bool hist_in_passes, const uint64_t* n_dev) {
+                              bool hist_in_passes, const uint64_t* n_dev,
+                              uint64_t* bucket_start) {
   const int passes = (hi - lo + 7) / 8;
   *sorted = a;
   if (n <= 1 || passes == 0) return cudaSuccess;
@@ -458,8 +473,10 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
     cudaError_t e = cudaMemsetAsync(status, 0, st_bytes, s);
     if (e != cudaSuccess) return e;
     prof_begin(s, tag, (double)n * 16.0);
+    unsigned long long* bs =
+        p + 1 == passes ? reinterpret_cast<unsigned long long*>(bucket_start) : nullptr;
     e = onesweep_launch(cfg, src, dst, n, n_dev, sh, bits, digit_base + p * RADIX, status, ctr, err,
-                        next, next_bits, s);
+                        next, next_bits, bs, lo, s);
     prof_end(s);
     if (e != cudaSuccess) return e;
     std::swap(src, dst);

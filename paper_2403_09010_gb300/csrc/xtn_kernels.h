@@ -46,11 +46,38 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
 // the next pass's digits itself (zeroed hist rows 1.. expected).
 // n_dev: when not null the key count is read on the device (n is then a
 // capacity that sizes the grid and the look-back status).
+// bucket_start: when not null (2^(hi-lo) entries, all bits set on entry), the
+// last pass leaves in bucket_start[b] the first sorted position whose bits
+// [lo, hi) equal b; buckets without records keep all bits set.
 cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
-                              bool hist_in_passes = false, const uint64_t* n_dev = nullptr);
+                              bool hist_in_passes = false, const uint64_t* n_dev = nullptr,
+                              uint64_t* bucket_start = nullptr);
 
+// k_bucket.cu --------------------------------------------------------------
+// Positions per flag tile of the group-bound kernels (head/tail counts are
+// kept per tile of this many sorted records).
+constexpr int GROUP_FLAG_TILE = 32768;
+// Split of the hs group-key bits: the top G are sorted by global radix
+// passes (bucket = those bits), the low L = hs - G in shared memory, 2^kbits
+// buckets per block.  G depends only on (n_rec, hs); kbits also on the
+// shared-memory step (hash grouping or sort).
+struct GroupingShape {
+  int G = 0, L = 0, kbits = 0;
+};
+GroupingShape choose_grouping(uint64_t n_rec, int hs, bool hash);
+int bucket_capacity(bool hash);
+// A holds n records sorted on their top G group-key bits (bits [lo + L, 64)),
+// bucket_start as left by radix_sort_passes (unused when G == 0).  Writes the
+// records to Y (A is scratch afterwards): with `hash`, every group's records
+// contiguous in arbitrary order; without, sorted on all group-key bits.
+// With `flags` (zeroed, group_flag_words(n)) and `tile_counts` (zeroed, one
+// per GROUP_FLAG_TILE positions) also the head/tail flags k_group_write
+// reads.  cap: records per shared-memory segment (0 = the full capacity).
+void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
+                   const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
+                   uint64_t* flags, uint64_t* tile_counts, uint32_t* err, cudaStream_t s);
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
 size_t group_status_bytes(int64_t n);
@@ -60,9 +87,17 @@ void launch_scan_group_pairs(const uint32_t* S, const uint32_t* E, int64_t n_gro
                              const uint64_t* n_groups_dev, uint64_t* out, uint64_t* status,
                              uint32_t* err, cudaStream_t s);
 size_t group_flag_words(int64_t n);
+// Group bounds = flags (k_group_flags, or k_bucket_sort) + finish (tile
+// prefix, k_group_write, group count).  `status` holds group_status_bytes(n).
 void launch_group_bounds(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
                          uint32_t* S, uint32_t* E, uint64_t cap, uint64_t* flags,
                          uint64_t* status, uint32_t* err, uint64_t* n_groups, cudaStream_t s);
+uint64_t* group_tile_counts(uint64_t* status, int64_t n);
+void launch_group_flags(const uint64_t* keys, int64_t n, const uint64_t* n_dev, int gshift,
+                        uint64_t* flags, uint64_t* status, cudaStream_t s);
+void launch_group_finish(const uint64_t* flags, int64_t n, const uint64_t* n_dev, uint32_t* S,
+                         uint32_t* E, uint64_t cap, uint64_t* status, uint32_t* err,
+                         uint64_t* n_groups, cudaStream_t s);
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        const uint64_t* pair_off, int64_t n_groups, const uint64_t* n_groups_dev,
                        uint64_t pair_cap, uint32_t id_bits, uint64_t* out, uint64_t* n_pairs_out,

@@ -4,6 +4,8 @@ Every case calls the C ABI through the thin binding.  Outputs are the sorted
 (i, j, dist) rows; the oracle computes the same rows from strings with full
 dynamic programming (oracle/xtn_oracle.cpp).
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -167,6 +169,101 @@ def test_every_sort_configuration(xtn):
         xtn.tune_set(R, default[0])
         xtn.tune_set(P, default[1])
         xtn.tune_set(H, default[2])
+
+
+# -------------------------------------------------------- grouping modes ---
+@functools.lru_cache(maxsize=None)
+def _case(name):
+    """(seqs, offsets, d, expected rows) of a named parity case; expected
+    values come from the oracle only."""
+    if name == "gen60k_d2":
+        seqs, off = gen.workload(gen.SELF_1M, 60_000)
+        return seqs, off, 2, oracle.symdel_self(seqs, off, 2)
+    if name == "small_d1":
+        seqs, off = gen.workload(gen.SELF_SMALL)
+        return seqs, off, 1, oracle.symdel_self(seqs, off, 1)
+    if name == "tiny_d2":  # one bucket only (no global pass)
+        seqs, off = gen.workload(gen.SELF_1M, 20)
+        return seqs, off, 2, oracle.bruteforce_self(seqs, off, 2)
+    if name == "alphabet_AC_d2":
+        strs = _rand_strings(np.random.default_rng(31), 400, "AC", 0, 9)
+        seqs, off = gen.from_strings(strs)
+        return seqs, off, 2, oracle.bruteforce_self(seqs, off, 2)
+    raise KeyError(name)
+
+
+def _with_copies(base_seqs, base_off, copy, n_copies, d):
+    """Input = base sequences followed by n_copies of `copy`, and its rows:
+    the oracle on base + one copy, the copy's rows repeated for every copy,
+    and every pair of copies at distance 0."""
+    base = gen.to_strings(base_seqs, base_off)
+    nb = len(base)
+    s1, o1 = gen.from_strings(base + [copy])
+    one = oracle.symdel_self(s1, o1, d).astype(np.int64)
+    keep = one[one[:, 1] < nb]
+    to_copy = one[one[:, 1] == nb]
+    parts = [keep]
+    for k in range(n_copies):
+        t = to_copy.copy()
+        t[:, 1] = nb + k
+        parts.append(t)
+    ii, jj = np.triu_indices(n_copies, 1)
+    parts.append(np.stack([ii + nb, jj + nb, np.zeros_like(ii)], 1))
+    rows = np.concatenate(parts)
+    rows = rows[np.lexsort((rows[:, 1], rows[:, 0]))]
+    seqs, off = gen.from_strings(base + [copy] * n_copies)
+    return seqs, off, rows.astype(np.uint32)
+
+
+@pytest.fixture
+def grouping(xtn):
+    G = xtn.XTN_TUNE_GROUPING
+    old = xtn.tune_get(G)
+    yield lambda mode: xtn.tune_set(G, mode)
+    xtn.tune_set(G, old)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_grouping_modes_match_oracle(xtn, grouping, mode):
+    grouping(mode)
+    for name in ["gen60k_d2", "small_d1", "tiny_d2", "alphabet_AC_d2"]:
+        seqs, off, d, want = _case(name)
+        assert np.array_equal(_rows(xtn.search_self(seqs, off, d)), want), (mode, name)
+    # planned path (device-side counts) and the 700-copy bucket
+    seqs, off, d, want = _case("gen60k_d2")
+    plan = xtn.Plan(off, d)
+    plan.run(torch.from_numpy(seqs).cuda())
+    assert np.array_equal(_rows(plan.result()), want), mode
+    plan.free()
+    n = 700
+    seqs, off = gen.from_strings(["CASSLGQETQYF"] * n)
+    got = _rows(xtn.search_self(seqs, off, 2))
+    ii, jj = np.triu_indices(n, 1)
+    assert got.shape[0] == ii.size and np.all(got[:, 2] == 0), mode
+    assert np.array_equal(got[:, 0], ii) and np.array_equal(got[:, 1], jj), mode
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_grouping_modes_query_index(xtn, grouping, mode):
+    grouping(mode)
+    rs, ro, reqs = gen.served(ref_n=30_000, n_req=3, max_req=2000)
+    idx = xtn.index_build(rs, ro, 2)
+    for r in reqs:
+        want = oracle.symdel_query(rs, ro, r.seqs, r.offsets, 2)
+        assert np.array_equal(_rows(xtn.search_query(idx, r.seqs, r.offsets)), want), mode
+    idx.free()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_bucket_larger_than_shared_memory(xtn, grouping, mode):
+    # 4,200 copies put more records in one bucket than a block's shared memory
+    # holds (2,048 when grouping, 4,096 when sorting): that bucket is sorted
+    # in global memory
+    grouping(mode)
+    bs, bo = gen.workload(gen.SELF_1M, 3000)
+    seqs, off, want = _with_copies(bs, bo, "CASS", 4200, 1)
+    got = _rows(xtn.search_self(seqs, off, 1))
+    assert got.shape == want.shape and np.array_equal(got, want)
 
 
 # --------------------------------------------------------------- batched ---
