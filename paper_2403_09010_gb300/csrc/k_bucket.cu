@@ -37,24 +37,26 @@ namespace {
 
 constexpr int BK_THREADS = 256;
 constexpr int BK_WARPS = BK_THREADS / 32;
-constexpr int BK_BITS = 9;
-constexpr int BK_BINS = 1 << BK_BITS;
-static_assert(BK_BINS == 2 * BK_THREADS, "each thread owns two digits");
 constexpr int SORT_ITEMS = 16;  // !HASH: 4096 records per segment, 2 blocks/SM
-constexpr int HASH_ITEMS = 8;   // HASH: 2048 records per segment, 4 blocks/SM
+constexpr int HASH_ITEMS = 8;   // HASH: 2048 records per segment, 5 blocks/SM
 
+// Radix digits of the shared-memory passes: 9 bits for the sorting variant
+// (two passes cover 17 bits); 8 for the hashing one, whose ranking only runs
+// on oversized buckets and whose smaller tables leave room for a fifth block.
 template <bool HASH>
 struct Bk {
   static constexpr int ITEMS = HASH ? HASH_ITEMS : SORT_ITEMS;
   static constexpr int CAP = BK_THREADS * ITEMS;
-  static constexpr int MIN_BLOCKS = HASH ? 4 : 2;
+  static constexpr int MIN_BLOCKS = HASH ? 5 : 2;
+  static constexpr int BITS = HASH ? 8 : 9;
+  static constexpr int BINS = 1 << BITS;
   static constexpr int HB = HASH ? 12 : 0;  // log2 of the hash slots (2 per record)
   static constexpr int H = 1 << HB;
   static constexpr size_t keys = (size_t)CAP * 8;
-  static constexpr size_t rank_tables = (size_t)2 * BK_WARPS * BK_BINS * 4;  // wh + mb
+  static constexpr size_t rank_tables = (size_t)2 * BK_WARPS * BINS * 4;  // wh + mb
   static constexpr size_t hash_tables = HASH ? (size_t)H * 4 + (size_t)H * 2 : 0;
   static constexpr size_t region = rank_tables > hash_tables ? rank_tables : hash_tables;
-  static constexpr size_t base = (size_t)BK_BINS * 4;
+  static constexpr size_t base = (size_t)BINS * 4;
   static constexpr size_t bytes = keys + region + base;
 };
 static_assert(Bk<true>::H >= 2 * Bk<true>::CAP, "hash load factor <= 1/2");
@@ -105,20 +107,20 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_wsum
 // digit counts) or, when `running` is set, s_base[d] -- which then advances
 // by the block's count of d.  The peer bins s_mb must be zero on entry
 // (clear_mb) and are zero again on return.
-template <int ITEMS, class DigitF>
+template <int ITEMS, int BINS, class DigitF>
 __device__ __forceinline__ void rank_pass(const uint64_t (&key)[ITEMS], uint16_t (&rank)[ITEMS],
                                           int m, DigitF digit, uint32_t* s_wh, uint32_t* s_mb,
                                           uint32_t* s_base, bool running, bool clear_mb,
                                           uint32_t* s_wsum) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int k = threadIdx.x; k < BK_WARPS * BK_BINS; k += BK_THREADS) {
+  for (int k = threadIdx.x; k < BK_WARPS * BINS; k += BK_THREADS) {
     s_wh[k] = 0;
     if (clear_mb) s_mb[k] = 0;
   }
   __syncthreads();
-  uint32_t* wh = s_wh + warp * BK_BINS;
-  uint32_t* mb = s_mb + warp * BK_BINS;
+  uint32_t* wh = s_wh + warp * BINS;
+  uint32_t* mb = s_mb + warp * BINS;
   const int wbase = (int)warp * 32 * ITEMS;
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
@@ -140,33 +142,45 @@ __device__ __forceinline__ void rank_pass(const uint64_t (&key)[ITEMS], uint16_t
     __syncwarp();
   }
   __syncthreads();
-  // thread t owns digits 2t and 2t+1: per-warp exclusive offsets, then the
-  // digits' starts
-  const int d0 = 2 * threadIdx.x;
-  uint32_t r0 = 0, r1 = 0;
+  // thread t owns digits DPT*t .. DPT*t + DPT - 1: per-warp exclusive
+  // offsets, then the digits' starts
+  constexpr int DPT = BINS / BK_THREADS;
+  static_assert(DPT >= 1 && BINS % BK_THREADS == 0, "whole digits per thread");
+  const int d0 = DPT * threadIdx.x;
+  uint32_t r[DPT];
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) r[k] = 0;
 #pragma unroll
   for (int w = 0; w < BK_WARPS; ++w) {
-    const uint32_t c0 = s_wh[w * BK_BINS + d0], c1 = s_wh[w * BK_BINS + d0 + 1];
-    s_wh[w * BK_BINS + d0] = r0;
-    s_wh[w * BK_BINS + d0 + 1] = r1;
-    r0 += c0;
-    r1 += c1;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      const uint32_t c = s_wh[w * BINS + d0 + k];
+      s_wh[w * BINS + d0 + k] = r[k];
+      r[k] += c;
+    }
   }
-  uint32_t st0, st1;
+  uint32_t st[DPT];
   if (running) {
-    st0 = s_base[d0];
-    st1 = s_base[d0 + 1];
-    s_base[d0] = st0 + r0;
-    s_base[d0 + 1] = st1 + r1;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      st[k] = s_base[d0 + k];
+      s_base[d0 + k] = st[k] + r[k];
+    }
   } else {
-    st0 = block_excl_scan(r0 + r1, s_wsum);
-    st1 = st0 + r0;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) tot += r[k];
+    uint32_t x = block_excl_scan(tot, s_wsum);
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      st[k] = x;
+      x += r[k];
+    }
   }
 #pragma unroll
-  for (int w = 0; w < BK_WARPS; ++w) {
-    s_wh[w * BK_BINS + d0] += st0;
-    s_wh[w * BK_BINS + d0 + 1] += st1;
-  }
+  for (int w = 0; w < BK_WARPS; ++w)
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) s_wh[w * BINS + d0 + k] += st[k];
   __syncthreads();
 }
 
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
   uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + C::keys);  // rank tables or hash tables
-  uint32_t* s_mb = s_wh + BK_WARPS * BK_BINS;
+  uint32_t* s_mb = s_wh + BK_WARPS * C::BINS;
   uint32_t* s_base = reinterpret_cast<uint32_t*>(smem + C::keys + C::region);
   __shared__ uint32_t s_wsum[BK_WARPS];
   __shared__ int64_t s_range[2];
@@ -375,16 +389,17 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
       }
       __syncthreads();
     } else {
-      const int passes = (L + kb + BK_BITS - 1) / BK_BITS;
+      const int passes = (L + kb + C::BITS - 1) / C::BITS;
       uint16_t rank[ITEMS];
       for (int pass = 0; pass < passes; ++pass) {
-        const int sh = BK_BITS * pass;
-        auto digit = [&](uint64_t k) { return (comp(k) >> sh) & (BK_BINS - 1); };
-        rank_pass(key, rank, m, digit, s_wh, s_mb, s_base, false, pass == 0, s_wsum);
+        const int sh = C::BITS * pass;
+        auto digit = [&](uint64_t k) { return (comp(k) >> sh) & (C::BINS - 1); };
+        rank_pass<ITEMS, C::BINS>(key, rank, m, digit, s_wh, s_mb, s_base, false, pass == 0,
+                                  s_wsum);
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
           if (wbase + i * 32 + (int)lane < m) {
-            const uint32_t pos = s_wh[warp * BK_BINS + digit(key[i])] + rank[i];
+            const uint32_t pos = s_wh[warp * C::BINS + digit(key[i])] + rank[i];
             if (pos < (uint32_t)m) s_k[pos] = key[i];
             else atomicOr(err, DERR_RANGE);
           }
@@ -406,17 +421,17 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   // ---- one bucket [p, q) larger than `cap`, sorted in global memory ----
   auto large = [&](int64_t p, int64_t q) {
     const uint64_t lmask = (1ull << L) - 1ull;  // one bucket: the low L bits decide
-    const int passes = (L + BK_BITS - 1) / BK_BITS;
+    const int passes = (L + C::BITS - 1) / C::BITS;
     uint64_t* src = A;
     uint64_t* dst = Y;
     uint64_t key[ITEMS];
     uint16_t rank[ITEMS];
     for (int pass = 0; pass < passes; ++pass) {
-      const int sh = BK_BITS * pass;
+      const int sh = C::BITS * pass;
       auto digit = [&](uint64_t k) {
-        return (uint32_t)((((k >> lo) & lmask) >> sh) & (BK_BINS - 1));
+        return (uint32_t)((((k >> lo) & lmask) >> sh) & (C::BINS - 1));
       };
-      for (int k = threadIdx.x; k < BK_BINS; k += BK_THREADS) s_base[k] = 0;
+      for (int k = threadIdx.x; k < C::BINS; k += BK_THREADS) s_base[k] = 0;
       __syncthreads();
       for (int64_t c = p; c < q; c += cap) {
         const int cm = (int)min((int64_t)cap, q - c);
@@ -424,11 +439,19 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
       }
       __syncthreads();
       {
-        const int d0 = 2 * threadIdx.x;
-        const uint32_t a = s_base[d0], b = s_base[d0 + 1];
-        const uint32_t x = block_excl_scan(a + b, s_wsum);
-        s_base[d0] = x;
-        s_base[d0 + 1] = x + a;
+        constexpr int DPT = C::BINS / BK_THREADS;
+        uint32_t c[DPT], tot = 0;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          c[k] = s_base[DPT * threadIdx.x + k];
+          tot += c[k];
+        }
+        uint32_t x = block_excl_scan(tot, s_wsum);
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          s_base[DPT * threadIdx.x + k] = x;
+          x += c[k];
+        }
         __syncthreads();
       }
       bool first = true;
@@ -439,12 +462,12 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
           const int pos = wbase + i * 32 + (int)lane;
           key[i] = pos < cm ? src[c + pos] : 0ull;
         }
-        rank_pass(key, rank, cm, digit, s_wh, s_mb, s_base, true, first, s_wsum);
+        rank_pass<ITEMS, C::BINS>(key, rank, cm, digit, s_wh, s_mb, s_base, true, first, s_wsum);
         first = false;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
           if (wbase + i * 32 + (int)lane < cm) {
-            const uint64_t pos = (uint64_t)s_wh[warp * BK_BINS + digit(key[i])] + rank[i];
+            const uint64_t pos = (uint64_t)s_wh[warp * C::BINS + digit(key[i])] + rank[i];
             if (pos < (uint64_t)(q - p)) dst[p + pos] = key[i];
             else atomicOr(err, DERR_RANGE);
           }
