@@ -1,7 +1,9 @@
 """Autotuner for the planned (batched) self-search.
 
-Picks, by timing on the caller's own data, where the record sort's digit
-counts are taken (in the expand kernel, or one pass ahead in each sort pass),
+Picks, by timing on the caller's own data, how records are grouped (global
+radix passes on the top bits plus a shared-memory bucket pass, or global
+passes on every bit plus a flag pass), where the record sort's digit counts
+are taken (in the expand kernel, or one pass ahead in each sort pass),
 the tile configuration of each radix sort (variant records and verified
 pairs; see xtn_tune_set) and a
 candidate-pair capacity for the plan (measured candidates x 1.25, so a plan
@@ -35,8 +37,8 @@ def _key(n, n_rep, d):
 def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int = 2,
          use_cache: bool = True) -> dict:
     """Time every sort configuration on this workload and apply the fastest.
-    Returns {"record_hist", "records_cfg", "pairs_cfg", "pair_capacity",
-    "sort_ms": {...}}."""
+    Returns {"grouping", "record_hist", "records_cfg", "pairs_cfg",
+    "pair_capacity", "sort_ms": {...}}."""
     n = int(offsets.shape[0]) - 1
     n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
     key = _key(n, n_rep, d)
@@ -49,13 +51,16 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
             cache = {}
     if use_cache and key in cache:
         r = cache[key]
+        xtn.tune_set(native.XTN_TUNE_GROUPING, r.get("grouping", 0))
         xtn.tune_set(native.XTN_TUNE_RECORD_HISTOGRAM, r.get("record_hist", 0))
         xtn.tune_set(native.XTN_TUNE_SORT_RECORDS, r["records_cfg"])
         xtn.tune_set(native.XTN_TUNE_SORT_PAIRS, r["pairs_cfg"])
         return r
     import torch
-    R, P, H = (native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS,
-               native.XTN_TUNE_RECORD_HISTOGRAM)
+    R, P, H, GR = (native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS,
+                   native.XTN_TUNE_RECORD_HISTOGRAM, native.XTN_TUNE_GROUPING)
+    # the grouping stage: expand, record sort passes, bucket or flag pass
+    group_kernels = ("k_expand", "k_onesweep_records", "k_bucket_group", "k_group_flags")
     configs = list(range(xtn.tune_count(R))) if configs is None else list(configs)
 
     def measure(*kernels):
@@ -71,13 +76,22 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
         prof = xtn.profile_report()
         stats = plan.stats()
         plan.free()
-        ms = sum(prof.get(k, (1, float("inf"), 0))[1] for k in kernels)
+        # kernels a mode does not launch count as zero time
+        ms = sum(prof[k][1] for k in kernels if k in prof)
+        if not any(k in prof for k in kernels):
+            ms = float("inf")
         return ms / repeats, stats
 
+    group_ms = {}
+    for gm in (0, 1):  # mode 2 only shrinks the shared-memory segments
+        xtn.tune_set(GR, gm)
+        group_ms[gm], _ = measure(*group_kernels)
+    best_g = min(group_ms, key=group_ms.get)
+    xtn.tune_set(GR, best_g)
     hist_ms = {}
     for h in range(xtn.tune_count(H)):
         xtn.tune_set(H, h)
-        hist_ms[h], _ = measure("k_expand", "k_onesweep_records")
+        hist_ms[h], _ = measure(*group_kernels)
     best_h = min(hist_ms, key=hist_ms.get)
     xtn.tune_set(H, best_h)
     rec_ms, pair_ms = {}, {}
@@ -93,7 +107,7 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
         pair_ms[c], _ = measure("k_onesweep_pairs")
     best_p = min(pair_ms, key=pair_ms.get)
     xtn.tune_set(P, best_p)
-    r = {"record_hist": best_h, "records_cfg": best_r, "pairs_cfg": best_p,
+    r = {"grouping": best_g, "record_hist": best_h, "records_cfg": best_r, "pairs_cfg": best_p,
          "pair_capacity": max(65536, int(cands * 1.25)),
          "sort_ms": {"records": rec_ms[best_r], "pairs": pair_ms[best_p]}}
     if use_cache:
