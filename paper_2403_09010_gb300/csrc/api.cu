@@ -121,6 +121,12 @@ class Arena {
     return static_cast<T*>(p);
   }
   bool failed() const { return failed_; }
+  // Frees everything now (stream-ordered), e.g. before a retry that
+  // allocates again.
+  void release() {
+    for (void* p : ptrs_) cudaFreeAsync(p, s_);
+    ptrs_.clear();
+  }
 
  private:
   cudaStream_t s_;
@@ -292,6 +298,12 @@ struct GroupScratch {
   uint64_t* bucket_start = nullptr;
   uint64_t* flags = nullptr;
   uint64_t* gstatus = nullptr;
+  // bucket mode with flags: candidate words of the buckets that fit shared
+  // memory go straight to cand[0, cand_cap); cand_count[0] counts them,
+  // cand_count[1] the records of larger buckets (zeroed by the caller)
+  uint64_t* cand = nullptr;
+  uint64_t cand_cap = 0;
+  uint64_t* cand_count = nullptr;
 };
 
 size_t bucket_start_words(uint64_t rec_cap, int hs, int mode) {
@@ -350,7 +362,8 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
     tile_counts = group_tile_counts(gs.gstatus, (int64_t)rec_cap);
   }
   launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo,
-                mode == 2 ? 512 : 0, gs.flags, tile_counts, err, s);
+                mode == 2 ? 512 : 0, gs.flags, tile_counts, hash ? gs.cand : nullptr, gs.cand_cap,
+                gs.cand_count, id_bits, err, s);
   XTN_CK(cudaGetLastError());
   *sorted = Y;
   return XTN_OK;
@@ -360,7 +373,8 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
 // sized for the group-bound and group-pair scans of up to g_cap groups).
 int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep, int sms,
                     Arena& ar, uint32_t* err, cudaStream_t s, Sorted* out,
-                    bool want_flags = false, uint64_t g_cap = 0) {
+                    bool want_flags = false, uint64_t g_cap = 0, int mode = -1,
+                    const GroupScratch* direct = nullptr) {
   const uint64_t n_rec = e.n_rec;
   out->id_bits = bits_for((uint64_t)n);
   out->hs = choose_hash_bits(n_rec, out->id_bits);
@@ -371,8 +385,13 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
   uint32_t* hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
   uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
   uint64_t* status = ar.get<uint64_t>(radix_status_bytes(n_rec, cfg) / 8 + 1);
-  const int mode = g_grouping.load();
+  if (mode < 0) mode = g_grouping.load();
   GroupScratch gs;
+  if (direct) {
+    gs.cand = direct->cand;
+    gs.cand_cap = direct->cand_cap;
+    gs.cand_count = direct->cand_count;
+  }
   gs.bucket_start = ar.get<uint64_t>(bucket_start_words(n_rec, out->hs, mode));
   if (want_flags) {
     gs.flags = ar.get<uint64_t>(group_flag_words((int64_t)n_rec));
@@ -493,9 +512,10 @@ __global__ void k_pair_total(const uint64_t* __restrict__ pair_off,
   *out = pair_off[*n_groups];
 }
 
+// mode: grouping mode (see g_grouping), -1 = the tuned one.
 int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                      const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
-                     int64_t* n_out, cudaStream_t s) {
+                     int64_t* n_out, cudaStream_t s, int mode = -1) {
   if (!n_out) return XTN_ERR_INVALID_ARG;
   *n_out = 0;
   if (n < 0 || d < 0 || d > XTN_MAX_D || cap < 0 || !offsets) return XTN_ERR_INVALID_ARG;
@@ -528,31 +548,61 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (rc) return rc;
   Sorted so;
   const uint64_t g_cap = e.n_rec / 2 + 1;
-  rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so, true, g_cap);
+  if (mode < 0) mode = g_grouping.load();
+  // Bucket modes emit the candidates of every bucket that fits shared memory
+  // during grouping, into a buffer sized by a guess; past it, the search runs
+  // again with all-global grouping, which sizes its buffers exactly.
+  GroupScratch direct;
+  if (mode != 1) {
+    direct.cand_cap = std::max<uint64_t>(e.n_rec / 2, 1u << 20);
+    direct.cand = ar.get<uint64_t>(direct.cand_cap + 8);
+    direct.cand_count = counters + 2;
+    XTN_ALLOC_OK(ar);
+  }
+  rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so, true, g_cap, mode,
+                       mode != 1 ? &direct : nullptr);
   if (rc) return rc;
   uint32_t* S = reinterpret_cast<uint32_t*>(so.spare);  // groups live in the spare buffer
   uint32_t* E = S + g_cap;
   uint64_t* pair_off = reinterpret_cast<uint64_t*>(E + g_cap);  // 8-byte aligned
-  launch_group_finish(so.flags, (int64_t)e.n_rec, nullptr, S, E, g_cap, so.gstatus, err, counters,
-                      s);
-  launch_scan_group_pairs(S, E, (int64_t)g_cap, counters, pair_off, so.gstatus, err, s);
-  k_pair_total<<<1, 1, 0, s>>>(pair_off, counters, counters + 1);
-  XTN_CK(cudaGetLastError());
   struct {
-    uint64_t groups, pairs;
+    uint64_t groups, pairs, direct, large;
     uint32_t err;
-  } h{0, 0, 0};
-  XTN_CK(cudaMemcpyAsync(&h.groups, counters, 16, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
-  if (h.err) return map_device_err(h.err);
-  const uint64_t n_pairs = h.pairs;
+  } h{0, 0, 0, 0, 0};
+  bool flagged = mode == 1;  // groups to emit through flags and S/E
+  if (mode != 1) {
+    XTN_CK(cudaMemcpyAsync(&h.direct, counters + 2, 16, cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaStreamSynchronize(s));
+    if (h.err & DERR_CAPACITY) {
+      ar.release();
+      return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1);
+    }
+    if (h.err) return map_device_err(h.err);
+    flagged = h.large > 0;
+  }
+  if (flagged) {
+    launch_group_finish(so.flags, (int64_t)e.n_rec, nullptr, S, E, g_cap, so.gstatus, err,
+                        counters, s);
+    launch_scan_group_pairs(S, E, (int64_t)g_cap, counters, pair_off, so.gstatus, err, s);
+    k_pair_total<<<1, 1, 0, s>>>(pair_off, counters, counters + 1);
+    XTN_CK(cudaGetLastError());
+    XTN_CK(cudaMemcpyAsync(&h.groups, counters, 16, cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaStreamSynchronize(s));
+    if (h.err) return map_device_err(h.err);
+  }
+  const uint64_t n_pairs = h.direct + h.pairs;
   if (n_pairs == 0) return XTN_OK;
   if (n_pairs >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  if (mode != 1 && n_pairs > direct.cand_cap) {
+    ar.release();
+    return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1);
+  }
 
-  // back: emit candidates, verify, sort survivors, dedup
+  // back: the remaining candidates, verify, sort survivors, dedup
   BackStage b;
-  b.P1 = ar.get<uint64_t>(n_pairs + 8);
+  b.P1 = mode != 1 ? direct.cand : ar.get<uint64_t>(n_pairs + 8);
   b.P2 = ar.get<uint64_t>(n_pairs + 8);
   b.hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
   b.digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
@@ -561,8 +611,9 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   b.counters = ar.get<uint64_t>(2);
   uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
   XTN_ALLOC_OK(ar);
-  launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)h.groups, nullptr, n_pairs, so.id_bits,
-                    b.P1, nullptr, sms, err, s);
+  if (h.pairs)
+    launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)h.groups, nullptr, h.pairs,
+                      so.id_bits, b.P1 + h.direct, nullptr, nullptr, sms, err, s);
   launch_peq(e.keys, e.lens, n, peq, s);
   OutRows o;
   rc = prepare_out(out, cap, n_pairs, ar, &o);
@@ -955,6 +1006,12 @@ int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
   gs.bucket_start = p->bucket_start;
   gs.flags = p->flags;
   gs.gstatus = p->status;
+  const bool direct = p->group_mode != 1;  // bucket modes emit most candidates while grouping
+  if (direct) {
+    gs.cand = p->back.P1;
+    gs.cand_cap = p->pair_cap;
+    gs.cand_count = p->counters + 2;
+  }
   XTN_CK(expand_sort_launch(p->keys, p->lens, p->eqprev, p->rec_off, n, p->d, p->seq_rep,
                             p->id_bits, p->A, p->B, p->rec_cap, lo, p->hist, p->digit_base,
                             p->status, p->cfg_rec, p->hist_mode, p->group_mode, gs, p->sms, p->err,
@@ -965,7 +1022,8 @@ int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
   launch_scan_group_pairs(p->S, p->E, (int64_t)p->g_cap, p->counters, p->pair_off, p->status,
                           p->err, s);
   launch_emit_pairs(sorted, p->rec_cap, p->S, p->pair_off, (int64_t)p->g_cap, p->counters,
-                    p->pair_cap, p->id_bits, p->back.P1, p->counters + 1, p->sms, p->err, s);
+                    p->pair_cap, p->id_bits, p->back.P1, direct ? p->counters + 2 : nullptr,
+                    p->counters + 1, p->sms, p->err, s);
   launch_peq(p->keys, p->lens, n, p->peq, s);
   XTN_CK(cudaGetLastError());
   return launch_back(p->back, p->pair_cap, p->counters + 1, 2 * p->id_bits, p->id_bits, p->peq,

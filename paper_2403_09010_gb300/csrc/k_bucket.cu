@@ -235,6 +235,8 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
              const uint64_t* __restrict__ n_dev,
              const unsigned long long* __restrict__ bucket_start, int G, int kbits, int lo, int L,
              int cap, uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts,
+             uint64_t* __restrict__ cand, uint64_t cand_cap,
+             unsigned long long* __restrict__ cand_count, int id_bits,
              uint32_t* __restrict__ err) {
   using C = Bk<HASH>;
   constexpr int ITEMS = C::ITEMS;
@@ -309,6 +311,61 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
     if (flags)
       write_flags(p, m, [&](int64_t j) { return gkey_of(s_k[j]); }, flags, tile_counts, tile_first,
                   acc0, acc1);
+    __syncthreads();  // s_k and the tables are reused by the next segment
+  };
+
+  // ---- candidate pairs of a grouped segment, straight from shared memory ----
+  // s_k[0, m) holds the groups contiguously, the group of slot h starting at
+  // start(h) (packed u16 in tc, slot order).  Every pair of a group of two or
+  // more records becomes a candidate word (min id << id_bits | max id),
+  // appended to `cand`.  Warp w owns slots w*32 + l + r*THREADS (its lanes
+  // read consecutive slots); it counts its pairs, reserves room with one
+  // atomic, then walks its groups: each group's pairs are spread over the
+  // lanes.  No block-wide step is needed.
+  auto emit_segment = [&](int m, const uint32_t* tc) {
+    constexpr int ROUNDS = C::H / BK_THREADS;
+    auto start_of = [&](uint32_t h) -> uint32_t {
+      return h < (uint32_t)C::H ? (tc[h >> 1] >> ((h & 1) * 16)) & 0xffffu : (uint32_t)m;
+    };
+    const uint64_t idmask = (1ull << id_bits) - 1ull;
+    uint32_t np = 0;
+#pragma unroll 4
+    for (int r = 0; r < ROUNDS; ++r) {
+      const uint32_t h = (uint32_t)(r * BK_THREADS) + warp * 32 + lane;
+      const uint32_t c = start_of(h + 1) - start_of(h);
+      if (c >= 2) np += c * (c - 1) / 2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(FULL_MASK, np, o);
+    unsigned long long base = 0;
+    if (lane == 0 && np) {
+      base = atomicAdd(cand_count, (unsigned long long)np);
+      if (base + np > cand_cap) atomicOr(err, DERR_CAPACITY);
+    }
+    uint64_t off = __shfl_sync(FULL_MASK, base, 0);
+    for (int r = 0; r < ROUNDS; ++r) {
+      const uint32_t h = (uint32_t)(r * BK_THREADS) + warp * 32 + lane;
+      const uint32_t st = start_of(h), c = start_of(h + 1) - st;
+      uint32_t groups = __ballot_sync(FULL_MASK, c >= 2);
+      while (groups) {
+        const int src = __ffs(groups) - 1;
+        groups &= groups - 1;
+        const uint32_t gst = __shfl_sync(FULL_MASK, st, src);
+        const uint32_t gc = __shfl_sync(FULL_MASK, c, src);
+        const uint32_t pairs = gc * (gc - 1) / 2;
+        for (uint32_t l = lane; l < pairs; l += 32) {
+          // colex unranking: l = b (b - 1) / 2 + a, a < b
+          uint32_t b = (uint32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)l)) * 0.5f);
+          while (b * (b - 1) / 2 > l) --b;
+          while ((b + 1) * b / 2 <= l) ++b;
+          const uint32_t a = l - b * (b - 1) / 2;
+          const uint64_t ia = s_k[gst + a] & idmask, ib = s_k[gst + b] & idmask;
+          if (off + l < cand_cap)
+            cand[off + l] = ((ia < ib ? ia : ib) << id_bits) | (ia < ib ? ib : ia);
+        }
+        off += pairs;
+      }
+    }
     __syncthreads();  // s_k and the tables are reused by the next segment
   };
 
@@ -388,6 +445,10 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
         }
       }
       __syncthreads();
+      if (cand) {
+        emit_segment(m, tc);
+        return;
+      }
     } else {
       const int passes = (L + kb + C::BITS - 1) / C::BITS;
       uint16_t rank[ITEMS];
@@ -420,6 +481,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
 
   // ---- one bucket [p, q) larger than `cap`, sorted in global memory ----
   auto large = [&](int64_t p, int64_t q) {
+    if (cand && threadIdx.x == 0) atomicAdd(cand_count + 1, (unsigned long long)(q - p));
     const uint64_t lmask = (1ull << L) - 1ull;  // one bucket: the low L bits decide
     const int passes = (L + C::BITS - 1) / C::BITS;
     uint64_t* src = A;
@@ -541,7 +603,8 @@ GroupingShape choose_grouping(uint64_t n_rec, int hs, bool hash) {
 
 void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
                    const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
-                   uint64_t* flags, uint64_t* tile_counts, uint32_t* err, cudaStream_t s) {
+                   uint64_t* flags, uint64_t* tile_counts, uint64_t* cand, uint64_t cand_cap,
+                   uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s) {
   if (n <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -560,11 +623,13 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
   if (hash) {
     prof_begin(s, "k_bucket_group", bytes);
     k_bucket<true><<<(unsigned)blocks, BK_THREADS, Bk<true>::bytes, s>>>(
-        A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, err);
+        A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, cand, cand_cap,
+        reinterpret_cast<unsigned long long*>(cand_count), id_bits, err);
   } else {
     prof_begin(s, "k_bucket_sort", bytes);
     k_bucket<false><<<(unsigned)blocks, BK_THREADS, Bk<false>::bytes, s>>>(
-        A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, err);
+        A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, nullptr, 0, nullptr,
+        0, err);
   }
   prof_end(s);
 }

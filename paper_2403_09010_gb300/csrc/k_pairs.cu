@@ -381,18 +381,22 @@ __global__ void __launch_bounds__(EMIT_THREADS)
     k_emit_pairs(const uint64_t* __restrict__ keys, uint64_t n_keys, const uint32_t* __restrict__ S,
                  const uint64_t* __restrict__ pair_off, int64_t n_groups_cap,
                  const uint64_t* __restrict__ n_groups_dev, uint64_t pair_cap, uint32_t id_bits,
-                 uint64_t* __restrict__ out, uint64_t* __restrict__ n_pairs_out,
-                 uint32_t* __restrict__ err) {
+                 uint64_t* __restrict__ out, const uint64_t* __restrict__ out_base,
+                 uint64_t* __restrict__ n_pairs_out, uint32_t* __restrict__ err) {
   __shared__ uint64_t s_off[EMIT_TILE + 1];
   __shared__ int64_t s_k0, s_k1;
   // group count and pair count may only be known on the device
   const int64_t n_groups = n_groups_dev ? min((int64_t)*n_groups_dev, n_groups_cap) : n_groups_cap;
   const uint64_t n_all = pair_off[n_groups];
+  // words already in `out` (written by the bucket pass): ours follow them
+  const uint64_t base = out_base ? *out_base : 0ull;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (n_pairs_out) *n_pairs_out = n_all;
-    if (n_all > pair_cap) atomicOr(err, DERR_CAPACITY);
+    if (n_pairs_out) *n_pairs_out = base + n_all;
+    if (base + n_all > pair_cap) atomicOr(err, DERR_CAPACITY);
   }
-  const uint64_t n_pairs = n_all < pair_cap ? n_all : pair_cap;
+  const uint64_t room = base < pair_cap ? pair_cap - base : 0ull;
+  const uint64_t n_pairs = n_all < room ? n_all : room;
+  out += base;
   const uint64_t idmask = (1ull << id_bits) - 1ull;
   for (uint64_t t0 = (uint64_t)blockIdx.x * EMIT_TILE; t0 < n_pairs;
        t0 += (uint64_t)gridDim.x * EMIT_TILE) {
@@ -439,14 +443,16 @@ __global__ void __launch_bounds__(EMIT_THREADS)
 
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        const uint64_t* pair_off, int64_t n_groups, const uint64_t* n_groups_dev,
-                       uint64_t pair_cap, uint32_t id_bits, uint64_t* out, uint64_t* n_pairs_out,
-                       int sms, uint32_t* err, cudaStream_t s) {
+                       uint64_t pair_cap, uint32_t id_bits, uint64_t* out,
+                       const uint64_t* out_base, uint64_t* n_pairs_out, int sms, uint32_t* err,
+                       cudaStream_t s) {
   if (pair_cap == 0 || n_groups <= 0) return;
   const uint64_t tiles = (pair_cap + EMIT_TILE - 1) / EMIT_TILE;
   const int blocks = (int)std::min<uint64_t>(tiles, (uint64_t)sms * 8);
   prof_begin(s, "k_emit_pairs", (double)pair_cap * (8.0 + 16.0));
   k_emit_pairs<<<blocks, EMIT_THREADS, 0, s>>>(keys, n_keys, S, pair_off, n_groups, n_groups_dev,
-                                               pair_cap, id_bits, out, n_pairs_out, err);
+                                               pair_cap, id_bits, out, out_base, n_pairs_out,
+                                               err);
   prof_end(s);
 }
 

@@ -200,6 +200,145 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
     if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
 }
 
+// Packed expansion for d <= 2.  A warp takes PACK_SEQS consecutive
+// sequences; lane i < PACK_SEQS first prepares sequence i alone (prefix sums
+// of the polynomial fingerprint, run starts, canonical variant count), then
+// the whole warp walks the batch's records as one stream: record t of the
+// batch belongs to the sequence whose start (exclusive scan of the counts) is
+// the largest <= t, found by a 4-step search over the lanes' starts.  Every
+// lane computes a record in every round and the batch's records are
+// contiguous in the output, so the stores stay coalesced; no warp-wide work
+// is spent per sequence.  16 sequences a batch keep the per-warp tables at
+// about 4 KB, so that enough warps fit on an SM to hide the arithmetic's
+// latency.
+constexpr int PACK_WARPS = 8;
+constexpr int PACK_SEQS = 16;
+constexpr int PACK_STRIDE = XTN_MAX_LEN + 3;  // P[0 .. L + 2]
+
+struct PackedSeqs {
+  uint32_t Plo[PACK_SEQS][PACK_STRIDE];
+  uint32_t Phi[PACK_SEQS][PACK_STRIDE];
+  uint8_t rs[PACK_SEQS][XTN_MAX_LEN + 1];
+  uint8_t ds[PACK_SEQS][XTN_MAX_LEN / 2 + 1];
+};
+
+__global__ void __launch_bounds__(PACK_WARPS * 32)
+    k_expand_packed(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens,
+                    const uint32_t* __restrict__ eqprev, const uint64_t* __restrict__ rec_off,
+                    int64_t n, int d, const uint32_t* __restrict__ seq_rep, uint32_t id_bits,
+                    uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist,
+                    int hist_lo, int hist_passes, int hist_hi, uint32_t* __restrict__ err) {
+  __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  __shared__ VariantTables s_tab;
+  __shared__ PackedSeqs s_seq[PACK_WARPS];
+  for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  init_variant_tables(&s_tab);
+  __syncthreads();
+  PackedSeqs* ps = &s_seq[threadIdx.x >> 5];
+  const uint32_t lane = lane_id();
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t idmask = (id_bits >= 64) ? ~0ull : ((1ull << id_bits) - 1ull);
+  const int last_bits = hist_hi - hist_lo - 8 * (hist_passes - 1);
+  const uint32_t last_mask = (1u << last_bits) - 1u;
+  static_assert(PACK_SEQS <= 32 && (PACK_SEQS & (PACK_SEQS - 1)) == 0, "power of two <= 32");
+  for (int64_t s0 = warp0 * PACK_SEQS; s0 < n; s0 += n_warps * PACK_SEQS) {
+    const int64_t my = s0 + lane;
+    // ---- this lane's sequence
+    uint32_t L = 0, R = 0, nD = 0, total = 0;
+    uint64_t salt = 0, base = 0;
+    if (lane < (uint32_t)PACK_SEQS && my < n) {
+      Key128 k = keys[my];
+      L = lens[my];
+      const uint32_t eq = eqprev[my];
+      base = rec_off[my];
+      const uint64_t cnt = rec_off[my + 1] - base;
+      if (seq_rep) salt = rep_salt(seq_rep[my]);
+      if (L > XTN_MAX_LEN) L = XTN_MAX_LEN;  // encode rejects longer ones
+      uint64_t acc = 0, pw = 1;
+      ps->Plo[lane][0] = 0u;
+      ps->Phi[lane][0] = 0u;
+      for (uint32_t p = 0; p < L; ++p) {
+        acc += (uint64_t)(uint32_t)(k.lo & 31u) * pw;
+        pw *= HASH_B;
+        k.lo = (k.lo >> 5) | (k.hi << 59);
+        k.hi >>= 5;
+        ps->Plo[lane][p + 1] = (uint32_t)acc;
+        ps->Phi[lane][p + 1] = (uint32_t)(acc >> 32);
+      }
+      for (uint32_t p = L + 1; p <= L + 2; ++p) {
+        ps->Plo[lane][p] = (uint32_t)acc;
+        ps->Phi[lane][p] = (uint32_t)(acc >> 32);
+      }
+      const uint32_t all = L ? (0xffffffffu >> (32 - L)) : 0u;
+      uint32_t runs = ~eq & all;
+      uint32_t dbl = runs & (eq >> 1);
+      R = __popc(runs);
+      nD = __popc(dbl);
+      for (uint32_t i = 0; runs; ++i, runs &= runs - 1) ps->rs[lane][i] = (uint8_t)(__ffs(runs) - 1);
+      for (uint32_t i = 0; dbl; ++i, dbl &= dbl - 1) ps->ds[lane][i] = (uint8_t)(__ffs(dbl) - 1);
+      total = canonical_total_d2(SeqShape{L, R, nD}, d);
+      if (total != cnt || base + cnt > n_rec) {
+        atomicOr(err, DERR_RANGE);
+        total = 0;
+      }
+    }
+    // ---- the batch's records, 32 at a time
+    uint32_t start = total;  // exclusive scan of the totals over lanes
+#pragma unroll
+    for (int o = 1; o < PACK_SEQS; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL_MASK, start, o);
+      if (lane >= (uint32_t)o) start += t;
+    }
+    const uint32_t T = __shfl_sync(FULL_MASK, start, PACK_SEQS - 1);
+    start -= total;
+    const uint64_t base0 = __shfl_sync(FULL_MASK, base, 0);
+    __syncwarp();  // the tables written above are read by every lane below
+    for (uint32_t t0 = 0; t0 < T; t0 += 32) {
+      const uint32_t t = t0 + lane;
+      // largest j with start[j] <= t (starts do not decrease)
+      uint32_t j = 0;
+#pragma unroll
+      for (int step = PACK_SEQS / 2; step > 0; step >>= 1) {
+        const uint32_t sj = __shfl_sync(FULL_MASK, start, (int)(j + step));
+        if (sj <= t) j += step;
+      }
+      const uint32_t sj = __shfl_sync(FULL_MASK, start, (int)j);
+      const uint32_t Lj = __shfl_sync(FULL_MASK, L, (int)j);
+      const uint32_t Rj = __shfl_sync(FULL_MASK, R, (int)j);
+      const uint32_t Dj = __shfl_sync(FULL_MASK, nD, (int)j);
+      const uint64_t saltj = __shfl_sync(FULL_MASK, salt, (int)j);
+      if (t < T) {
+        const uint32_t v = t - sj;
+        // canonical variant v of sequence j (numbering of canonical_fingerprint_d2)
+        const uint32_t u = v - 1 - Rj;
+        const uint32_t c2 = Rj * (Rj - 1) / 2;
+        const bool single = v >= 1 && v <= Rj;
+        const bool pair = v > Rj && u < c2;
+        const bool dbl = v > Rj && u >= c2;
+        const uint32_t pr = s_tab.pair[pair ? u : 0u];
+        const uint32_t a = ps->rs[j][single ? v - 1 : (pr & 255u)];
+        const uint32_t b = ps->rs[j][pr >> 8];
+        const uint32_t c = ps->ds[j][dbl ? u - c2 : 0u];
+        const uint32_t p1 = single || pair ? a : (dbl ? c : Lj);
+        const uint32_t p2 = pair ? b : (dbl ? c + 1 : (single ? Lj : Lj + 1));
+        auto P = [&](uint32_t x) {
+          return ((uint64_t)ps->Phi[j][x] << 32) | ps->Plo[j][x];
+        };
+        const uint64_t h = P(p1) + HASH_BINV * ((P(p2) - P(p1 + 1)) +
+                                                HASH_BINV * (P(Lj) - P(p2 + 1)));
+        const uint64_t rec = (mix64(h ^ saltj) & ~idmask) | (uint64_t)(s0 + j);
+        out[base0 + t] = rec;
+        count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+      }
+    }
+    __syncwarp();  // the next batch overwrites the tables
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+}
+
 // Match vectors: peq[i * PEQ_STRIDE + c - 1] = {positions p of sequence i with code c}.
 constexpr int PEQ_THREADS = 128;
 
@@ -269,8 +408,17 @@ void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqpr
   int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   if (blocks < 1) blocks = 1;
   prof_begin(s, "k_expand", (double)n_rec * 8.0 + (double)n * 29.0);
-  k_expand<<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits,
-                                             out, n_rec, hist, hist_lo, passes, hist_hi, err);
+  if (d <= 2) {
+    const int pblocks = (int)std::min<int64_t>(
+        (n + PACK_WARPS * PACK_SEQS - 1) / (PACK_WARPS * PACK_SEQS), (int64_t)sms * 8);
+    k_expand_packed<<<pblocks > 0 ? pblocks : 1, PACK_WARPS * 32, 0, s>>>(
+        keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec, hist, hist_lo, passes,
+        hist_hi, err);
+  } else {
+    k_expand<<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, eqprev, rec_off, n, d, seq_rep,
+                                               id_bits, out, n_rec, hist, hist_lo, passes, hist_hi,
+                                               err);
+  }
   prof_end(s);
 }
 

@@ -75,9 +75,15 @@ int bucket_capacity(bool hash);
 // With `flags` (zeroed, group_flag_words(n)) and `tile_counts` (zeroed, one
 // per GROUP_FLAG_TILE positions) also the head/tail flags k_group_write
 // reads.  cap: records per shared-memory segment (0 = the full capacity).
+// With `cand` (hash only): buckets that fit a segment write no records and no
+// flags but append their candidate pair words (min id << id_bits | max id)
+// to cand[0, cand_cap), counting them in cand_count[0] (DERR_CAPACITY past
+// the capacity); larger buckets go the flag route as before and add their
+// record count to cand_count[1].
 void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
                    const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
-                   uint64_t* flags, uint64_t* tile_counts, uint32_t* err, cudaStream_t s);
+                   uint64_t* flags, uint64_t* tile_counts, uint64_t* cand, uint64_t cand_cap,
+                   uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s);
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
 size_t group_status_bytes(int64_t n);
@@ -98,10 +104,13 @@ void launch_group_flags(const uint64_t* keys, int64_t n, const uint64_t* n_dev, 
 void launch_group_finish(const uint64_t* flags, int64_t n, const uint64_t* n_dev, uint32_t* S,
                          uint32_t* E, uint64_t cap, uint64_t* status, uint32_t* err,
                          uint64_t* n_groups, cudaStream_t s);
+// Candidate words of the groups [S, E] into out[base + t], t < pairs of the
+// groups, base = *out_base (0 when null); *n_pairs_out = base + pairs.
 void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        const uint64_t* pair_off, int64_t n_groups, const uint64_t* n_groups_dev,
-                       uint64_t pair_cap, uint32_t id_bits, uint64_t* out, uint64_t* n_pairs_out,
-                       int sms, uint32_t* err, cudaStream_t s);
+                       uint64_t pair_cap, uint32_t id_bits, uint64_t* out,
+                       const uint64_t* out_base, uint64_t* n_pairs_out, int sms, uint32_t* err,
+                       cudaStream_t s);
 
 // k_verify.cu --------------------------------------------------------------
 size_t verify_status_bytes(int64_t n);
