@@ -318,34 +318,24 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   // s_k[0, m) holds the groups contiguously, the group of slot h starting at
   // start(h) (packed u16 in tc, slot order).  Every pair of a group of two or
   // more records becomes a candidate word (min id << id_bits | max id),
-  // appended to `cand`.  Warp w owns slots w*32 + l + r*THREADS (its lanes
-  // read consecutive slots); it counts its pairs, reserves room with one
-  // atomic, then walks its groups: each group's pairs are spread over the
-  // lanes.  No block-wide step is needed.
-  auto emit_segment = [&](int m, const uint32_t* tc) {
-    constexpr int ROUNDS = C::H / BK_THREADS;
+  // appended to `cand` from `off` on (room reserved per warp during the slot
+  // scan).  gmask marks this thread's slots with such groups (bit k = slot
+  // threadIdx.x * H / THREADS + k); the warp takes the marked slots one at a
+  // time and spreads each group's pairs over its lanes.  No block-wide step.
+  auto emit_segment = [&](int m, const uint32_t* tc, uint32_t gmask, uint64_t off) {
+    constexpr uint32_t PER = C::H / BK_THREADS;
     auto start_of = [&](uint32_t h) -> uint32_t {
       return h < (uint32_t)C::H ? (tc[h >> 1] >> ((h & 1) * 16)) & 0xffffu : (uint32_t)m;
     };
     const uint64_t idmask = (1ull << id_bits) - 1ull;
-    uint32_t np = 0;
-#pragma unroll 4
-    for (int r = 0; r < ROUNDS; ++r) {
-      const uint32_t h = (uint32_t)(r * BK_THREADS) + warp * 32 + lane;
-      const uint32_t c = start_of(h + 1) - start_of(h);
-      if (c >= 2) np += c * (c - 1) / 2;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(FULL_MASK, np, o);
-    unsigned long long base = 0;
-    if (lane == 0 && np) {
-      base = atomicAdd(cand_count, (unsigned long long)np);
-      if (base + np > cand_cap) atomicOr(err, DERR_CAPACITY);
-    }
-    uint64_t off = __shfl_sync(FULL_MASK, base, 0);
-    for (int r = 0; r < ROUNDS; ++r) {
-      const uint32_t h = (uint32_t)(r * BK_THREADS) + warp * 32 + lane;
-      const uint32_t st = start_of(h), c = start_of(h + 1) - st;
+    while (__any_sync(FULL_MASK, gmask != 0)) {
+      uint32_t st = 0, c = 0;
+      if (gmask) {
+        const uint32_t h = threadIdx.x * PER + (uint32_t)(__ffs(gmask) - 1);
+        gmask &= gmask - 1;
+        st = start_of(h);
+        c = start_of(h + 1) - st;
+      }
       uint32_t groups = __ballot_sync(FULL_MASK, c >= 2);
       while (groups) {
         const int src = __ffs(groups) - 1;
@@ -427,11 +417,34 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
         tot += (w[k] & 0xffffu) + (w[k] >> 16);
       }
       uint32_t run = block_excl_scan(tot, s_wsum);
+      // with `cand`: slots of this thread holding groups of two or more (bit
+      // k = slot threadIdx.x * PER + k) and their pairs
+      uint32_t gmask = 0, np = 0;
 #pragma unroll
       for (int k = 0; k < PER / 2; ++k) {
         const uint32_t a = w[k] & 0xffffu, b = w[k] >> 16;
         tc[threadIdx.x * (PER / 2) + k] = run | ((run + a) << 16);
         run += a + b;
+        if (a >= 2) {
+          gmask |= 1u << (2 * k);
+          np += a * (a - 1) / 2;
+        }
+        if (b >= 2) {
+          gmask |= 2u << (2 * k);
+          np += b * (b - 1) / 2;
+        }
+      }
+      uint64_t cbase = 0;  // where this thread's warp writes its candidates
+      if (cand) {
+        uint32_t wp = np;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wp += __shfl_xor_sync(FULL_MASK, wp, o);
+        unsigned long long b = 0;
+        if (lane == 0 && wp) {
+          b = atomicAdd(cand_count, (unsigned long long)wp);
+          if (b + wp > cand_cap) atomicOr(err, DERR_CAPACITY);
+        }
+        cbase = __shfl_sync(FULL_MASK, b, 0);
       }
       __syncthreads();
 #pragma unroll
@@ -446,7 +459,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
       }
       __syncthreads();
       if (cand) {
-        emit_segment(m, tc);
+        emit_segment(m, tc, gmask, cbase);
         return;
       }
     } else {
@@ -618,7 +631,11 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
   const int full = bucket_capacity(hash);
   if (cap <= 0 || cap > full) cap = full;
   const uint64_t blocks = ((uint64_t)1 << g.G) >> g.kbits;
-  const double bytes = (double)n * 16.0 + (flags ? (double)n / 4.0 : 0.0);
+  // algorithmic bytes: every record read once; written back unless the
+  // candidates leave straight from shared memory (their words are not counted:
+  // their number is unknown at launch and small next to the records)
+  const double bytes = (hash && cand) ? (double)n * 8.0
+                                      : (double)n * 16.0 + (flags ? (double)n / 4.0 : 0.0);
   const unsigned long long* bs = reinterpret_cast<const unsigned long long*>(bucket_start);
   if (hash) {
     prof_begin(s, "k_bucket_group", bytes);
