@@ -26,10 +26,16 @@
 namespace xtn {
 
 // 'A'..'Z' -> residue code (alphabetical order of the 20 one-letter codes),
-// 0 for letters outside the alphabet.
-__constant__ uint8_t c_letter_code[26] = {
-    1,  0,  2,  3,  4,  5,  6,  7,  8, 0, 9,  10, 11,   // A B C D E F G H I J K L M
-    12, 0, 13, 14, 15, 16, 17, 0, 18, 19, 0, 20, 0};     // N O P Q R S T U V W X Y Z
+// 0 for letters outside the alphabet (B J O U X Z) and for anything else.
+// Computed, not looked up: lanes of a warp read different letters, which a
+// constant-memory table would serve one at a time.
+constexpr uint32_t NOT_RESIDUE = (1u << 1) | (1u << 9) | (1u << 14) | (1u << 20) | (1u << 23) |
+                                 (1u << 25);  // B J O U X Z
+__device__ __forceinline__ uint32_t letter_code(uint32_t ch) {
+  const uint32_t x = ch - (uint32_t)'A';
+  if (x >= 26u || ((NOT_RESIDUE >> x) & 1u)) return 0u;
+  return x + 1u - (uint32_t)__popc(NOT_RESIDUE & ((1u << x) - 1u));
+}
 
 constexpr int ENCODE_WARPS = 8;
 
@@ -72,7 +78,7 @@ __global__ void __launch_bounds__(ENCODE_WARPS * 32)
     uint32_t prev = 0;
     for (uint32_t p = 0; p < L; ++p) {
       const uint32_t ch = shared_span ? buf[a - A + p] : seqs[a + p];
-      const uint32_t c = (ch >= 'A' && ch <= 'Z') ? c_letter_code[ch - 'A'] : 0u;
+      const uint32_t c = letter_code(ch);
       if (c == 0) atomicOr(err, DERR_BAD_RESIDUE);
       if (p > 0 && c == prev) eqprev |= 1u << p;
       prev = c;
@@ -89,7 +95,14 @@ __global__ void __launch_bounds__(ENCODE_WARPS * 32)
     keys[i] = key;
     lens[i] = (uint8_t)L;
     eqprev_out[i] = eqprev;
-    vcount[i] = canonical_count(eqprev, L, (uint32_t)d);
+    if (d <= 2) {  // closed form of canonical_count, the one k_expand checks against
+      const uint32_t all = L ? (0xffffffffu >> (32 - L)) : 0u;
+      const uint32_t runs = ~eqprev & all;
+      vcount[i] = canonical_total_d2(
+          SeqShape{L, (uint32_t)__popc(runs), (uint32_t)__popc(runs & (eqprev >> 1))}, d);
+    } else {
+      vcount[i] = canonical_count(eqprev, L, (uint32_t)d);
+    }
   }
 }
 

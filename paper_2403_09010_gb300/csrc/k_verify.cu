@@ -188,60 +188,75 @@ __global__ void __launch_bounds__(VER_THREADS)
   __shared__ uint32_t s_w[VER_THREADS / 32];
   __shared__ uint64_t s_prefix;
   const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t jmask = (1ull << j_bits) - 1ull;
   // persistent: every block takes tiles in start order until the input runs out
   for (;;) {
   const uint32_t tile = tile_id(ctr, &s_tile);
   const int64_t tbase = (int64_t)tile * VER_TILE;
   if (tbase >= n) break;
-  const int64_t base = tbase + (int64_t)threadIdx.x * VER_ITEMS;
-  const uint64_t jmask = (1ull << j_bits) - 1ull;
-  uint64_t prev = (base > 0 && base - 1 < n) ? pairs[base - 1] : ~0ull;
-  uint32_t keep = 0, cnt = 0;
-  uint32_t dist[VER_ITEMS];
+  // warp w covers positions [wbase, wbase + 32 * ITEMS), lane l position
+  // wbase + it * 32 + l of round it: reads coalesce and the rounds follow
+  // position order, so ballots compact each round in order
+  const int64_t wbase = tbase + (int64_t)warp * 32 * VER_ITEMS;
+  uint32_t keep = 0, wtotal = 0;
+  uint32_t rank[VER_ITEMS], dist[VER_ITEMS];
+  uint64_t word[VER_ITEMS];
 #pragma unroll
   for (int it = 0; it < VER_ITEMS; ++it) {
+    const int64_t p = wbase + it * 32 + lane;
+    bool ok = false;
     dist[it] = 0;
-    const int64_t p = base + it;
+    word[it] = 0;
     if (p < n) {
       const uint64_t w = pairs[p];
+      const uint64_t prev = p > 0 ? pairs[p - 1] : ~w;
       const uint64_t i = w >> j_bits, j = w & jmask;
-      bool ok = w != prev;
+      ok = w != prev;
       if (i >= n_i || j >= n_j) {
         atomicOr(err, DERR_RANGE);
         ok = false;
       }
       if (ok) dist[it] = edit_distance(peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]);
-      keep |= (uint32_t)ok << it;
-      cnt += ok;
-      prev = w;
+      word[it] = w;
     }
+    const uint32_t bal = __ballot_sync(FULL_MASK, ok);
+    rank[it] = wtotal + __popc(bal & lt_mask);
+    wtotal += __popc(bal);
+    keep |= (uint32_t)ok << it;
   }
-  uint32_t excl;
-  const uint32_t total = block_excl_scan_u32<VER_THREADS>(cnt, s_w, excl);
-  if (threadIdx.x < 32) {
+  if (lane == 0) s_w[warp] = wtotal;
+  __syncthreads();
+  uint32_t woff = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < VER_THREADS / 32; ++w) {
+    if (w < (int)warp) woff += s_w[w];
+    total += s_w[w];
+  }
+  if (warp == 0) {
     const uint64_t pre = warp_lookback(status, tile, total, err);
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       s_prefix = pre;
       if (tbase + VER_TILE >= n) *total_out = pre + total;
     }
   }
   __syncthreads();
-  int64_t o = (int64_t)(s_prefix + excl);
+  const int64_t o0 = (int64_t)(s_prefix + woff);
 #pragma unroll
   for (int it = 0; it < VER_ITEMS; ++it) {
     if (keep >> it & 1u) {
+      const int64_t o = o0 + rank[it];
       if (o < cap) {
-        const uint64_t w = pairs[base + it];
         xtn_triple t;
-        t.i = (uint32_t)(w >> j_bits);
-        t.j = (uint32_t)(w & jmask);
+        t.i = (uint32_t)(word[it] >> j_bits);
+        t.j = (uint32_t)(word[it] & jmask);
         t.dist = dist[it];
         out[o] = t;
       }
-      ++o;
     }
   }
-  __syncthreads();  // s_prefix and s_tile are reused by the next tile
+  __syncthreads();  // s_prefix, s_w and s_tile are reused by the next tile
   }
 }
 
