@@ -315,26 +315,24 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   };
 
   // ---- candidate pairs of a grouped segment, straight from shared memory ----
-  // s_k[0, m) holds the groups contiguously, the group of slot h starting at
-  // start(h) (packed u16 in tc, slot order).  Every pair of a group of two or
-  // more records becomes a candidate word (min id << id_bits | max id),
-  // appended to `cand` from `off` on (room reserved per warp during the slot
-  // scan).  gmask marks this thread's slots with such groups (bit k = slot
-  // threadIdx.x * H / THREADS + k); the warp takes the marked slots one at a
-  // time and spreads each group's pairs over its lanes.  No block-wide step.
-  auto emit_segment = [&](int m, const uint32_t* tc, uint32_t gmask, uint64_t off) {
+  // The ids of every group of two or more records lie contiguously in s_k
+  // (as u32), the group of slot h from start(h) (packed u16 in tc) with
+  // size tk[h].  Every pair of such a group becomes a candidate word
+  // (min id << id_bits | max id), appended to `cand` from `off` on (room
+  // reserved per warp during the slot scan).  gmask marks this thread's slots
+  // with such groups (bit k = slot threadIdx.x * H / THREADS + k); the warp
+  // takes the marked slots one at a time and spreads each group's pairs over
+  // its lanes.  No block-wide step.
+  auto emit_segment = [&](const uint32_t* tc, const uint32_t* tk, uint32_t gmask, uint64_t off) {
     constexpr uint32_t PER = C::H / BK_THREADS;
-    auto start_of = [&](uint32_t h) -> uint32_t {
-      return h < (uint32_t)C::H ? (tc[h >> 1] >> ((h & 1) * 16)) & 0xffffu : (uint32_t)m;
-    };
-    const uint64_t idmask = (1ull << id_bits) - 1ull;
+    const uint32_t* s_ids = reinterpret_cast<const uint32_t*>(s_k);
     while (__any_sync(FULL_MASK, gmask != 0)) {
       uint32_t st = 0, c = 0;
       if (gmask) {
         const uint32_t h = threadIdx.x * PER + (uint32_t)(__ffs(gmask) - 1);
         gmask &= gmask - 1;
-        st = start_of(h);
-        c = start_of(h + 1) - st;
+        st = (tc[h >> 1] >> ((h & 1) * 16)) & 0xffffu;
+        c = tk[h];
       }
       uint32_t groups = __ballot_sync(FULL_MASK, c >= 2);
       while (groups) {
@@ -349,7 +347,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
           while (b * (b - 1) / 2 > l) --b;
           while ((b + 1) * b / 2 <= l) ++b;
           const uint32_t a = l - b * (b - 1) / 2;
-          const uint64_t ia = s_k[gst + a] & idmask, ib = s_k[gst + b] & idmask;
+          const uint64_t ia = s_ids[gst + a], ib = s_ids[gst + b];
           if (off + l < cand_cap)
             cand[off + l] = ((ia < ib ? ia : ib) << id_bits) | (ia < ib ? ib : ia);
         }
@@ -409,12 +407,18 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
       // H / THREADS consecutive slots), written back over the counts
       constexpr int PER = C::H / BK_THREADS;
       static_assert(PER % 2 == 0, "whole count words per thread");
+      // With `cand` only the groups of two or more records are placed (as
+      // 4-byte ids): single records pair with nothing, so they get start
+      // NO_PLACE and leave no trace; such a slot's size goes to the key table
+      // (free now) for the emitter.
+      constexpr uint32_t NO_PLACE = 0xffffu;
       uint32_t w[PER / 2];
       uint32_t tot = 0;
 #pragma unroll
       for (int k = 0; k < PER / 2; ++k) {
         w[k] = tc[threadIdx.x * (PER / 2) + k];
-        tot += (w[k] & 0xffffu) + (w[k] >> 16);
+        const uint32_t a = w[k] & 0xffffu, b = w[k] >> 16;
+        tot += cand ? (a >= 2 ? a : 0u) + (b >= 2 ? b : 0u) : a + b;
       }
       uint32_t run = block_excl_scan(tot, s_wsum);
       // with `cand`: slots of this thread holding groups of two or more (bit
@@ -423,8 +427,19 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
 #pragma unroll
       for (int k = 0; k < PER / 2; ++k) {
         const uint32_t a = w[k] & 0xffffu, b = w[k] >> 16;
-        tc[threadIdx.x * (PER / 2) + k] = run | ((run + a) << 16);
-        run += a + b;
+        if (cand) {
+          const uint32_t h = threadIdx.x * PER + 2 * k;
+          const uint32_t sa = a >= 2 ? run : NO_PLACE;
+          run += a >= 2 ? a : 0u;
+          const uint32_t sb = b >= 2 ? run : NO_PLACE;
+          run += b >= 2 ? b : 0u;
+          tc[threadIdx.x * (PER / 2) + k] = sa | (sb << 16);
+          if (a >= 2) tk[h] = a;
+          if (b >= 2) tk[h + 1] = b;
+        } else {
+          tc[threadIdx.x * (PER / 2) + k] = run | ((run + a) << 16);
+          run += a + b;
+        }
         if (a >= 2) {
           gmask |= 1u << (2 * k);
           np += a * (a - 1) / 2;
@@ -447,6 +462,25 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
         cbase = __shfl_sync(FULL_MASK, b, 0);
       }
       __syncthreads();
+      if (cand) {
+        uint32_t* s_ids = reinterpret_cast<uint32_t*>(s_k);
+        const uint64_t idmask = (1ull << id_bits) - 1ull;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          if (wbase + i * 32 + (int)lane < m && sr[i] != 0xffffffffu) {
+            const uint32_t h = sr[i] >> 16;
+            const uint32_t start = (tc[h >> 1] >> ((h & 1) * 16)) & 0xffffu;
+            if (start != NO_PLACE) {
+              const uint32_t pos = start + (sr[i] & 0xffffu);
+              if (pos < (uint32_t)m) s_ids[pos] = (uint32_t)(key[i] & idmask);
+              else atomicOr(err, DERR_RANGE);
+            }
+          }
+        }
+        __syncthreads();
+        emit_segment(tc, tk, gmask, cbase);
+        return;
+      }
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         if (wbase + i * 32 + (int)lane < m && sr[i] != 0xffffffffu) {
@@ -458,10 +492,6 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
         }
       }
       __syncthreads();
-      if (cand) {
-        emit_segment(m, tc, gmask, cbase);
-        return;
-      }
     } else {
       const int passes = (L + kb + C::BITS - 1) / C::BITS;
       uint16_t rank[ITEMS];
