@@ -243,6 +243,22 @@ def test_grouping_modes_match_oracle(xtn, grouping, mode):
     assert np.array_equal(got[:, 0], ii) and np.array_equal(got[:, 1], jj), mode
 
 
+@pytest.mark.parametrize("mode", [0, 2])
+def test_plan_with_buckets_larger_than_shared_memory(xtn, grouping, mode):
+    # a plan emits the pairs of small buckets while grouping and those of
+    # large ones (here 700 copies, and with 512-record segments also some
+    # generator buckets) through the flag route, appended after them
+    grouping(mode)
+    bs, bo = gen.workload(gen.SELF_1M, 4000)
+    seqs, off, want = _with_copies(bs, bo, "CASSLGQETQYF", 700, 2)
+    # 700 copies of a 12-residue sequence: about 19.3 M candidate words
+    plan = xtn.Plan(off, 2, pair_capacity=30_000_000)
+    plan.run(torch.from_numpy(seqs).cuda())
+    got = _rows(plan.result())
+    plan.free()
+    assert got.shape == want.shape and np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_grouping_modes_query_index(xtn, grouping, mode):
     grouping(mode)
