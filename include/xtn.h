@@ -105,6 +105,13 @@ XTN_API int xtn_version(void);
  *   out, cap         : output rows and their capacity (out may be NULL when
  *                      cap == 0, to learn the count).
  *   n_out            : host; receives the exact number of result rows.
+ * Scratch comes from the device's stream-ordered pool and is released
+ * before the call returns; the call synchronises the stream three times
+ * (record count, candidate count, row count).  With the default grouping the
+ * candidate buffer is sized at half the record count before grouping; an
+ * input that needs more (thousands of copies of one sequence) is searched
+ * again with all-global grouping, which sizes it exactly, so the result is
+ * the same, only slower.
  * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, BUFFER_TOO_SMALL,
  * CUDA, DEVICE_TIMEOUT, TOO_LARGE.
  */
