@@ -127,6 +127,17 @@ class Server:
             return out[: n_out.value]
 
     # ------------------------------------------------------------- public
+    def warm(self, seqs, offsets):
+        """Run one search on every slot's stream before serving, so that no
+        request pays first-use costs (pool growth on a new stream)."""
+        s = np.asarray(seqs, np.uint8)
+        o = np.asarray(offsets, np.int64)
+        for k in range(self.slots):
+            self._search(s, o, self._streams[k])
+        if self._device_streams:
+            import torch
+            torch.cuda.synchronize()
+
     def submit(self, rid: int, seqs, offsets, arrival: float | None = None) -> _Pending:
         p = _Pending(rid, np.asarray(seqs, np.uint8), np.asarray(offsets, np.int64),
                      time.perf_counter() if arrival is None else arrival)

@@ -99,3 +99,17 @@ def test_cancel_before_dispatch():
     srv.close()
     assert np.array_equal(first.rows, alone(s, o))
     assert srv.stats()["requests"] == 1
+
+
+def test_warm_runs_one_search_per_slot():
+    calls = []
+
+    def fake(seqs, offsets, stream):
+        calls.append(stream)
+        return np.zeros((0, 3), np.uint32)
+
+    srv = serve.Server(None, slots=3, memory_budget=1 << 30, search_fn=fake, device_streams=False)
+    seqs, off = gen.from_strings(["CASSLG", "CASSF"])
+    srv.warm(seqs, off)
+    srv.close()
+    assert len(calls) == 3
