@@ -335,7 +335,8 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
                   in_passes ? std::min(64, lo + 8) : 64, sms, err, s);
     XTN_CK(cudaGetLastError());
     XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
-                             sorted, "k_onesweep_records", s, in_passes, n_rec_dev));
+                             sorted, "k_onesweep_records", s, in_passes, n_rec_dev, nullptr,
+                             onesweep_unstable_config()));
     if (gs.flags) {
       XTN_CK(cudaMemsetAsync(gs.gstatus, 0, group_status_bytes((int64_t)rec_cap), s));
       launch_group_flags(*sorted, (int64_t)rec_cap, n_rec_dev, lo, gs.flags, gs.gstatus, s);
@@ -353,7 +354,8 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
   XTN_CK(cudaGetLastError());
   uint64_t* X = A;
   XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, glo, 64, hist, digit_base, status, cfg, err,
-                           &X, "k_onesweep_records", s, in_passes, n_rec_dev, gs.bucket_start));
+                           &X, "k_onesweep_records", s, in_passes, n_rec_dev, gs.bucket_start,
+                           onesweep_unstable_config()));
   uint64_t* Y = X == A ? B : A;
   uint64_t* tile_counts = nullptr;
   if (gs.flags) {
@@ -441,7 +443,8 @@ int launch_back(const BackStage& b, uint64_t cand_cap, const uint64_t* n_cand_de
                            (int)pair_bits, sms, err, s);
   uint64_t* sorted = nullptr;
   XTN_CK(radix_sort_passes(b.P2, b.P1, (int64_t)cand_cap, 0, (int)pair_bits, b.hist, b.digit_base,
-                           b.status, cfg, err, &sorted, "k_onesweep_pairs", s, false, b.counters));
+                           b.status, cfg, err, &sorted, "k_onesweep_pairs", s, false, b.counters,
+                           nullptr, onesweep_unstable_config()));
   launch_unique_finalize(sorted, (int64_t)cand_cap, b.counters, j_bits, peq_i, lens_i, n_i, keys_j,
                          lens_j, n_j, rows, row_cap, b.status, err, b.counters + 1, s);
   XTN_CK(cudaGetLastError());

@@ -94,6 +94,17 @@ __device__ __forceinline__ void rank_items(const uint64_t (&key)[ITEMS], uint16_
                                            uint32_t* wh, uint32_t* mb, int64_t wbase, int64_t n,
                                            int shift, uint32_t dmask, uint32_t lane) {
   const uint32_t lt_mask = (1u << lane) - 1u;
+  if (MATCH == 4) {
+    // unstable: one shared-memory atomic per item.  Ranks within a warp
+    // follow no order, so only a pass whose input order does not matter may
+    // use it (the first pass of a sort).
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool valid = FULL || (wbase + i * 32 + lane < n);
+      if (valid) rank[i] = (uint16_t)atomicAdd(&wh[(uint32_t)(key[i] >> shift) & dmask], 1u);
+    }
+    return;
+  }
   if (MATCH == 3) {
     // ballot match; the lowest peer adds the group's size to the warp counter
     // with one shared atomic and hands the old count to its peers
@@ -365,8 +376,10 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 
 // Tile configurations (id, threads, items per thread, min blocks per SM,
 // ranking: 0 ballots / 1 match.any / 2 atomic-OR bins / 3 ballots with one
-// leader atomic per group, ranking chains).  Both sorts use configuration 9 by
-// default; the autotuner may pick others.
+// leader atomic per group / 4 unstable, one atomic per key, ranking chains).
+// Both sorts use configuration 9 by default; the autotuner may pick others
+// among 0-19.  Configuration 20 is only for the first pass of a sort, whose
+// input order does not matter.
 #define XTN_ONESWEEP_CONFIGS(X) \
   X(0, 256, 16, 3, 0, 1)           \
   X(1, 256, 24, 2, 0, 1)           \
@@ -387,7 +400,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   X(16, 256, 20, 3, 3, 1)       \
   X(17, 256, 16, 3, 3, 1)       \
   X(18, 256, 24, 2, 3, 1)       \
-  X(19, 512, 12, 2, 3, 1)
+  X(19, 512, 12, 2, 3, 1)       \
+  X(20, 256, 20, 3, 4, 1)
 
 int onesweep_tile(int cfg) {
   switch (cfg) {
@@ -399,7 +413,9 @@ int onesweep_tile(int cfg) {
   return 0;
 }
 
-int onesweep_configs() { return 20; }
+int onesweep_configs() { return 20; }  // the tunable ones; 20 is the unstable first pass
+
+int onesweep_unstable_config() { return 20; }
 
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    const uint64_t* n_dev, int shift, int bits, const uint64_t* digit_base,
@@ -451,8 +467,10 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
                               bool hist_in_passes, const uint64_t* n_dev,
-                              uint64_t* bucket_start) {
+                              uint64_t* bucket_start, int first_cfg) {
   const int passes = (hi - lo + 7) / 8;
+  // the status words are sized for cfg's tile
+  if (first_cfg >= 0 && onesweep_tile(first_cfg) != onesweep_tile(cfg)) first_cfg = -1;
   *sorted = a;
   if (n <= 1 || passes == 0) return cudaSuccess;
   // hist_in_passes: `hist` holds pass 0's counts on entry, pass p counts the
@@ -475,7 +493,8 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
     prof_begin(s, tag, (double)n * 16.0);
     unsigned long long* bs =
         p + 1 == passes ? reinterpret_cast<unsigned long long*>(bucket_start) : nullptr;
-    e = onesweep_launch(cfg, src, dst, n, n_dev, sh, bits, digit_base + p * RADIX, status, ctr, err,
+    e = onesweep_launch(p == 0 && first_cfg >= 0 ? first_cfg : cfg, src, dst, n, n_dev, sh, bits,
+                        digit_base + p * RADIX, status, ctr, err,
                         next, next_bits, bs, lo, s);
     prof_end(s);
     if (e != cudaSuccess) return e;

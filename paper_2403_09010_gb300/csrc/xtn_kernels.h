@@ -49,11 +49,15 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
 // bucket_start: when not null (2^(hi-lo) entries, all bits set on entry), the
 // last pass leaves in bucket_start[b] the first sorted position whose bits
 // [lo, hi) equal b; buckets without records keep all bits set.
+// first_cfg: configuration of the first pass (>= 0), e.g. the unstable one;
+// LSD order needs only the later passes to be stable.  Ignored when its tile
+// differs from cfg's.
 cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
                               bool hist_in_passes = false, const uint64_t* n_dev = nullptr,
-                              uint64_t* bucket_start = nullptr);
+                              uint64_t* bucket_start = nullptr, int first_cfg = -1);
+int onesweep_unstable_config();
 
 // k_bucket.cu --------------------------------------------------------------
 // Positions per flag tile of the group-bound kernels (head/tail counts are
