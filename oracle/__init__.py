@@ -13,6 +13,9 @@ ctypes. Every function returns numpy arrays of uint32 rows:
 * ``symdel_query``     (q, r, dist)                 -- steps 1-2 on the reference,
                                                        step 3 with the queries
 * ``bruteforce_self`` / ``bruteforce_query``        -- exhaustive search (pin)
+* ``hamming``; ``metric="hamming"`` of ``symdel_self`` / ``symdel_batched`` /
+  ``bruteforce_self``  -- the Hamming variant (the last step filters by
+  Hamming distance; unequal lengths are never neighbours)
 * ``neighbors_of``     (j, dist) for one i          -- plain definition, sampled checks
 * ``tcrdist_filter`` / ``tcrdist_allpairs``          -- TCRdist post-filter (Results)
 """
@@ -52,11 +55,15 @@ def _load():
     if _lib is not None:
         return _lib
     lib = ctypes.CDLL(build())
-    for name in ("xo_symdel_self", "xo_bruteforce_self"):
+    for name in ("xo_symdel_self", "xo_symdel_self_hamming", "xo_bruteforce_self"):
         getattr(lib, name).argtypes = [_P, _P, _I64, ctypes.c_int]
         getattr(lib, name).restype = _P
-    lib.xo_symdel_batched.argtypes = [_P, _P, _P, _I64, ctypes.c_int]
+    lib.xo_bruteforce_self_metric.argtypes = [_P, _P, _I64, ctypes.c_int, ctypes.c_int]
+    lib.xo_bruteforce_self_metric.restype = _P
+    lib.xo_symdel_batched.argtypes = [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
     lib.xo_symdel_batched.restype = _P
+    lib.xo_hamming.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+    lib.xo_hamming.restype = ctypes.c_int
     for name in ("xo_symdel_query", "xo_bruteforce_query"):
         getattr(lib, name).argtypes = [_P, _P, _I64, _P, _P, _I64, ctypes.c_int]
         getattr(lib, name).restype = _P
@@ -106,15 +113,22 @@ def _take(h) -> np.ndarray:
     return out
 
 
-def symdel_self(seqs, offsets, d: int) -> np.ndarray:
+_METRICS = {"levenshtein": 0, "hamming": 1}
+
+
+def symdel_self(seqs, offsets, d: int, metric: str = "levenshtein") -> np.ndarray:
     s, o = _prep(seqs, offsets)
-    return _take(_load().xo_symdel_self(_ptr(s), _ptr(o), o.size - 1, d))
+    if metric not in _METRICS:
+        raise ValueError(f"unknown metric {metric!r}")
+    fn = _load().xo_symdel_self_hamming if metric == "hamming" else _load().xo_symdel_self
+    return _take(fn(_ptr(s), _ptr(o), o.size - 1, d))
 
 
-def symdel_batched(seqs, offsets, rep_offsets, d: int) -> np.ndarray:
+def symdel_batched(seqs, offsets, rep_offsets, d: int, metric: str = "levenshtein") -> np.ndarray:
     s, o = _prep(seqs, offsets)
     r = np.ascontiguousarray(rep_offsets, dtype=np.int64)
-    return _take(_load().xo_symdel_batched(_ptr(s), _ptr(o), _ptr(r), r.size - 1, d))
+    return _take(_load().xo_symdel_batched(_ptr(s), _ptr(o), _ptr(r), r.size - 1, d,
+                                           _METRICS[metric]))
 
 
 def symdel_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int) -> np.ndarray:
@@ -124,9 +138,10 @@ def symdel_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int) -> np.ndarray
                                          _ptr(qs), _ptr(qo), qo.size - 1, d))
 
 
-def bruteforce_self(seqs, offsets, d: int) -> np.ndarray:
+def bruteforce_self(seqs, offsets, d: int, metric: str = "levenshtein") -> np.ndarray:
     s, o = _prep(seqs, offsets)
-    return _take(_load().xo_bruteforce_self(_ptr(s), _ptr(o), o.size - 1, d))
+    return _take(_load().xo_bruteforce_self_metric(_ptr(s), _ptr(o), o.size - 1, d,
+                                                   _METRICS[metric]))
 
 
 def bruteforce_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int) -> np.ndarray:
@@ -152,6 +167,13 @@ def tcrdist_filter(seqs, offsets, triples, max_score: int) -> np.ndarray:
 def tcrdist_allpairs(seqs, offsets, lev_max: int, max_score: int) -> np.ndarray:
     s, o = _prep(seqs, offsets)
     return _take(_load().xo_tcrdist_allpairs(_ptr(s), _ptr(o), o.size - 1, lev_max, max_score))
+
+
+def hamming(a: str, b: str) -> int:
+    """Differing positions of two equal-length strings; -1 when the lengths
+    differ (never Hamming neighbours)."""
+    ab, bb = a.encode(), b.encode()
+    return _load().xo_hamming(ab, len(ab), bb, len(bb))
 
 
 def levenshtein(a: str, b: str) -> int:

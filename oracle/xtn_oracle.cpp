@@ -1,4 +1,5 @@
-// CPU oracle for symmetric-deletion (SymDel) Levenshtein neighbour search.
+// CPU oracle for symmetric-deletion (SymDel) Levenshtein neighbour search
+// (and its Hamming variant).
 //
 // TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the
 // benchmark's CPU-baseline leg may load this library. It shares no code,
@@ -66,6 +67,23 @@ int lev_full(const std::string& a, const std::string& b) {
   return D[la * w + lb];
 }
 
+// Hamming distance (Results, comparison with CompAIRR: the last step filters
+// by Hamming instead of Levenshtein distance): the number of positions at
+// which two strings of equal length differ; strings of different lengths are
+// never Hamming neighbours (returned as a distance no threshold admits).
+constexpr int NOT_NEIGHBOURS = 1 << 30;
+int hamming(const std::string& a, const std::string& b) {
+  if (a.size() != b.size()) return NOT_NEIGHBOURS;
+  int h = 0;
+  for (size_t p = 0; p < a.size(); ++p) h += a[p] != b[p];
+  return h;
+}
+
+// The last step's distance: 0 = Levenshtein, 1 = Hamming.
+int distance(const std::string& a, const std::string& b, int metric) {
+  return metric == 1 ? hamming(a, b) : lev_full(a, b);
+}
+
 // Step 1: all strings reachable from s by at most d single-character deletions.
 std::unordered_set<std::string> deletion_variants(const std::string& s, int d) {
   std::unordered_set<std::string> all{s};
@@ -98,7 +116,8 @@ Result* pack(std::vector<std::vector<uint32_t>>& rows, int width) {
 
 // Self search over sequences [lo, hi) with indices reported relative to lo.
 std::vector<std::vector<uint32_t>> symdel_self_range(const uint8_t* seqs, const int64_t* off,
-                                                     int64_t lo, int64_t hi, int d) {
+                                                     int64_t lo, int64_t hi, int d,
+                                                     int metric = 0) {
   const int64_t n = hi - lo;
   std::vector<std::string> s(n);
   for (int64_t i = 0; i < n; ++i) s[i] = seq_at(seqs, off, lo + i);
@@ -114,13 +133,16 @@ std::vector<std::vector<uint32_t>> symdel_self_range(const uint8_t* seqs, const 
   for (int64_t i = 0; i < n; ++i)
     for (const std::string& v : x[i])
       for (uint32_t j : table[v]) y.emplace_back(static_cast<uint32_t>(i), j);
-  // Step 4: keep unordered pairs once (i < j), verify by Lev <= d, dedup.
+  // Step 4: keep unordered pairs once (i < j), verify the distance, dedup.
+  // Two strings of one length with h <= d differing positions share the
+  // string left after deleting those positions from both, so every Hamming
+  // neighbour is a candidate too.
   std::vector<std::vector<uint32_t>> rows;
   std::sort(y.begin(), y.end());
   y.erase(std::unique(y.begin(), y.end()), y.end());
   for (auto& c : y) {
     if (c.first >= c.second) continue;
-    int dist = lev_full(s[c.first], s[c.second]);
+    int dist = distance(s[c.first], s[c.second], metric);
     if (dist <= d) rows.push_back({c.first, c.second, static_cast<uint32_t>(dist)});
   }
   sort_unique(rows);
@@ -196,6 +218,12 @@ void xo_result_copy(void* h, uint32_t* dst) {
 void xo_result_free(void* h) { delete static_cast<Result*>(h); }
 
 // ---------------- scalar helpers ----------------
+int xo_hamming(const uint8_t* a, int la, const uint8_t* b, int lb) {
+  const int h = hamming(std::string(reinterpret_cast<const char*>(a), la),
+                        std::string(reinterpret_cast<const char*>(b), lb));
+  return h == NOT_NEIGHBOURS ? -1 : h;
+}
+
 int xo_levenshtein(const uint8_t* a, int la, const uint8_t* b, int lb) {
   return lev_full(std::string(reinterpret_cast<const char*>(a), la),
                   std::string(reinterpret_cast<const char*>(b), lb));
@@ -220,12 +248,19 @@ void* xo_symdel_self(const uint8_t* seqs, const int64_t* off, int64_t n, int d) 
   return pack(rows, 3);
 }
 
+// The same with the Hamming distance in the last step.
+void* xo_symdel_self_hamming(const uint8_t* seqs, const int64_t* off, int64_t n, int d) {
+  auto rows = symdel_self_range(seqs, off, 0, n, d, 1);
+  return pack(rows, 3);
+}
+
 // Independent repertoires: rows (rep, i_local, j_local, dist), sorted.
+// metric: 0 = Levenshtein, 1 = Hamming.
 void* xo_symdel_batched(const uint8_t* seqs, const int64_t* off, const int64_t* rep_off,
-                        int64_t n_rep, int d) {
+                        int64_t n_rep, int d, int metric) {
   std::vector<std::vector<uint32_t>> all;
   for (int64_t r = 0; r < n_rep; ++r) {
-    auto rows = symdel_self_range(seqs, off, rep_off[r], rep_off[r + 1], d);
+    auto rows = symdel_self_range(seqs, off, rep_off[r], rep_off[r + 1], d, metric);
     for (auto& row : rows)
       all.push_back({static_cast<uint32_t>(r), row[0], row[1], row[2]});
   }
@@ -264,18 +299,24 @@ void* xo_symdel_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n
 }
 
 // Exhaustive search over all n(n-1)/2 pairs (the brute-force pin).
-void* xo_bruteforce_self(const uint8_t* seqs, const int64_t* off, int64_t n, int d) {
+// metric: 0 = Levenshtein, 1 = Hamming.
+void* xo_bruteforce_self_metric(const uint8_t* seqs, const int64_t* off, int64_t n, int d,
+                                int metric) {
   std::vector<std::string> s(n);
   for (int64_t i = 0; i < n; ++i) s[i] = seq_at(seqs, off, i);
   std::vector<std::vector<uint32_t>> rows;
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = i + 1; j < n; ++j) {
-      int dist = lev_full(s[i], s[j]);
+      int dist = distance(s[i], s[j], metric);
       if (dist <= d)
         rows.push_back({static_cast<uint32_t>(i), static_cast<uint32_t>(j),
                         static_cast<uint32_t>(dist)});
     }
   return pack(rows, 3);
+}
+
+void* xo_bruteforce_self(const uint8_t* seqs, const int64_t* off, int64_t n, int d) {
+  return xo_bruteforce_self_metric(seqs, off, n, d, 0);
 }
 
 // All (q, r) with Lev <= d by exhaustive comparison.

@@ -287,3 +287,71 @@ def test_tcrdist_filter_and_allpairs_agree():
     strs = gen.to_strings(seqs, off)
     for i, j, _, score in allp:
         assert oracle.tcrdist(strs[i], strs[j]) == score <= 24
+
+
+# ----------------------------------------------------------------- Hamming ---
+# The Hamming variant (Results, comparison with CompAIRR): the same SymDel
+# steps, with the last one filtering by Hamming distance.
+@pytest.mark.parametrize("a, b, dist", [("KAROLIN", "KATHRIN", 3), ("CASSF", "CASSF", 0),
+                                        ("ACDE", "WYKL", 4), ("", "", 0)])
+def test_hamming_textbook(a, b, dist):
+    assert oracle.hamming(a, b) == dist
+
+
+def test_hamming_unequal_lengths_are_never_neighbours():
+    assert oracle.hamming("CASS", "CAS") == -1
+    seqs, off = gen.from_strings(["CASS", "CAS", "CASSS"])
+    assert oracle.bruteforce_self(seqs, off, 3, "hamming").shape[0] == 0
+    assert oracle.symdel_self(seqs, off, 3, "hamming").shape[0] == 0
+    # ... while CASS, one deletion from each of the others, has two
+    # Levenshtein neighbours at d = 1 (CAS and CASSS are two apart)
+    assert oracle.symdel_self(seqs, off, 1).shape[0] == 2
+
+
+def test_hamming_is_at_least_levenshtein():
+    rng = random.Random(77)
+    for _ in range(300):
+        L = rng.randint(0, 10)
+        a = "".join(rng.choice("ACD") for _ in range(L))
+        b = "".join(rng.choice("ACD") for _ in range(L))
+        h, lev = oracle.hamming(a, b), oracle.levenshtein(a, b)
+        assert h == sum(x != y for x, y in zip(a, b))
+        assert lev <= h
+
+
+def test_hamming_ball_closed_form():
+    # all strings of length 4 over {A, C, D}: the ball of radius k around one
+    # of them holds sum_{i <= k} C(4, i) 2^i strings
+    alphabet = "ACD"
+    strs = ["".join(t) for t in itertools.product(alphabet, repeat=4)]
+    centre = strs.index("ACDA")
+    seqs, off = gen.from_strings(strs)
+    for d in range(4):
+        rows = oracle.bruteforce_self(seqs, off, d, "hamming")
+        mine = rows[(rows[:, 0] == centre) | (rows[:, 1] == centre)]
+        assert mine.shape[0] == sum(math.comb(4, i) * 2 ** i for i in range(1, d + 1))
+        assert np.array_equal(rows, oracle.symdel_self(seqs, off, d, "hamming"))
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_hamming_symdel_equals_bruteforce(d):
+    rng = random.Random(40 + d)
+    strs = _rand_strings(rng, 300, "AC", 0, 9)
+    seqs, off = gen.from_strings(strs)
+    want = oracle.bruteforce_self(seqs, off, d, "hamming")
+    assert np.array_equal(oracle.symdel_self(seqs, off, d, "hamming"), want)
+    g_seqs, g_off = gen.generate(1200, 300 + d, 0.3, 0.02)
+    assert np.array_equal(oracle.symdel_self(g_seqs, g_off, d, "hamming"),
+                          oracle.bruteforce_self(g_seqs, g_off, d, "hamming"))
+
+
+def test_hamming_batched_is_per_repertoire():
+    seqs, off, rep = gen.batched(n_rep=5, seed=12, size_min=50, size_max=400)
+    got = oracle.symdel_batched(seqs, off, rep, 2, "hamming")
+    parts = []
+    for r in range(rep.size - 1):
+        lo, hi = rep[r], rep[r + 1]
+        s, o = gen.from_strings(gen.to_strings(seqs, off)[lo:hi])
+        rows = oracle.bruteforce_self(s, o, 2, "hamming")
+        parts.append(np.column_stack([np.full(rows.shape[0], r, np.uint32), rows]))
+    assert np.array_equal(got, np.concatenate(parts))
