@@ -120,6 +120,20 @@ XTN_API int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t
                     int64_t* n_out, xtn_stream_t stream);
 
 /*
+ * The Hamming variant of the self-search (Results, comparison with
+ * CompAIRR): the same symmetric-deletion candidates, the last step filtering
+ * by Hamming distance instead.  Rows are {i, j, dist} with i < j, equal
+ * lengths and dist = the number of differing positions <= d, sorted by
+ * (i, j); sequences of different lengths are never neighbours.  Two
+ * sequences with h <= d differing positions share the string left after
+ * deleting those positions, so no neighbour is missed.  Arguments, batched
+ * mode and errors as xtn_search_self.
+ */
+XTN_API int xtn_search_self_hamming(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                                    const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out,
+                                    int64_t cap, int64_t* n_out, xtn_stream_t stream);
+
+/*
  * Build a device-resident index of a reference set: its encoded sequences
  * and its deletion variants, grouped by sorting (Appendix A, XTNeighbor steps
  * 1-4; the paper's multi-value hash map of the SymDel step list, realised as a

@@ -435,18 +435,18 @@ int launch_back(const BackStage& b, uint64_t cand_cap, const uint64_t* n_cand_de
                 uint32_t pair_bits, uint32_t j_bits, const uint32_t* peq_i, const uint8_t* lens_i,
                 uint64_t n_i, const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                 const uint32_t* seq_rep, int self_mode, int d, xtn_triple* rows, int64_t row_cap,
-                int sms, uint32_t* err, cudaStream_t s, int cfg) {
+                int sms, uint32_t* err, cudaStream_t s, int cfg, int metric = 0) {
   XTN_CK(cudaMemsetAsync(b.hist, 0, MAX_PASSES * RADIX * 4, s));
   XTN_CK(cudaMemsetAsync(b.counters, 0, 16, s));
   launch_verify_candidates(b.P1, cand_cap, n_cand_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
-                           n_j, seq_rep, self_mode, d, b.P2, cand_cap, b.counters, b.hist,
+                           n_j, seq_rep, self_mode, d, metric, b.P2, cand_cap, b.counters, b.hist,
                            (int)pair_bits, sms, err, s);
   uint64_t* sorted = nullptr;
   XTN_CK(radix_sort_passes(b.P2, b.P1, (int64_t)cand_cap, 0, (int)pair_bits, b.hist, b.digit_base,
                            b.status, cfg, err, &sorted, "k_onesweep_pairs", s, false, b.counters,
                            nullptr, onesweep_unstable_config()));
   launch_unique_finalize(sorted, (int64_t)cand_cap, b.counters, j_bits, peq_i, lens_i, n_i, keys_j,
-                         lens_j, n_j, rows, row_cap, b.status, err, b.counters + 1, s);
+                         lens_j, n_j, metric, rows, row_cap, b.status, err, b.counters + 1, s);
   XTN_CK(cudaGetLastError());
   return XTN_OK;
 }
@@ -515,10 +515,12 @@ __global__ void k_pair_total(const uint64_t* __restrict__ pair_off,
   *out = pair_off[*n_groups];
 }
 
-// mode: grouping mode (see g_grouping), -1 = the tuned one.
+// mode: grouping mode (see g_grouping), -1 = the tuned one.  metric: 0 =
+// Levenshtein, 1 = Hamming (the Hamming variant: the same candidates, the
+// last step filters by Hamming distance).
 int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                      const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
-                     int64_t* n_out, cudaStream_t s, int mode = -1) {
+                     int64_t* n_out, cudaStream_t s, int mode = -1, int metric = 0) {
   if (!n_out) return XTN_ERR_INVALID_ARG;
   *n_out = 0;
   if (n < 0 || d < 0 || d > XTN_MAX_D || cap < 0 || !offsets) return XTN_ERR_INVALID_ARG;
@@ -579,7 +581,8 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     XTN_CK(cudaStreamSynchronize(s));
     if (h.err & DERR_CAPACITY) {
       ar.release();
-      return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1);
+      return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
+                              metric);
     }
     if (h.err) return map_device_err(h.err);
     flagged = h.large > 0;
@@ -600,7 +603,8 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (n_pairs >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
   if (mode != 1 && n_pairs > direct.cand_cap) {
     ar.release();
-    return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1);
+    return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
+                            metric);
   }
 
   // back: the remaining candidates, verify, sort survivors, dedup
@@ -622,7 +626,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   rc = prepare_out(out, cap, n_pairs, ar, &o);
   if (rc) return rc;
   rc = launch_back(b, n_pairs, nullptr, 2 * so.id_bits, so.id_bits, peq, e.lens, n, e.keys, e.lens,
-                   n, seq_rep, 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs);
+                   n, seq_rep, 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs, metric);
   if (rc) return rc;
   XTN_CK(cudaMemcpyAsync(&h.pairs, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
@@ -1091,6 +1095,13 @@ int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int 
                     int64_t* n_out, xtn_stream_t stream) {
   return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_search_self_hamming(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                            const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out,
+                            int64_t cap, int64_t* n_out, xtn_stream_t stream) {
+  return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
+                               reinterpret_cast<cudaStream_t>(stream), -1, 1);
 }
 
 int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,

@@ -74,6 +74,33 @@ __device__ __forceinline__ uint32_t edit_distance(const uint32_t* __restrict__ p
   return score;
 }
 
+// Hamming distance (the last step of the Hamming variant, Results) between
+// pattern (match vectors peq) and text t of the same length n: the positions
+// p whose text residue's match vector lacks bit p.
+__device__ __forceinline__ uint32_t hamming_distance(const uint32_t* __restrict__ peq, Key128 t,
+                                                     uint32_t n) {
+  uint32_t match = 0;
+#pragma unroll
+  for (int j = 0; j < XTN_MAX_LEN; ++j) {
+    const uint32_t c = (uint32_t)(t.lo & 31u);
+    t.lo = (t.lo >> 5) | (t.hi << 59);
+    t.hi >>= 5;
+    if ((uint32_t)j < n && c - 1u < 20u) match |= __ldg(peq + (c - 1u)) & (1u << j);
+  }
+  return n - (uint32_t)__popc(match);
+}
+
+// The distance of the last step: metric 0 = Levenshtein (<= d needs
+// |m - n| <= d), 1 = Hamming (equal lengths only).  Returns d + 1 for a pair
+// that cannot be within d.
+__device__ __forceinline__ uint32_t pair_distance(int metric, int d,
+                                                  const uint32_t* __restrict__ peq, uint32_t m,
+                                                  Key128 t, uint32_t n) {
+  if (metric == 1) return m == n ? hamming_distance(peq, t, n) : (uint32_t)d + 1u;
+  if ((m > n ? m - n : n - m) > (uint32_t)d) return (uint32_t)d + 1u;
+  return edit_distance(peq, m, t, n);
+}
+
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_w, uint32_t& excl) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -102,7 +129,7 @@ __global__ void __launch_bounds__(256)
                         const uint32_t* __restrict__ peq_i, const uint8_t* __restrict__ lens_i,
                         uint64_t n_i, const Key128* __restrict__ keys_j,
                         const uint8_t* __restrict__ lens_j, uint64_t n_j,
-                        const uint32_t* __restrict__ seq_rep, int self_mode, int d,
+                        const uint32_t* __restrict__ seq_rep, int self_mode, int d, int metric,
                         uint64_t* __restrict__ surv, uint64_t surv_cap,
                         unsigned long long* __restrict__ n_surv, uint32_t* __restrict__ hist,
                         int hist_hi, uint32_t* __restrict__ err) {
@@ -127,11 +154,9 @@ __global__ void __launch_bounds__(256)
       if (!ok) atomicOr(err, DERR_RANGE);
       if (self_mode) ok = ok && i != j;
       if (ok && seq_rep) ok = seq_rep[i] == seq_rep[j];
-      if (ok) {
-        const uint32_t la = lens_i[i], lb = lens_j[j];
-        ok = (la > lb ? la - lb : lb - la) <= (uint32_t)d &&
-             edit_distance(peq_i + i * PEQ_STRIDE, la, keys_j[j], lb) <= (uint32_t)d;
-      }
+      if (ok)
+        ok = pair_distance(metric, d, peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]) <=
+             (uint32_t)d;
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
     if (bal) {
@@ -163,14 +188,14 @@ void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* 
                               uint32_t j_bits,
                               const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                               const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
-                              const uint32_t* seq_rep, int self_mode, int d, uint64_t* surv,
-                              uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist, int hist_hi,
-                              int sms, uint32_t* err, cudaStream_t s) {
+                              const uint32_t* seq_rep, int self_mode, int d, int metric,
+                              uint64_t* surv, uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist,
+                              int hist_hi, int sms, uint32_t* err, cudaStream_t s) {
   if (n == 0) return;
   const int blocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
   prof_begin(s, "k_verify_candidates", (double)n * (8.0 + 2 * 17.0 + 4.0 * 4));
   k_verify_candidates<<<blocks, 256, 0, s>>>(
-      cand, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep, self_mode, d, surv,
+      cand, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep, self_mode, d, metric, surv,
       surv_cap, reinterpret_cast<unsigned long long*>(n_surv), hist, hist_hi, err);
   prof_end(s);
 }
@@ -181,9 +206,9 @@ __global__ void __launch_bounds__(VER_THREADS)
                       const uint32_t* __restrict__ peq_i, const uint8_t* __restrict__ lens_i,
                       uint64_t n_i, const Key128* __restrict__ keys_j,
                       const uint8_t* __restrict__ lens_j, uint64_t n_j,
-                      xtn_triple* __restrict__ out, int64_t cap, uint64_t* __restrict__ status,
-                      uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
-                      uint64_t* __restrict__ total_out) {
+                      int metric, xtn_triple* __restrict__ out, int64_t cap,
+                      uint64_t* __restrict__ status, uint32_t* __restrict__ ctr,
+                      uint32_t* __restrict__ err, uint64_t* __restrict__ total_out) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_w[VER_THREADS / 32];
   __shared__ uint64_t s_prefix;
@@ -218,7 +243,9 @@ __global__ void __launch_bounds__(VER_THREADS)
         atomicOr(err, DERR_RANGE);
         ok = false;
       }
-      if (ok) dist[it] = edit_distance(peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]);
+      if (ok)
+        dist[it] = pair_distance(metric, XTN_MAX_LEN, peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j],
+                                 lens_j[j]);
       word[it] = w;
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
@@ -266,16 +293,16 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_
                             uint32_t j_bits,
                             const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
-                            xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
-                            uint64_t* total, cudaStream_t s) {
+                            int metric, xtn_triple* out, int64_t cap, uint64_t* status,
+                            uint32_t* err, uint64_t* total, cudaStream_t s) {
   if (n <= 0) return;
   const size_t st = verify_status_bytes(n);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
   cudaMemsetAsync(status, 0, st, s);
   prof_begin(s, "k_unique_finalize", (double)n * 8.0);
   k_unique_finalize<<<std::min<uint32_t>(div_up_u32(n, VER_TILE), 152 * 8), VER_THREADS, 0, s>>>(
-      pairs, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, out, cap, status, ctr, err,
-      total);
+      pairs, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, metric, out, cap, status,
+      ctr, err, total);
   prof_end(s);
 }
 

@@ -117,20 +117,21 @@ void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        cudaStream_t s);
 
 // k_verify.cu --------------------------------------------------------------
+// metric: 0 = Levenshtein, 1 = Hamming (pairs of equal length only).
 size_t verify_status_bytes(int64_t n);
 void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* n_dev,
                               uint32_t j_bits,
                               const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                               const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
-                              const uint32_t* seq_rep, int self_mode, int d, uint64_t* surv,
-                              uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist, int hist_hi,
-                              int sms, uint32_t* err, cudaStream_t s);
+                              const uint32_t* seq_rep, int self_mode, int d, int metric,
+                              uint64_t* surv, uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist,
+                              int hist_hi, int sms, uint32_t* err, cudaStream_t s);
 void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_dev,
                             uint32_t j_bits,
                             const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
-                            xtn_triple* out, int64_t cap, uint64_t* status, uint32_t* err,
-                            uint64_t* total, cudaStream_t s);
+                            int metric, xtn_triple* out, int64_t cap, uint64_t* status,
+                            uint32_t* err, uint64_t* total, cudaStream_t s);
 void launch_tcrdist_filter(const xtn_triple* in, int64_t n, const Key128* keys,
                            const uint8_t* lens, int64_t n_seq, int max_score, xtn_triple* out,
                            uint64_t* status, uint32_t* err, uint64_t* total, cudaStream_t s);

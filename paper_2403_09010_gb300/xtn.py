@@ -70,8 +70,13 @@ def _call_with_rows(fn, cap, like, where):
     return out[: n_out.value]
 
 
-def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None):
-    """All pairs (i < j) within Levenshtein distance d; see xtn_search_self."""
+def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None,
+                metric: str = "levenshtein"):
+    """All pairs (i < j) within distance d; see xtn_search_self.  metric
+    "hamming" calls xtn_search_self_hamming (equal lengths, substitutions)."""
+    if metric not in ("levenshtein", "hamming"):
+        raise ValueError(f"unknown metric {metric!r}")
+    entry = "xtn_search_self_hamming" if metric == "hamming" else "xtn_search_self"
     n = _n_items(offsets)
     sp, sk, _ = _ptr(seqs, np.uint8)
     op, ok, _ = _ptr(offsets, np.int64)
@@ -82,9 +87,9 @@ def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None)
         cap = 4 * n + 4096
 
     def fn(optr, c, nref):
-        return native.lib().xtn_search_self(sp, op, n, int(d), rp, n_rep, optr, c, nref, stream)
+        return getattr(native.lib(), entry)(sp, op, n, int(d), rp, n_rep, optr, c, nref, stream)
 
-    return _call_with_rows(fn, cap, seqs, "xtn_search_self")
+    return _call_with_rows(fn, cap, seqs, entry)
 
 
 class Index:

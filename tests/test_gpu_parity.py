@@ -354,6 +354,49 @@ def test_plan_capacity_is_reported(xtn):
     assert np.array_equal(_rows(big.result(like=ds)), want)
 
 
+# --------------------------------------------------------------- Hamming ---
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_hamming_matches_oracle(xtn, d):
+    seqs, off = gen.workload(gen.SELF_1M, 20_000 if d < 3 else 3_000)
+    want = oracle.symdel_self(seqs, off, d, "hamming")
+    assert np.array_equal(_rows(xtn.search_self(seqs, off, d, metric="hamming")), want)
+    # two letters: many equal-length near-copies and repeated residues
+    strs = _rand_strings(np.random.default_rng(60 + d), 400, "AC", 0, 9)
+    s2, o2 = gen.from_strings(strs)
+    assert np.array_equal(_rows(xtn.search_self(s2, o2, d, metric="hamming")),
+                          oracle.bruteforce_self(s2, o2, d, "hamming"))
+
+
+def test_hamming_batched_matches_oracle(xtn):
+    seqs, off, rep = gen.batched(n_rep=8, seed=21, size_min=100, size_max=3000)
+    want = oracle.symdel_batched(seqs, off, rep, 2, "hamming")
+    got = _rows(xtn.search_self(seqs, off, 2, rep_offsets=rep, metric="hamming"))
+    rep_of = np.searchsorted(rep, got[:, 0], side="right") - 1
+    local = np.stack([rep_of, got[:, 0] - rep[rep_of], got[:, 1] - rep[rep_of], got[:, 2]], 1)
+    assert np.array_equal(local.astype(np.uint32), want)
+
+
+def test_hamming_pairs_are_levenshtein_pairs_1m(xtn):
+    # at full size: every Hamming pair is a Levenshtein pair of the same d
+    # with no larger distance, and has equal lengths
+    seqs, off = gen.workload(gen.SELF_1M)
+    ds, do = _dev(seqs, off)
+    ham = _rows(xtn.search_self(ds, do, 2, metric="hamming"))
+    lev = _rows(xtn.search_self(ds, do, 2))
+    assert 0 < ham.shape[0] <= lev.shape[0]
+    key = lambda r: r[:, 0].astype(np.uint64) << np.uint64(32) | r[:, 1].astype(np.uint64)
+    pos = np.searchsorted(key(lev), key(ham))
+    assert np.all(pos < lev.shape[0]) and np.array_equal(key(lev)[pos], key(ham))
+    assert np.all(lev[pos, 2] <= ham[:, 2])
+    lens = np.diff(off)
+    assert np.array_equal(lens[ham[:, 0]], lens[ham[:, 1]])
+    # a sample of rows against the plain definition
+    strs = gen.to_strings(seqs, off)
+    rng = np.random.default_rng(5)
+    for r in ham[rng.choice(ham.shape[0], 200, replace=False)]:
+        assert oracle.hamming(strs[r[0]], strs[r[1]]) == r[2]
+
+
 # ----------------------------------------------------------------- query ---
 @pytest.mark.parametrize("d", [1, 2])
 def test_query_matches_oracle(xtn, d):
