@@ -323,6 +323,20 @@ def run_tcrdist(reps: int = 10):
             "kept_pairs": int(kept.shape[0]), "search_ms": search_ms, "filter_ms": filter_ms}
 
 
+def run_hamming(reps: int = 10):
+    """The Hamming variant (same candidates, Hamming filter) of the 1M d<=2
+    self-search: time per search and pairs, next to the Levenshtein search."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    seqs, off = gen.workload(WORKLOAD)
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    cur = torch.cuda.current_stream()
+    ham = xtn.search_self(ds, do, 2, metric="hamming")
+    ms = _events_ms(lambda: xtn.search_self(ds, do, 2, metric="hamming"), reps, cur)
+    return {"workload": "selfsearch_n1e6_d2_hamming", "hamming_pairs": int(ham.shape[0]),
+            "search_ms": ms, "pairs_per_s": ham.shape[0] / (ms / 1e3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,7 +345,7 @@ def main():
     ap.add_argument("--impl", default="xtn", choices=["xtn", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched / served / TCRdist side measurements")
+                    help="skip the batched / served / TCRdist / Hamming side measurements")
     ap.add_argument("--n", type=int, default=None,
                     help="use only the first n sequences (small cases for profiling)")
     args = ap.parse_args()
@@ -464,6 +478,7 @@ def main():
         line["batched"] = run_batched()
         line["served"] = run_served()
         line["tcrdist"] = run_tcrdist()
+        line["hamming"] = run_hamming()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
