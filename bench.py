@@ -323,6 +323,51 @@ def run_tcrdist(reps: int = 10):
             "kept_pairs": int(kept.shape[0]), "search_ms": search_ms, "filter_ms": filter_ms}
 
 
+def run_retention(n_sub: int = 5000, thresholds=(12, 18, 24, 30, 36)):
+    """TCRdist retention of the SymDel prefilter (the paper's TCRdist figure,
+    panel B) on the first n_sub sequences: of the pairs within each TCRdist
+    threshold (every pair filtered by the library's TCRdist kernel), the
+    share that SymDel(d) + filter keeps, for d = 2 and 3; and the time of the
+    exhaustive filter against SymDel(d) + filter (panel A)."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    seqs, off = gen.workload(gen.TCRDIST_1M, n_sub)
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    cur = torch.cuda.current_stream()
+    ii, jj = np.triu_indices(n_sub, 1)
+    every = torch.from_numpy(np.stack([ii, jj, np.zeros_like(ii)], 1).astype(np.int32)).cuda()
+    lev = {d: xtn.search_self(ds, do, d) for d in (2, 3)}
+    curve = []
+    for t in thresholds:
+        exh = int(xtn.tcrdist_filter(ds, do, every, t).shape[0])
+        row = {"tcrdist_max": t, "exhaustive_pairs": exh}
+        for d in (2, 3):
+            kept = int(xtn.tcrdist_filter(ds, do, lev[d], t).shape[0])
+            row[f"kept_d{d}"] = kept
+            row[f"retention_d{d}"] = kept / exh if exh else None
+        curve.append(row)
+    t = 24
+    exh_ms = _events_ms(lambda: xtn.tcrdist_filter(ds, do, every, t), 5, cur)
+    sym_ms = {f"symdel_d{d}_plus_filter_ms": _events_ms(
+        lambda d=d: xtn.tcrdist_filter(ds, do, xtn.search_self(ds, do, d), t), 5, cur)
+        for d in (2, 3)}
+    return {"workload": f"tcrdist_retention_n{n_sub}", "all_pairs": int(ii.size),
+            "curve": curve, "exhaustive_filter_ms": exh_ms, **sym_ms}
+
+
+def run_d3(reps: int = 3):
+    """The 1M search at d <= 3 (about 560 deletion subsets per sequence)."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    seqs, off = gen.workload(WORKLOAD)
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    cur = torch.cuda.current_stream()
+    rows = xtn.search_self(ds, do, 3)
+    ms = _events_ms(lambda: xtn.search_self(ds, do, 3), reps, cur)
+    return {"workload": "selfsearch_n1e6_d3", "verified_pairs": int(rows.shape[0]),
+            "search_ms": ms, "pairs_per_s": rows.shape[0] / (ms / 1e3)}
+
+
 def run_hamming(reps: int = 10):
     """The Hamming variant (same candidates, Hamming filter) of the 1M d<=2
     self-search: time per search and pairs, next to the Levenshtein search."""
@@ -479,6 +524,8 @@ def main():
         line["served"] = run_served()
         line["tcrdist"] = run_tcrdist()
         line["hamming"] = run_hamming()
+        line["tcrdist_retention"] = run_retention()
+        line["d3"] = run_d3()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

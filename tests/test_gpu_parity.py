@@ -435,6 +435,25 @@ def test_tcrdist_filter_matches_oracle(xtn):
     assert np.array_equal(got, allp[:, :3])
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_tcrdist_thresholds_and_exhaustive_rows(xtn, d):
+    # the retention experiment: SymDel(d) rows filtered at several TCRdist
+    # thresholds equal the all-pairs scorer restricted to Lev <= d; filtering
+    # every pair gives the exhaustive TCRdist neighbours
+    seqs, off = gen.workload(gen.TCRDIST_1M, 2000)
+    lev = _rows(xtn.search_self(seqs, off, d))
+    n = off.size - 1
+    ii, jj = np.triu_indices(n, 1)
+    every = np.stack([ii, jj, np.zeros_like(ii)], 1).astype(np.uint32)
+    for t in (12, 24, 36):
+        got = _rows(xtn.tcrdist_filter(seqs, off, lev, t))
+        want = oracle.tcrdist_allpairs(seqs, off, d, t)
+        assert np.array_equal(got, want[:, :3]), (d, t)
+        exh = _rows(xtn.tcrdist_filter(seqs, off, every, t))
+        want_exh = oracle.tcrdist_allpairs(seqs, off, 25, t)
+        assert np.array_equal(exh[:, :2], want_exh[:, :2]), (d, t)
+
+
 def test_tcrdist_every_residue_pair(xtn):
     # one pair per ordered residue pair (a, b) at the same position: covers
     # every BLOSUM62 entry the score uses.
