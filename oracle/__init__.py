@@ -10,6 +10,7 @@ ctypes. Every function returns numpy arrays of uint32 rows:
 
 * ``symdel_self``      (i, j, dist), i < j          -- Appendix, SymDel steps 0-4
 * ``symdel_batched``   (rep, i, j, dist)            -- the same per repertoire
+* ``symdel_cross``     (i, j, dist)                 -- pairs between repertoires
 * ``symdel_query``     (q, r, dist)                 -- steps 1-2 on the reference,
                                                        step 3 with the queries
 * ``bruteforce_self`` / ``bruteforce_query``        -- exhaustive search (pin)
@@ -62,6 +63,8 @@ def _load():
     lib.xo_bruteforce_self_metric.restype = _P
     lib.xo_symdel_batched.argtypes = [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
     lib.xo_symdel_batched.restype = _P
+    lib.xo_symdel_cross.argtypes = [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
+    lib.xo_symdel_cross.restype = _P
     lib.xo_hamming.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     lib.xo_hamming.restype = ctypes.c_int
     for name in ("xo_symdel_query", "xo_bruteforce_query"):
@@ -129,6 +132,14 @@ def symdel_batched(seqs, offsets, rep_offsets, d: int, metric: str = "levenshtei
     r = np.ascontiguousarray(rep_offsets, dtype=np.int64)
     return _take(_load().xo_symdel_batched(_ptr(s), _ptr(o), _ptr(r), r.size - 1, d,
                                            _METRICS[metric]))
+
+
+def symdel_cross(seqs, offsets, rep_offsets, d: int, metric: str = "levenshtein") -> np.ndarray:
+    """Pairs (i, j, dist) whose sequences lie in different repertoires."""
+    s, o = _prep(seqs, offsets)
+    r = np.ascontiguousarray(rep_offsets, dtype=np.int64)
+    return _take(_load().xo_symdel_cross(_ptr(s), _ptr(o), _ptr(r), r.size - 1, d,
+                                         _METRICS[metric]))
 
 
 def symdel_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int) -> np.ndarray:

@@ -268,6 +268,23 @@ void* xo_symdel_batched(const uint8_t* seqs, const int64_t* off, const int64_t* 
   return pack(all, 4);
 }
 
+// Pairs between repertoires (the repertoire-overlap workload of the CompAIRR
+// comparison): the SymDel self-search of the whole concatenation, keeping the
+// pairs whose two sequences lie in different repertoires.  Rows (i, j, dist)
+// with global indices, sorted.  metric: 0 = Levenshtein, 1 = Hamming.
+void* xo_symdel_cross(const uint8_t* seqs, const int64_t* off, const int64_t* rep_off,
+                      int64_t n_rep, int d, int metric) {
+  const int64_t n = rep_off[n_rep];
+  auto rows = symdel_self_range(seqs, off, 0, n, d, metric);
+  std::vector<std::vector<uint32_t>> keep;
+  auto rep_of = [&](uint32_t i) {
+    return std::upper_bound(rep_off, rep_off + n_rep + 1, (int64_t)i) - rep_off - 1;
+  };
+  for (auto& row : rows)
+    if (rep_of(row[0]) != rep_of(row[1])) keep.push_back(row);
+  return pack(keep, 3);
+}
+
 // SymDel query-vs-reference: rows (q, r, dist) with Lev <= d, sorted by (q, r).
 // Steps 1-2 on the reference, step 3 with the queries' own variants.
 void* xo_symdel_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,

@@ -355,3 +355,20 @@ def test_hamming_batched_is_per_repertoire():
         rows = oracle.bruteforce_self(s, o, 2, "hamming")
         parts.append(np.column_stack([np.full(rows.shape[0], r, np.uint32), rows]))
     assert np.array_equal(got, np.concatenate(parts))
+
+
+# ---------------------------------------------------- between repertoires ---
+@pytest.mark.parametrize("metric", ["levenshtein", "hamming"])
+def test_cross_and_within_partition_the_whole_search(metric):
+    # every pair of the concatenation lies within one repertoire or between two
+    seqs, off, rep = gen.batched(n_rep=6, seed=14, size_min=50, size_max=300)
+    whole = oracle.bruteforce_self(seqs, off, 2, metric)
+    cross = oracle.symdel_cross(seqs, off, rep, 2, metric)
+    within = oracle.symdel_batched(seqs, off, rep, 2, metric)
+    glob = np.stack([within[:, 1] + rep[within[:, 0]], within[:, 2] + rep[within[:, 0]],
+                     within[:, 3]], 1).astype(np.uint32)
+    both = np.concatenate([cross, glob])
+    both = both[np.lexsort((both[:, 1], both[:, 0]))]
+    assert np.array_equal(both, whole)
+    r_of = lambda i: np.searchsorted(rep, i, side="right") - 1
+    assert np.all(r_of(cross[:, 0]) != r_of(cross[:, 1]))
