@@ -227,7 +227,7 @@ def run_batched(reps: int = 5):
     ds = torch.from_numpy(seqs).cuda()
     do = torch.from_numpy(off).cuda()
     tuned = autotune.tune(ds, off, gen.BATCH_D, rep_offsets=rep, use_cache=False)
-    plan = xtn.Plan(off, gen.BATCH_D, rep_offsets=rep, pair_capacity=tuned["pair_capacity"])
+    plan = xtn.Plan(off, gen.BATCH_D, rep_offsets=rep, tuning=tuned)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
@@ -382,6 +382,24 @@ def run_hamming(reps: int = 10):
             "search_ms": ms, "pairs_per_s": ham.shape[0] / (ms / 1e3)}
 
 
+def run_between(reps: int = 10, n_rep: int = 8):
+    """Repertoire overlap: the 1M set as eight repertoires of equal size, the
+    pairs between different repertoires at d<=2 (Levenshtein and Hamming)."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    seqs, off = gen.workload(WORKLOAD)
+    n = off.size - 1
+    rep = (np.arange(n_rep + 1, dtype=np.int64) * n) // n_rep
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    cur = torch.cuda.current_stream()
+    out = {"workload": f"between_n1e6_{n_rep}reps_d2"}
+    for metric in ("levenshtein", "hamming"):
+        rows = xtn.search_between(ds, do, 2, rep, metric=metric)
+        ms = _events_ms(lambda: xtn.search_between(ds, do, 2, rep, metric=metric), reps, cur)
+        out[metric] = {"pairs": int(rows.shape[0]), "search_ms": ms}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,7 +408,8 @@ def main():
     ap.add_argument("--impl", default="xtn", choices=["xtn", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched / served / TCRdist / Hamming side measurements")
+                    help="skip the batched / served / TCRdist / Hamming / overlap side "
+                         "measurements")
     ap.add_argument("--n", type=int, default=None,
                     help="use only the first n sequences (small cases for profiling)")
     args = ap.parse_args()
@@ -526,6 +545,7 @@ def main():
         line["hamming"] = run_hamming()
         line["tcrdist_retention"] = run_retention()
         line["d3"] = run_d3()
+        line["between"] = run_between()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

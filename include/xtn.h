@@ -134,6 +134,25 @@ XTN_API int xtn_search_self_hamming(const uint8_t* seqs, const int64_t* offsets,
                                     int64_t cap, int64_t* n_out, xtn_stream_t stream);
 
 /*
+ * Pairs between repertoires (Results, comparison with CompAIRR: the
+ * repertoire-overlap workload).  Rows are {i, j, dist} with i < j global
+ * indices, i and j in different repertoires, dist = Levenshtein distance
+ * (metric XTN_METRIC_LEVENSHTEIN) or Hamming distance (XTN_METRIC_HAMMING,
+ * equal lengths only) <= d, sorted by (i, j).  The search is the self-search
+ * of the concatenated repertoires (Appendix A, XTNeighbor steps 0-7) whose
+ * last step keeps a pair only when its repertoires differ: together with the
+ * rows of xtn_search_self's batched mode these are exactly the rows of one
+ * self-search over all sequences.  rep_offsets (required, n_rep >= 1) as in
+ * xtn_search_self; other arguments and errors as xtn_search_self, plus
+ * INVALID_ARG for a NULL rep_offsets or an unknown metric.
+ */
+#define XTN_METRIC_LEVENSHTEIN 0
+#define XTN_METRIC_HAMMING 1
+XTN_API int xtn_search_between(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                               const int64_t* rep_offsets, int64_t n_rep, int metric,
+                               xtn_triple* out, int64_t cap, int64_t* n_out, xtn_stream_t stream);
+
+/*
  * Build a device-resident index of a reference set: its encoded sequences
  * and its deletion variants, grouped by sorting (Appendix A, XTNeighbor steps
  * 1-4; the paper's multi-value hash map of the SymDel step list, realised as a

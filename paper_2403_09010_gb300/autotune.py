@@ -10,7 +10,9 @@ candidate-pair capacity for the plan (measured candidates x 1.25, so a plan
 holds no more pair memory than it needs).  The pipeline splits large buckets
 of shared variants at the granularity of its emit tiles whatever their size,
 so there is no bucket-split threshold to tune.  Results are cached as JSON,
-keyed by GPU name, workload size and d.
+keyed by GPU name, workload size and d.  The process-wide knobs are put
+back as they were when tuning ends: pass the result to ``xtn.Plan(...,
+tuning=r)`` to build a plan with it.
 """
 from __future__ import annotations
 
@@ -36,9 +38,9 @@ def _key(n, n_rep, d):
 
 def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int = 2,
          use_cache: bool = True) -> dict:
-    """Time every sort configuration on this workload and apply the fastest.
-    Returns {"grouping", "record_hist", "records_cfg", "pairs_cfg",
-    "pair_capacity", "sort_ms": {...}}."""
+    """Time every sort configuration on this workload and return the fastest:
+    {"grouping", "record_hist", "records_cfg", "pairs_cfg", "pair_capacity",
+    "sort_ms": {...}}.  The knobs hold their previous values afterwards."""
     n = int(offsets.shape[0]) - 1
     n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
     key = _key(n, n_rep, d)
@@ -50,12 +52,21 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
         except (OSError, ValueError):
             cache = {}
     if use_cache and key in cache:
-        r = cache[key]
-        xtn.tune_set(native.XTN_TUNE_GROUPING, r.get("grouping", 0))
-        xtn.tune_set(native.XTN_TUNE_RECORD_HISTOGRAM, r.get("record_hist", 0))
-        xtn.tune_set(native.XTN_TUNE_SORT_RECORDS, r["records_cfg"])
-        xtn.tune_set(native.XTN_TUNE_SORT_PAIRS, r["pairs_cfg"])
-        return r
+        return cache[key]
+    current = {name: xtn.tune_get(knob) for name, knob in xtn._TUNING_KNOBS}
+    with xtn.tuning_applied(current):  # puts them back when tuning ends
+        r = _tune(seqs_dev, offsets, d, rep_offsets, configs, repeats)
+    if use_cache:
+        cache[key] = r
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            json.dump(cache, open(path, "w"), indent=1)
+        except OSError:
+            pass
+    return r
+
+
+def _tune(seqs_dev, offsets, d, rep_offsets, configs, repeats):
     import torch
     R, P, H, GR = (native.XTN_TUNE_SORT_RECORDS, native.XTN_TUNE_SORT_PAIRS,
                    native.XTN_TUNE_RECORD_HISTOGRAM, native.XTN_TUNE_GROUPING)
@@ -107,14 +118,6 @@ def tune(seqs_dev, offsets, d: int, rep_offsets=None, configs=None, repeats: int
         pair_ms[c], _ = measure("k_onesweep_pairs")
     best_p = min(pair_ms, key=pair_ms.get)
     xtn.tune_set(P, best_p)
-    r = {"grouping": best_g, "record_hist": best_h, "records_cfg": best_r, "pairs_cfg": best_p,
-         "pair_capacity": max(65536, int(cands * 1.25)),
-         "sort_ms": {"records": rec_ms[best_r], "pairs": pair_ms[best_p]}}
-    if use_cache:
-        cache[key] = r
-        try:
-            os.makedirs(os.path.dirname(path), exist_ok=True)
-            json.dump(cache, open(path, "w"), indent=1)
-        except OSError:
-            pass
-    return r
+    return {"grouping": best_g, "record_hist": best_h, "records_cfg": best_r,
+            "pairs_cfg": best_p, "pair_capacity": max(65536, int(cands * 1.25)),
+            "sort_ms": {"records": rec_ms[best_r], "pairs": pair_ms[best_p]}}

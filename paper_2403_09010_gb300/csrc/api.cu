@@ -517,15 +517,19 @@ __global__ void k_pair_total(const uint64_t* __restrict__ pair_off,
 
 // mode: grouping mode (see g_grouping), -1 = the tuned one.  metric: 0 =
 // Levenshtein, 1 = Hamming (the Hamming variant: the same candidates, the
-// last step filters by Hamming distance).
+// last step filters by Hamming distance).  between: report the pairs between
+// different repertoires instead of those within one; the variants then carry
+// no repertoire salt, so that equal variants of different repertoires meet.
 int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                      const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
-                     int64_t* n_out, cudaStream_t s, int mode = -1, int metric = 0) {
+                     int64_t* n_out, cudaStream_t s, int mode = -1, int metric = 0,
+                     bool between = false) {
   if (!n_out) return XTN_ERR_INVALID_ARG;
   *n_out = 0;
   if (n < 0 || d < 0 || d > XTN_MAX_D || cap < 0 || !offsets) return XTN_ERR_INVALID_ARG;
   if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
   if (rep_offsets && n_rep < 1) return XTN_ERR_INVALID_ARG;
+  if (between && !rep_offsets) return XTN_ERR_INVALID_ARG;
   if (n == 0) return XTN_OK;
   int sms = 0;
   int rc = current_device_info(&sms);
@@ -564,8 +568,8 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     direct.cand_count = counters + 2;
     XTN_ALLOC_OK(ar);
   }
-  rc = expand_and_sort(e, n, d, seq_rep, sms, ar, err, s, &so, true, g_cap, mode,
-                       mode != 1 ? &direct : nullptr);
+  rc = expand_and_sort(e, n, d, between ? nullptr : seq_rep, sms, ar, err, s, &so, true, g_cap,
+                       mode, mode != 1 ? &direct : nullptr);
   if (rc) return rc;
   uint32_t* S = reinterpret_cast<uint32_t*>(so.spare);  // groups live in the spare buffer
   uint32_t* E = S + g_cap;
@@ -582,7 +586,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     if (h.err & DERR_CAPACITY) {
       ar.release();
       return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
-                              metric);
+                              metric, between);
     }
     if (h.err) return map_device_err(h.err);
     flagged = h.large > 0;
@@ -604,7 +608,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (mode != 1 && n_pairs > direct.cand_cap) {
     ar.release();
     return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
-                            metric);
+                            metric, between);
   }
 
   // back: the remaining candidates, verify, sort survivors, dedup
@@ -626,7 +630,8 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   rc = prepare_out(out, cap, n_pairs, ar, &o);
   if (rc) return rc;
   rc = launch_back(b, n_pairs, nullptr, 2 * so.id_bits, so.id_bits, peq, e.lens, n, e.keys, e.lens,
-                   n, seq_rep, 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs, metric);
+                   n, seq_rep, between ? 2 : 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs,
+                   metric);
   if (rc) return rc;
   XTN_CK(cudaMemcpyAsync(&h.pairs, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
@@ -1102,6 +1107,16 @@ int xtn_search_self_hamming(const uint8_t* seqs, const int64_t* offsets, int64_t
                             int64_t cap, int64_t* n_out, xtn_stream_t stream) {
   return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
                                reinterpret_cast<cudaStream_t>(stream), -1, 1);
+}
+
+int xtn_search_between(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                       const int64_t* rep_offsets, int64_t n_rep, int metric, xtn_triple* out,
+                       int64_t cap, int64_t* n_out, xtn_stream_t stream) {
+  if (n_out) *n_out = 0;
+  if (metric != XTN_METRIC_LEVENSHTEIN && metric != XTN_METRIC_HAMMING)
+    return XTN_ERR_INVALID_ARG;
+  return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
+                               reinterpret_cast<cudaStream_t>(stream), -1, metric, true);
 }
 
 int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,

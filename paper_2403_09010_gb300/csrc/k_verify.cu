@@ -10,7 +10,8 @@
 //
 //   k_verify_candidates : per candidate (i, j): drop i == j (one sequence
 //                         sharing a variant with itself through repeated
-//                         residues) and pairs from different repertoires,
+//                         residues) and pairs from different repertoires
+//                         (from the same one when searching between them),
 //                         reject |len_i - len_j| > d, compute the edit
 //                         distance bit-parallel, keep it if <= d.  Survivors
 //                         are appended with one atomic per warp; their radix
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256)
       ok = i < n_i && j < n_j;
       if (!ok) atomicOr(err, DERR_RANGE);
       if (self_mode) ok = ok && i != j;
-      if (ok && seq_rep) ok = seq_rep[i] == seq_rep[j];
+      if (ok && seq_rep) ok = (seq_rep[i] == seq_rep[j]) == (self_mode != 2);
       if (ok)
         ok = pair_distance(metric, d, peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]) <=
              (uint32_t)d;

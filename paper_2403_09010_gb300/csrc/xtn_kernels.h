@@ -118,6 +118,9 @@ void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
 
 // k_verify.cu --------------------------------------------------------------
 // metric: 0 = Levenshtein, 1 = Hamming (pairs of equal length only).
+// self_mode: 0 = query vs reference, 1 = self-search (pairs within a
+// repertoire when seq_rep is given), 2 = self-search keeping only pairs
+// between different repertoires.
 size_t verify_status_bytes(int64_t n);
 void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* n_dev,
                               uint32_t j_bits,

@@ -41,6 +41,7 @@ SIGNATURES = {
     "xtn_version": (_I, []),
     "xtn_search_self": (_I, [_P, _P, _I64, _I, _P, _I64, _P, _I64, _P, _P]),
     "xtn_search_self_hamming": (_I, [_P, _P, _I64, _I, _P, _I64, _P, _I64, _P, _P]),
+    "xtn_search_between": (_I, [_P, _P, _I64, _I, _P, _I64, _I, _P, _I64, _P, _P]),
     "xtn_index_build": (_I, [_P, _P, _I64, _I, _P, _P]),
     "xtn_index_free": (_I, [_P]),
     "xtn_index_info": (_I, [_P, _P, _P, _P, _P]),

@@ -70,6 +70,9 @@ def _call_with_rows(fn, cap, like, where):
     return out[: n_out.value]
 
 
+_METRICS = {"levenshtein": 0, "hamming": 1}
+
+
 def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None,
                 metric: str = "levenshtein"):
     """All pairs (i < j) within distance d; see xtn_search_self.  metric
@@ -90,6 +93,30 @@ def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None,
         return getattr(native.lib(), entry)(sp, op, n, int(d), rp, n_rep, optr, c, nref, stream)
 
     return _call_with_rows(fn, cap, seqs, entry)
+
+
+def search_between(seqs, offsets, d: int, rep_offsets, cap: int | None = None,
+                   metric: str = "levenshtein"):
+    """All pairs (i < j) within distance d whose sequences lie in different
+    repertoires; see xtn_search_between."""
+    if metric not in _METRICS:
+        raise ValueError(f"unknown metric {metric!r}")
+    if rep_offsets is None:
+        raise ValueError("search_between needs rep_offsets")
+    n = _n_items(offsets)
+    sp, sk, _ = _ptr(seqs, np.uint8)
+    op, ok, _ = _ptr(offsets, np.int64)
+    rp, rk, _ = _ptr(rep_offsets, np.int64)
+    n_rep = int(rep_offsets.shape[0]) - 1
+    stream = _stream(seqs)
+    if cap is None:
+        cap = 4 * n + 4096
+
+    def fn(optr, c, nref):
+        return native.lib().xtn_search_between(sp, op, n, int(d), rp, n_rep, _METRICS[metric],
+                                               optr, c, nref, stream)
+
+    return _call_with_rows(fn, cap, seqs, "xtn_search_between")
 
 
 class Index:
@@ -121,19 +148,54 @@ class Index:
             pass
 
 
+_TUNING_KNOBS = (("grouping", native.XTN_TUNE_GROUPING),
+                 ("record_hist", native.XTN_TUNE_RECORD_HISTOGRAM),
+                 ("records_cfg", native.XTN_TUNE_SORT_RECORDS),
+                 ("pairs_cfg", native.XTN_TUNE_SORT_PAIRS))
+
+
+class tuning_applied:
+    """Context manager: set the knobs named in a tuning dict (keys grouping,
+    record_hist, records_cfg, pairs_cfg; missing keys are left alone) and put
+    the previous values back on exit."""
+
+    def __init__(self, tuning: dict | None):
+        self.tuning = tuning or {}
+
+    def __enter__(self):
+        self.saved = [(knob, tune_get(knob)) for name, knob in _TUNING_KNOBS
+                      if name in self.tuning]
+        for name, knob in _TUNING_KNOBS:
+            if name in self.tuning:
+                tune_set(knob, int(self.tuning[name]))
+        return self
+
+    def __exit__(self, *exc):
+        for knob, value in self.saved:
+            tune_set(knob, value)
+        return False
+
+
 class Plan:
     """Planned self-search (see xtn_plan_create): device memory allocated once,
     `run` only queues kernels on the current stream (CUDA-graph capturable),
-    `result` waits and returns the rows of the last run."""
+    `result` waits and returns the rows of the last run.  The tuning knobs are
+    read when the plan is created; `tuning` (a dict as returned by
+    autotune.tune) applies to this plan only, and its pair_capacity is used
+    when `pair_capacity` is 0."""
 
-    def __init__(self, offsets, d: int, rep_offsets=None, pair_capacity: int = 0):
+    def __init__(self, offsets, d: int, rep_offsets=None, pair_capacity: int = 0,
+                 tuning: dict | None = None):
         n = _n_items(offsets)
         op, ok, _ = _ptr(offsets, np.int64)
         rp, rk, _ = _ptr(rep_offsets, np.int64)
         n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
+        if not pair_capacity and tuning:
+            pair_capacity = int(tuning.get("pair_capacity", 0))
         h = ctypes.c_void_p(0)
-        check(native.lib().xtn_plan_create(op, n, int(d), rp, n_rep, int(pair_capacity),
-                                           ctypes.byref(h)), "xtn_plan_create")
+        with tuning_applied(tuning):
+            check(native.lib().xtn_plan_create(op, n, int(d), rp, n_rep, int(pair_capacity),
+                                               ctypes.byref(h)), "xtn_plan_create")
         self._h = h
         self.n = n
         self.d = int(d)

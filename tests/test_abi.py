@@ -72,6 +72,11 @@ def test_argument_checks_before_device_work(lib):
     assert lib.xtn_index_free(None) == native.XTN_OK
     assert lib.xtn_index_info(None, None, None, None, None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_tcrdist_filter(seq, off, 1, None, 0, 24, None, ctypes.byref(n_out), None) == native.XTN_OK
+    # pairs between repertoires: repertoires required, metric 0 or 1
+    rep = (ctypes.c_int64 * 2)(0, 1)
+    assert lib.xtn_search_between(seq, off, 1, 1, None, 0, 0, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_between(seq, off, 1, 1, rep, 1, 2, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_between(seq, off, 0, 1, rep, 1, 1, None, 0, ctypes.byref(n_out), None) == native.XTN_OK
 
 
 def test_tuning_knobs(lib):
@@ -89,3 +94,16 @@ def test_tuning_knobs(lib):
         assert lib.xtn_tune_set(knob, last) == native.XTN_OK and lib.xtn_tune_get(knob) == last
         assert lib.xtn_tune_set(knob, old) == native.XTN_OK
     assert lib.xtn_tune_set(99, 0) == native.XTN_ERR_INVALID_ARG
+
+
+def test_tuning_applied_restores_knobs(lib):
+    from paper_2403_09010_gb300 import xtn
+    knobs = [k for _, k in xtn._TUNING_KNOBS]
+    before = [lib.xtn_tune_get(k) for k in knobs]
+    want = {"grouping": 1, "record_hist": 1, "records_cfg": 0, "pairs_cfg": 1}
+    with xtn.tuning_applied(want):
+        assert [lib.xtn_tune_get(k) for k in knobs] == [1, 1, 0, 1]
+    assert [lib.xtn_tune_get(k) for k in knobs] == before
+    with xtn.tuning_applied({"pairs_cfg": 2}):   # keys left out stay as they are
+        assert [lib.xtn_tune_get(k) for k in knobs] == before[:3] + [2]
+    assert [lib.xtn_tune_get(k) for k in knobs] == before

@@ -397,6 +397,79 @@ def test_hamming_pairs_are_levenshtein_pairs_1m(xtn):
         assert oracle.hamming(strs[r[0]], strs[r[1]]) == r[2]
 
 
+def test_autotuned_plan_matches_oracle_and_leaves_knobs(xtn):
+    from paper_2403_09010_gb300 import autotune
+    seqs, off, rep = gen.batched(n_rep=8, seed=22, size_min=100, size_max=3000)
+    knobs = [k for _, k in xtn.xtn._TUNING_KNOBS]
+    before = [xtn.tune_get(k) for k in knobs]
+    ds = torch.from_numpy(seqs).cuda()
+    r = autotune.tune(ds, off, 2, rep_offsets=rep, configs=[0, 9], repeats=1, use_cache=False)
+    assert [xtn.tune_get(k) for k in knobs] == before
+    plan = xtn.Plan(off, 2, rep_offsets=rep, tuning=r)
+    assert plan.info()["pair_capacity"] >= r["pair_capacity"]
+    plan.run(ds)
+    got = _rows(plan.result(like=ds))
+    want = oracle.symdel_batched(seqs, off, rep, 2)
+    rep_of = np.searchsorted(rep, got[:, 0], side="right") - 1
+    local = np.stack([rep_of, got[:, 0] - rep[rep_of], got[:, 1] - rep[rep_of], got[:, 2]], 1)
+    assert np.array_equal(local.astype(np.uint32), want)
+    plan.free()
+
+
+# ---------------------------------------------------- between repertoires ---
+@pytest.mark.parametrize("d,metric", [(1, "levenshtein"), (2, "levenshtein"),
+                                      (3, "levenshtein"), (2, "hamming")])
+def test_between_matches_oracle(xtn, d, metric):
+    # one generated set cut into eight repertoires at random points: its
+    # near-copies land in other repertoires, so there are pairs between them
+    n = 20_000 if d < 3 else 3_000
+    seqs, off = gen.workload(gen.SELF_1M, n)
+    cuts = np.sort(np.random.default_rng(40 + d).choice(np.arange(1, n), 7, replace=False))
+    rep = np.concatenate([[0], cuts, [n]]).astype(np.int64)
+    want = oracle.symdel_cross(seqs, off, rep, d, metric)
+    got = _rows(xtn.search_between(seqs, off, d, rep, metric=metric))
+    assert want.shape[0] > 0 and np.array_equal(got, want)
+
+
+def test_between_independent_repertoires(xtn):
+    # repertoires drawn independently share few neighbours
+    seqs, off, rep = gen.batched(n_rep=8, seed=33, size_min=100, size_max=3000)
+    want = oracle.symdel_cross(seqs, off, rep, 2)
+    assert np.array_equal(_rows(xtn.search_between(seqs, off, 2, rep)), want)
+
+
+def test_between_small_alphabet_and_empty_repertoires(xtn):
+    # two letters give many shared variants across repertoires; empty
+    # repertoires and a single repertoire are degenerate cases
+    rng = np.random.default_rng(70)
+    strs = _rand_strings(rng, 500, "AC", 0, 8)
+    s2, o2 = gen.from_strings(strs)
+    rep = np.array([0, 0, 120, 120, 121, 380, 500, 500], dtype=np.int64)
+    for d in (0, 1, 2):
+        got = _rows(xtn.search_between(s2, o2, d, rep))
+        assert np.array_equal(got, oracle.symdel_cross(s2, o2, rep, d))
+    one = np.array([0, 500], dtype=np.int64)
+    assert _rows(xtn.search_between(s2, o2, 2, one)).shape[0] == 0
+
+
+def test_within_and_between_partition_the_1m_search(xtn):
+    # at full size: the rows between four repertoires of the 1M set and the
+    # rows within them together are the rows of the whole self-search
+    seqs, off = gen.workload(gen.SELF_1M)
+    n = off.size - 1
+    rep = np.array([0, n // 5, n // 2, n - 1000, n], dtype=np.int64)
+    ds, do = _dev(seqs, off)
+    whole = _rows(xtn.search_self(ds, do, 2))
+    between = _rows(xtn.search_between(ds, do, 2, rep))
+    within = _rows(xtn.search_self(ds, do, 2, rep_offsets=rep))
+    r_of = lambda i: np.searchsorted(rep, i, side="right") - 1
+    assert np.all(r_of(between[:, 0]) != r_of(between[:, 1]))
+    assert np.all(r_of(within[:, 0]) == r_of(within[:, 1]))
+    both = np.concatenate([between, within])
+    both = both[np.lexsort((both[:, 1], both[:, 0]))]
+    assert np.array_equal(both, whole)
+
+
 # ----------------------------------------------------------------- query ---
 @pytest.mark.parametrize("d", [1, 2])
 def test_query_matches_oracle(xtn, d):

@@ -361,7 +361,9 @@ def test_hamming_batched_is_per_repertoire():
 @pytest.mark.parametrize("metric", ["levenshtein", "hamming"])
 def test_cross_and_within_partition_the_whole_search(metric):
     # every pair of the concatenation lies within one repertoire or between two
-    seqs, off, rep = gen.batched(n_rep=6, seed=14, size_min=50, size_max=300)
+    # one generated set cut into repertoires: its near-copies cross the cuts
+    seqs, off = gen.workload(gen.SELF_1M, 1500)
+    rep = np.array([0, 200, 210, 700, 1100, 1500], dtype=np.int64)
     whole = oracle.bruteforce_self(seqs, off, 2, metric)
     cross = oracle.symdel_cross(seqs, off, rep, 2, metric)
     within = oracle.symdel_batched(seqs, off, rep, 2, metric)
@@ -372,3 +374,4 @@ def test_cross_and_within_partition_the_whole_search(metric):
     assert np.array_equal(both, whole)
     r_of = lambda i: np.searchsorted(rep, i, side="right") - 1
     assert np.all(r_of(cross[:, 0]) != r_of(cross[:, 1]))
+    assert cross.shape[0] >= 10 and within.shape[0] >= 10
