@@ -474,6 +474,9 @@ def main():
         torch.cuda.synchronize()
     xtn.profile_enable(False)
     prof = xtn.profile_report()
+    # host-side spans (whole calls, scratch allocations, stream waits) apart
+    host = {k: v for k, v in prof.items() if k.startswith("host_")}
+    prof = {k: v for k, v in prof.items() if not k.startswith("host_")}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1000.0
     value = replica_throughput(pairs * args.steps, total_s)
@@ -536,6 +539,8 @@ def main():
         "gpu_launches": int(launches),
         "roofline": roofline,
         "kernels": kernels,
+        "host_per_step": {k: {"count": v[0] / args.steps, "ms": v[1] / args.steps}
+                          for k, v in host.items()},
         "clocks": clk.summary(),
     }
     if not args.no_extras and world == 1 and args.n is None:

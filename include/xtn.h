@@ -105,8 +105,8 @@ XTN_API int xtn_version(void);
  *   out, cap         : output rows and their capacity (out may be NULL when
  *                      cap == 0, to learn the count).
  *   n_out            : host; receives the exact number of result rows.
- * Scratch comes from the device's stream-ordered pool and is released
- * before the call returns; the call synchronises the stream three times
+ * Scratch comes from the scratch cache (see xtn_scratch_trim) and is given
+ * back before the call returns; the call synchronises the stream three times
  * (record count, candidate count, row count).  With the default grouping the
  * candidate buffer is sized at half the record count before grouping; an
  * input that needs more (thousands of copies of one sequence) is searched
@@ -299,12 +299,31 @@ XTN_API int xtn_tune_get(int knob);
 XTN_API int xtn_tune_count(int knob);
 
 /*
+ * Scratch cache.  Each search, index build or filter call carves its scratch
+ * out of one device block taken from a per-device cache and gives it back
+ * when it returns (stream-ordered: the next call that takes the block waits,
+ * on its own stream, for the work of the call before); a call that needs more
+ * takes the rest from the stream-ordered allocator, and the block grows to
+ * that size the next time it is taken.  So calls in steady state allocate
+ * nothing, and the cache holds about as much device memory as the largest
+ * calls that ran at the same time needed.  xtn_scratch_trim() waits for and
+ * frees the cached blocks of the current device that no call holds, and
+ * returns the allocator's unused memory to the device.
+ * Errors: CUDA.
+ */
+XTN_API int xtn_scratch_trim(void);
+
+/*
  * Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by CUDA events on its stream and tagged with the algorithmic
  * bytes it must move.  xtn_profile_report() synchronises those events and
  * writes one line per kernel name, "name launches total_ms total_bytes\n",
  * into buf (NUL-terminated, truncated to buf_len); it returns the number of
  * lines, and clears the records.  Enabling costs two event records per launch.
+ * Host-side spans are reported the same way, with zero bytes and wall-clock
+ * milliseconds: host_call_search_self / _between / _query (the whole call),
+ * host_scratch_alloc (each scratch allocation outside the cache) and
+ * host_stream_wait (each wait for the stream to drain).
  */
 XTN_API int xtn_profile_enable(int on);
 XTN_API int xtn_profile_report(char* buf, int64_t buf_len);

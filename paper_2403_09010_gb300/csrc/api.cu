@@ -3,6 +3,7 @@
 // self-search, index build, query search and TCRdist filter.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,13 +22,14 @@ namespace {
 struct ProfRec {
   const char* name;
   double bytes;
-  cudaEvent_t a, b;
+  cudaEvent_t a, b;  // null for a host-side span
+  double host_ms;    // wall-clock length of a host-side span
 };
 std::mutex g_prof_mu;
 std::atomic<bool> g_prof_on{false};
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_ev_pool;
-thread_local ProfRec t_pending{nullptr, 0.0, nullptr, nullptr};
+thread_local ProfRec t_pending{nullptr, 0.0, nullptr, nullptr, 0.0};
 
 cudaEvent_t ev_get() {
   {
@@ -60,6 +62,35 @@ void prof_end(cudaStream_t s) {
   g_prof.push_back(t_pending);
   t_pending.name = nullptr;
 }
+
+namespace {
+// Host-side span for the profiler: the wall-clock time of a scope (a whole
+// call, a scratch allocation, a wait for the stream), reported like a kernel.
+class HostSpan {
+ public:
+  explicit HostSpan(const char* name)
+      : name_(name), on_(g_prof_on.load(std::memory_order_relaxed)) {
+    if (on_) t0_ = std::chrono::steady_clock::now();
+  }
+  ~HostSpan() {
+    if (!on_) return;
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.push_back(ProfRec{name_, 0.0, nullptr, nullptr, ms});
+  }
+
+ private:
+  const char* name_;
+  bool on_;
+  std::chrono::steady_clock::time_point t0_;
+};
+
+cudaError_t host_sync(cudaStream_t s) {
+  HostSpan span("host_stream_wait");
+  return cudaStreamSynchronize(s);
+}
+}  // namespace
 
 // --------------------------------------------------------------- device ---
 namespace {
@@ -101,18 +132,50 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Stream-ordered scratch owned by one call; returned to the pool at scope exit.
+// Cached scratch.  Each call carves its buffers out of one workspace, a
+// device block taken from a per-device cache and given back when the call
+// returns, so that a call in steady state allocates nothing: the stream-
+// ordered allocator's own per-call cost grows with the process's history of
+// streams and allocations.  Reuse is stream-ordered through an event: the
+// call that takes a workspace makes its stream wait for the event the
+// previous user recorded on its own stream when it gave the block back.  A
+// call that needs more than the block holds takes the rest from the stream-
+// ordered allocator; the block is grown to the call's total when it is next
+// taken.
+struct Workspace {
+  char* base = nullptr;
+  size_t cap = 0;              // bytes at base
+  size_t want = 0;             // the largest total a call carved from it
+  cudaEvent_t done = nullptr;  // recorded where its last user finished
+};
+struct WorkspaceCache {
+  std::vector<Workspace*> idle;
+};
+std::mutex g_ws_mu;
+std::map<int, WorkspaceCache> g_ws;
+
+constexpr size_t SCRATCH_ALIGN = 256;
+
+// Stream-ordered scratch owned by one call; given back at scope exit.
 class Arena {
  public:
   explicit Arena(cudaStream_t s) : s_(s) {}
-  ~Arena() {
-    for (void* p : ptrs_) cudaFreeAsync(p, s_);
-  }
+  ~Arena() { release(); }
   template <class T>
   T* get(size_t count) {
     if (count == 0) count = 1;
+    // 64 spare bytes behind every buffer, 256-byte aligned starts
+    const size_t bytes = (count * sizeof(T) + 64 + SCRATCH_ALIGN - 1) & ~(SCRATCH_ALIGN - 1);
+    if (!taken_) take();
+    total_ += bytes;
+    if (ws_ && off_ + bytes <= ws_->cap) {
+      void* p = ws_->base + off_;
+      off_ += bytes;
+      return static_cast<T*>(p);
+    }
     void* p = nullptr;
-    if (cudaMallocAsync(&p, count * sizeof(T) + 64, s_) != cudaSuccess) {
+    HostSpan span("host_scratch_alloc");
+    if (cudaMallocAsync(&p, bytes, s_) != cudaSuccess) {
       cudaGetLastError();
       failed_ = true;
       return nullptr;
@@ -121,18 +184,97 @@ class Arena {
     return static_cast<T*>(p);
   }
   bool failed() const { return failed_; }
-  // Frees everything now (stream-ordered), e.g. before a retry that
-  // allocates again.
+  // Gives everything back now (stream-ordered), e.g. before a retry that
+  // takes scratch again.
   void release() {
     for (void* p : ptrs_) cudaFreeAsync(p, s_);
     ptrs_.clear();
+    if (ws_) {
+      ws_->want = std::max(ws_->want, total_);
+      cudaEventRecord(ws_->done, s_);
+      std::lock_guard<std::mutex> g(g_ws_mu);
+      g_ws[dev_].idle.push_back(ws_);
+      ws_ = nullptr;
+    }
+    taken_ = false;
+    off_ = total_ = 0;
   }
 
  private:
+  void take() {
+    taken_ = true;
+    if (cudaGetDevice(&dev_) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(g_ws_mu);
+      auto& idle = g_ws[dev_].idle;
+      if (!idle.empty()) {
+        ws_ = idle.back();
+        idle.pop_back();
+      }
+    }
+    if (!ws_) {
+      ws_ = new Workspace;
+      if (cudaEventCreateWithFlags(&ws_->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete ws_;
+        ws_ = nullptr;
+        return;
+      }
+    }
+    // the previous user's kernels are done with the block before ours start
+    if (cudaStreamWaitEvent(s_, ws_->done, 0) != cudaSuccess) cudaGetLastError();
+    if (ws_->want > ws_->cap) {
+      if (ws_->base) cudaFreeAsync(ws_->base, s_);
+      ws_->base = nullptr;
+      ws_->cap = 0;
+      HostSpan span("host_scratch_alloc");
+      void* p = nullptr;
+      if (cudaMallocAsync(&p, ws_->want, s_) == cudaSuccess) {
+        ws_->base = static_cast<char*>(p);
+        ws_->cap = ws_->want;
+      } else {
+        cudaGetLastError();  // the call takes its buffers one by one instead
+      }
+    }
+  }
+
   cudaStream_t s_;
+  int dev_ = 0;
+  Workspace* ws_ = nullptr;
+  bool taken_ = false;
+  size_t off_ = 0, total_ = 0;
   std::vector<void*> ptrs_;
   bool failed_ = false;
 };
+
+// Frees the cached workspaces of the current device that no call holds.
+int trim_scratch() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return XTN_ERR_CUDA;
+  std::vector<Workspace*> idle;
+  {
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    idle.swap(g_ws[dev].idle);
+  }
+  bool ok = true;
+  for (Workspace* w : idle) {
+    ok &= cudaEventSynchronize(w->done) == cudaSuccess;  // its last user is done
+    if (w->base) ok &= cudaFreeAsync(w->base, 0) == cudaSuccess;
+    cudaEventDestroy(w->done);
+    delete w;
+  }
+  ok &= cudaStreamSynchronize(0) == cudaSuccess;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  if (!ok) {
+    cudaGetLastError();
+    return XTN_ERR_CUDA;
+  }
+  return XTN_OK;
+}
 
 int map_device_err(uint32_t e) {
   if (e & DERR_TIMEOUT) return XTN_ERR_DEVICE_TIMEOUT;
@@ -159,7 +301,7 @@ int map_device_err(uint32_t e) {
 template <class T>
 int read_back(T* host, const T* dev, size_t n, cudaStream_t s) {
   XTN_CK(cudaMemcpyAsync(host, dev, n * sizeof(T), cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
+  XTN_CK(host_sync(s));
   return XTN_OK;
 }
 
@@ -274,7 +416,7 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
   } h{0, 0};
   XTN_CK(cudaMemcpyAsync(&h.n_rec, e->rec_off + n, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
+  XTN_CK(host_sync(s));
   if (h.err) return map_device_err(h.err);
   e->n_rec = h.n_rec;
   if (h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
@@ -484,7 +626,7 @@ int finish_out(const OutRows& o, xtn_triple* out, int64_t cap, uint64_t n_rows, 
   const int64_t w = std::min<int64_t>(cap, (int64_t)n_rows);
   if (o.host && w > 0) {
     XTN_CK(cudaMemcpyAsync(out, o.dev, w * sizeof(xtn_triple), cudaMemcpyDeviceToHost, s));
-    XTN_CK(cudaStreamSynchronize(s));
+    XTN_CK(host_sync(s));
   }
   return (int64_t)n_rows > cap ? XTN_ERR_BUFFER_TOO_SMALL : XTN_OK;
 }
@@ -582,7 +724,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (mode != 1) {
     XTN_CK(cudaMemcpyAsync(&h.direct, counters + 2, 16, cudaMemcpyDeviceToHost, s));
     XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-    XTN_CK(cudaStreamSynchronize(s));
+    XTN_CK(host_sync(s));
     if (h.err & DERR_CAPACITY) {
       ar.release();
       return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
@@ -599,7 +741,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     XTN_CK(cudaGetLastError());
     XTN_CK(cudaMemcpyAsync(&h.groups, counters, 16, cudaMemcpyDeviceToHost, s));
     XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-    XTN_CK(cudaStreamSynchronize(s));
+    XTN_CK(host_sync(s));
     if (h.err) return map_device_err(h.err);
   }
   const uint64_t n_pairs = h.direct + h.pairs;
@@ -635,7 +777,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (rc) return rc;
   XTN_CK(cudaMemcpyAsync(&h.pairs, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
+  XTN_CK(host_sync(s));
   if (h.err) return map_device_err(h.err);
   return finish_out(o, out, cap, h.pairs, s, n_out);
 }
@@ -795,7 +937,7 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
   } h{0, 0};
   XTN_CK(cudaMemcpyAsync(&h.rows, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
+  XTN_CK(host_sync(s));
   if (h.err) return map_device_err(h.err);
   const uint64_t n_rows = h.rows;
   return finish_out(o, out, cap, n_rows, s, n_out);
@@ -844,7 +986,7 @@ int tcrdist_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, const x
   if (herr) return map_device_err(herr);
   if (host_out && total > 0) {
     XTN_CK(cudaMemcpyAsync(out, d_out, total * sizeof(xtn_triple), cudaMemcpyDeviceToHost, s));
-    XTN_CK(cudaStreamSynchronize(s));
+    XTN_CK(host_sync(s));
   }
   *n_out = (int64_t)total;
   return XTN_OK;
@@ -1054,7 +1196,7 @@ int plan_result_impl(xtn_plan* p, xtn_triple* out, int64_t cap, int64_t* n_out, 
   XTN_CK(cudaMemcpyAsync(&h.pairs, p->counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.rows, p->back.counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, p->err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaStreamSynchronize(s));
+  XTN_CK(host_sync(s));
   if (h.err & DERR_CAPACITY) {
     *n_out = (int64_t)h.pairs;
     return XTN_ERR_CAPACITY;
@@ -1064,7 +1206,7 @@ int plan_result_impl(xtn_plan* p, xtn_triple* out, int64_t cap, int64_t* n_out, 
   const int64_t w = std::min<int64_t>(cap, (int64_t)h.rows);
   if (w > 0) {
     XTN_CK(cudaMemcpyAsync(out, p->rows, w * sizeof(xtn_triple), cudaMemcpyDefault, s));
-    XTN_CK(cudaStreamSynchronize(s));
+    XTN_CK(host_sync(s));
   }
   return (int64_t)h.rows > cap ? XTN_ERR_BUFFER_TOO_SMALL : XTN_OK;
 }
@@ -1098,6 +1240,7 @@ int xtn_version(void) { return 10000; }
 int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                     const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
                     int64_t* n_out, xtn_stream_t stream) {
+  xtn::HostSpan span("host_call_search_self");
   return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
                                reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1105,6 +1248,7 @@ int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int 
 int xtn_search_self_hamming(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                             const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out,
                             int64_t cap, int64_t* n_out, xtn_stream_t stream) {
+  xtn::HostSpan span("host_call_search_self");
   return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
                                reinterpret_cast<cudaStream_t>(stream), -1, 1);
 }
@@ -1115,6 +1259,7 @@ int xtn_search_between(const uint8_t* seqs, const int64_t* offsets, int64_t n, i
   if (n_out) *n_out = 0;
   if (metric != XTN_METRIC_LEVENSHTEIN && metric != XTN_METRIC_HAMMING)
     return XTN_ERR_INVALID_ARG;
+  xtn::HostSpan span("host_call_search_between");
   return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
                                reinterpret_cast<cudaStream_t>(stream), -1, metric, true);
 }
@@ -1147,6 +1292,7 @@ int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
 int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out,
                      xtn_stream_t stream) {
+  xtn::HostSpan span("host_call_search_query");
   return xtn::search_query_impl(idx, q_seqs, q_offsets, n_q, out, cap, n_out,
                                 reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1236,6 +1382,8 @@ int xtn_tune_count(int knob) {
   return XTN_ERR_INVALID_ARG;
 }
 
+int xtn_scratch_trim(void) { return xtn::trim_scratch(); }
+
 int xtn_profile_enable(int on) {
   xtn::g_prof_on.store(on != 0);
   return XTN_OK;
@@ -1253,9 +1401,11 @@ int xtn_profile_report(char* buf, int64_t buf_len) {
   };
   std::map<std::string, Agg> agg;
   for (auto& r : recs) {
-    float ms = 0.f;
-    cudaEventSynchronize(r.b);
-    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) cudaGetLastError();
+    float ms = (float)r.host_ms;
+    if (r.a) {
+      cudaEventSynchronize(r.b);
+      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) cudaGetLastError();
+    }
     Agg& a = agg[r.name];
     a.launches++;
     a.ms += ms;
@@ -1264,6 +1414,7 @@ int xtn_profile_report(char* buf, int64_t buf_len) {
   {
     std::lock_guard<std::mutex> g(xtn::g_prof_mu);
     for (auto& r : recs) {
+      if (!r.a) continue;
       xtn::g_ev_pool.push_back(r.a);
       xtn::g_ev_pool.push_back(r.b);
     }

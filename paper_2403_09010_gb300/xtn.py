@@ -293,6 +293,11 @@ def tcrdist_filter(seqs, offsets, rows, max_score: int = 24):
     return out[: n_out.value]
 
 
+def scratch_trim() -> None:
+    """Free the cached scratch blocks of the current device (xtn_scratch_trim)."""
+    check(native.lib().xtn_scratch_trim(), "xtn_scratch_trim")
+
+
 def profile_enable(on: bool = True) -> None:
     native.lib().xtn_profile_enable(1 if on else 0)
 

@@ -416,6 +416,44 @@ def test_autotuned_plan_matches_oracle_and_leaves_knobs(xtn):
     plan.free()
 
 
+def test_scratch_cache_reuse_grow_trim_and_threads(xtn):
+    # calls carve scratch from cached blocks: repeated calls, a larger call
+    # that grows the block, a trim, and calls on two streams from two threads
+    import threading
+    a_s, a_o = gen.workload(gen.SELF_1M, 20_000)
+    b_s, b_o = gen.workload(gen.SELF_1M, 12_000)
+    want_a = oracle.symdel_self(a_s, a_o, 2)
+    want_b = oracle.symdel_self(b_s, b_o, 2)
+    for _ in range(3):
+        assert np.array_equal(_rows(xtn.search_self(a_s, a_o, 2)), want_a)
+    big_s, big_o = gen.workload(gen.SELF_1M, 200_000)
+    big = _rows(xtn.search_self(big_s, big_o, 2))
+    assert np.array_equal(_rows(xtn.search_self(big_s, big_o, 2)), big)
+    assert np.array_equal(_rows(xtn.search_self(b_s, b_o, 2)), want_b)
+    xtn.scratch_trim()
+    assert np.array_equal(_rows(xtn.search_self(a_s, a_o, 2)), want_a)
+    results, errors = {}, []
+
+    def worker(name, s, o, reps):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                ds, do = _dev(s, o)
+                results[name] = [_rows(xtn.search_self(ds, do, 2)) for _ in range(reps)]
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    ts = [threading.Thread(target=worker, args=("a", a_s, a_o, 6)),
+          threading.Thread(target=worker, args=("b", b_s, b_o, 6))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors
+    assert all(np.array_equal(r, want_a) for r in results["a"])
+    assert all(np.array_equal(r, want_b) for r in results["b"])
+
+
 # ---------------------------------------------------- between repertoires ---
 @pytest.mark.parametrize("d,metric", [(1, "levenshtein"), (2, "levenshtein"),
                                       (3, "levenshtein"), (2, "hamming")])
