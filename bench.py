@@ -287,21 +287,29 @@ def run_served(speed: float = 1.0):
     # faster, and all at once (capacity): continuous batching vs a plain queue
     ref_rows = None
     identical = True
-    for label, sp in [("rate_200", speed), ("rate_800", 4 * speed), ("rate_3200", 16 * speed),
-                      ("all_at_once", 1e9)]:
+    # A replay at the faster rates lasts well under a second, so one pause of
+    # the process sets its p99: those rates are replayed three times and the
+    # run with the median p99 is reported, with every run's p99 beside it.
+    for label, sp, reps in [("rate_200", speed, 1), ("rate_800", 4 * speed, 3),
+                            ("rate_3200", 16 * speed, 3), ("all_at_once", 1e9, 3)]:
         res = {}
         for name, kw in [("continuous", dict(slots=4)),
                          ("plain_queue", dict(slots=1, max_batch_queries=1))]:
-            srv = serve.Server(idx, **kw)
-            srv.warm(big.seqs, big.offsets)
-            pend = serve.replay(srv, reqs, speed=sp)
-            srv.close()
-            res[name] = srv.stats(pend)
-            rows = [p.rows for p in pend]
-            if ref_rows is None:
-                ref_rows = rows
-            else:
-                identical &= all(np.array_equal(a, b) for a, b in zip(rows, ref_rows))
+            runs = []
+            for _ in range(reps):
+                srv = serve.Server(idx, **kw)
+                srv.warm(big.seqs, big.offsets)
+                pend = serve.replay(srv, reqs, speed=sp)
+                srv.close()
+                runs.append(srv.stats(pend))
+                rows = [p.rows for p in pend]
+                if ref_rows is None:
+                    ref_rows = rows
+                else:
+                    identical &= all(np.array_equal(a, b) for a, b in zip(rows, ref_rows))
+            runs.sort(key=lambda r: r["p99_ms"])
+            res[name] = dict(runs[len(runs) // 2], replays=reps,
+                             p99_ms_runs=[r["p99_ms"] for r in runs])
         out[label] = res
     out["identical_output"] = bool(identical)
     idx.free()

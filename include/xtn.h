@@ -113,7 +113,9 @@ XTN_API int xtn_version(void);
  * again with all-global grouping, which sizes it exactly, so the result is
  * the same, only slower.
  * Errors: INVALID_ARG, BAD_RESIDUE, SEQ_TOO_LONG, OOM, BUFFER_TOO_SMALL,
- * CUDA, DEVICE_TIMEOUT, TOO_LARGE.
+ * CUDA, DEVICE_TIMEOUT, TOO_LARGE.  An input with 2^32 variant records or more,
+ * or 2^32 candidate pairs or more, is searched in passes as
+ * xtn_search_self_streaming does with max_pass_records = 0.
  */
 XTN_API int xtn_search_self(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                     const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
@@ -151,6 +153,33 @@ XTN_API int xtn_search_self_hamming(const uint8_t* seqs, const int64_t* offsets,
 XTN_API int xtn_search_between(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                                const int64_t* rep_offsets, int64_t n_rep, int metric,
                                xtn_triple* out, int64_t cap, int64_t* n_out, xtn_stream_t stream);
+
+/*
+ * The self-search in passes, for inputs whose variant records do not fit the
+ * device at once (Sec. 2.3, "Overcoming memory bottlenecks"; Appendix A,
+ * XTNeighbor-streaming).  A first expansion only counts the records of each
+ * of 2048 bins of the variant fingerprint.  Next-Fit packs consecutive bins
+ * into passes of at most max_pass_records records (a bin larger than that is
+ * a pass of its own).  Each pass expands only its bins' records, groups them,
+ * and emits and verifies their candidate pairs.  Equal variants fall in one
+ * bin, so no neighbour is missed.  Verified pairs of all passes are kept and
+ * sorted once at the end, which drops pairs found in several passes.  A pass
+ * whose candidate pairs exceed 2^32 words or device memory is split in two.
+ * The rows are those of xtn_search_self (metric 0), xtn_search_self_hamming
+ * (metric 1) or xtn_search_between (between != 0).
+ *   max_pass_records : records per pass; <= 0 takes what fits in half the
+ *                      free device memory (about 32 bytes per record).
+ *   n_passes         : host, may be NULL; receives the passes run.
+ * Other arguments as xtn_search_self.  Device memory: the sequences and
+ * their match vectors, buffers for the largest pass, and the verified pairs.
+ * Errors: as xtn_search_self; INVALID_ARG for an unknown metric, or for
+ * between != 0 without rep_offsets.
+ */
+XTN_API int xtn_search_self_streaming(const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                                      int d, const int64_t* rep_offsets, int64_t n_rep, int metric,
+                                      int between, int64_t max_pass_records, xtn_triple* out,
+                                      int64_t cap, int64_t* n_out, int64_t* n_passes,
+                                      xtn_stream_t stream);
 
 /*
  * Build a device-resident index of a reference set: its encoded sequences

@@ -397,8 +397,10 @@ struct Encoded {
   uint64_t n_rec = 0;
 };
 
+// allow_large: return the count even when it is 2^32 or more (the caller
+// then searches in passes); otherwise that is TOO_LARGE.
 int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStream_t s,
-                     Encoded* e) {
+                     Encoded* e, bool allow_large = false) {
   const int64_t n = in.n;
   e->keys = ar.get<Key128>(n);
   e->lens = ar.get<uint8_t>(n);
@@ -419,7 +421,7 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
   XTN_CK(host_sync(s));
   if (h.err) return map_device_err(h.err);
   e->n_rec = h.n_rec;
-  if (h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  if (!allow_large && h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
   return XTN_OK;
 }
 
@@ -470,11 +472,12 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
                        int id_bits, uint64_t* A, uint64_t* B, uint64_t rec_cap, int lo,
                        uint32_t* hist, uint64_t* digit_base, uint64_t* status, int cfg,
                        int hist_mode, int mode, const GroupScratch& gs, int sms, uint32_t* err,
-                       cudaStream_t s, const uint64_t* n_rec_dev, uint64_t** sorted) {
+                       cudaStream_t s, const uint64_t* n_rec_dev, uint64_t** sorted,
+                       const BinSel* sel = nullptr) {
   if (mode == 1) {
     const bool in_passes = hist_mode == 1;
     launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, lo,
-                  in_passes ? std::min(64, lo + 8) : 64, sms, err, s);
+                  in_passes ? std::min(64, lo + 8) : 64, sms, err, s, sel);
     XTN_CK(cudaGetLastError());
     XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
                              sorted, "k_onesweep_records", s, in_passes, n_rec_dev, nullptr,
@@ -492,7 +495,7 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
   if (g.G > 0)
     XTN_CK(cudaMemsetAsync(gs.bucket_start, 0xFF, ((size_t)1 << g.G) * 8, s));
   launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, glo,
-                g.G == 0 ? glo : (in_passes ? glo + 8 : 64), sms, err, s);
+                g.G == 0 ? glo : (in_passes ? glo + 8 : 64), sms, err, s, sel);
   XTN_CK(cudaGetLastError());
   uint64_t* X = A;
   XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, glo, 64, hist, digit_base, status, cfg, err,
@@ -573,6 +576,26 @@ size_t back_status_bytes(uint64_t cand_cap, int cfg) {
                   verify_status_bytes((int64_t)cand_cap));
 }
 
+// Sort the verified words surv[0, n) (n = *n_dev when given, else cap; tmp
+// is the second buffer, both hold cap words) by their pair_bits low bits
+// with the digit counts in hist, drop repeated words and write the rows;
+// *n_rows receives the row count.
+int launch_sort_unique(uint64_t* surv, uint64_t* tmp, uint64_t cap, const uint64_t* n_dev,
+                       uint32_t pair_bits, uint32_t j_bits, uint32_t* hist, uint64_t* digit_base,
+                       uint64_t* status, const uint32_t* peq_i, const uint8_t* lens_i,
+                       uint64_t n_i, const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
+                       int metric, xtn_triple* rows, int64_t row_cap, uint32_t* err,
+                       uint64_t* n_rows, cudaStream_t s, int cfg) {
+  uint64_t* sorted = nullptr;
+  XTN_CK(radix_sort_passes(surv, tmp, (int64_t)cap, 0, (int)pair_bits, hist, digit_base, status,
+                           cfg, err, &sorted, "k_onesweep_pairs", s, false, n_dev, nullptr,
+                           onesweep_unstable_config()));
+  launch_unique_finalize(sorted, (int64_t)cap, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
+                         n_j, metric, rows, row_cap, status, err, n_rows, s);
+  XTN_CK(cudaGetLastError());
+  return XTN_OK;
+}
+
 int launch_back(const BackStage& b, uint64_t cand_cap, const uint64_t* n_cand_dev,
                 uint32_t pair_bits, uint32_t j_bits, const uint32_t* peq_i, const uint8_t* lens_i,
                 uint64_t n_i, const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
@@ -583,14 +606,9 @@ int launch_back(const BackStage& b, uint64_t cand_cap, const uint64_t* n_cand_de
   launch_verify_candidates(b.P1, cand_cap, n_cand_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
                            n_j, seq_rep, self_mode, d, metric, b.P2, cand_cap, b.counters, b.hist,
                            (int)pair_bits, sms, err, s);
-  uint64_t* sorted = nullptr;
-  XTN_CK(radix_sort_passes(b.P2, b.P1, (int64_t)cand_cap, 0, (int)pair_bits, b.hist, b.digit_base,
-                           b.status, cfg, err, &sorted, "k_onesweep_pairs", s, false, b.counters,
-                           nullptr, onesweep_unstable_config()));
-  launch_unique_finalize(sorted, (int64_t)cand_cap, b.counters, j_bits, peq_i, lens_i, n_i, keys_j,
-                         lens_j, n_j, metric, rows, row_cap, b.status, err, b.counters + 1, s);
-  XTN_CK(cudaGetLastError());
-  return XTN_OK;
+  return launch_sort_unique(b.P2, b.P1, cand_cap, b.counters, pair_bits, j_bits, b.hist,
+                            b.digit_base, b.status, peq_i, lens_i, n_i, keys_j, lens_j, n_j, metric,
+                            rows, row_cap, err, b.counters + 1, s, cfg);
 }
 
 // Result rows go to `out` directly when it is device memory; otherwise into
@@ -657,6 +675,280 @@ __global__ void k_pair_total(const uint64_t* __restrict__ pair_off,
   *out = pair_off[*n_groups];
 }
 
+// A device buffer of 64-bit words that a multi-pass call grows as it goes
+// (stream-ordered, outside the scratch cache: its size is not known ahead).
+struct GrowBuf {
+  explicit GrowBuf(cudaStream_t st) : s(st) {}
+  ~GrowBuf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  // At least `need` words; the first `keep` words survive a move.
+  bool reserve(uint64_t need, uint64_t keep) {
+    if (need <= cap) return true;
+    const uint64_t c = std::max(need, cap + cap / 2);
+    void* q = nullptr;
+    HostSpan span("host_scratch_alloc");
+    if (cudaMallocAsync(&q, (c + 8) * 8, s) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (keep && cudaMemcpyAsync(q, p, keep * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeAsync(q, s);
+      return false;
+    }
+    if (p) cudaFreeAsync(p, s);
+    p = static_cast<uint64_t*>(q);
+    cap = c;
+    return true;
+  }
+  cudaStream_t s;
+  uint64_t* p = nullptr;
+  uint64_t cap = 0;
+};
+
+// Records one pass may hold when the caller sets no budget: what a pass needs
+// (two record buffers, candidate words, flags: about 32 bytes per record) in
+// half the free device memory, below 2^32.
+uint64_t default_pass_records() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 1ull << 28;
+  }
+  return std::max<uint64_t>(1ull << 20, (uint64_t)free_b / 2 / 32);
+}
+
+// The self-search in passes over fingerprint bins, for inputs whose variant
+// records do not fit at once (Sec. 2.3, "Overcoming memory bottlenecks";
+// Appendix A, XTNeighbor-streaming).  A counting expansion gives the records
+// of every bin (the MAX_BIN_BITS lowest bits of the fingerprint field);
+// Next-Fit packs consecutive bins into passes of at most max_pass records;
+// each pass expands only its bins' records, groups them and emits and
+// verifies their candidate pairs.  Equal variants share their fingerprint
+// and so their bin, so every candidate of the one-pass search is a candidate
+// of some pass.  A pair that shares variants in several bins is found in
+// several passes: the verified words of all passes are kept and sorted once
+// at the end, which drops those repeats.  (The paper bins candidate pairs by
+// min(i, j) instead, so that it can remove repeats before verifying; here
+// verification comes first, and only its survivors are kept.)  A pass whose
+// candidates exceed 2^32 words or device memory is split in two at its
+// middle bin.  Arguments as search_self_impl; max_pass <= 0 takes
+// default_pass_records(); *n_passes receives the passes run.
+int search_stream_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                       const int64_t* rep_offsets, int64_t n_rep, int metric, bool between,
+                       int64_t max_pass, xtn_triple* out, int64_t cap, int64_t* n_out,
+                       int64_t* n_passes, cudaStream_t s) {
+  if (!n_out) return XTN_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (n_passes) *n_passes = 0;
+  if (n < 0 || d < 0 || d > XTN_MAX_D || cap < 0 || !offsets) return XTN_ERR_INVALID_ARG;
+  if (metric != XTN_METRIC_LEVENSHTEIN && metric != XTN_METRIC_HAMMING) return XTN_ERR_INVALID_ARG;
+  if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
+  if (rep_offsets && n_rep < 1) return XTN_ERR_INVALID_ARG;
+  if (between && !rep_offsets) return XTN_ERR_INVALID_ARG;
+  if (n == 0) return XTN_OK;
+  int sms = 0;
+  int rc = current_device_info(&sms);
+  if (rc) return rc;
+  Arena ar(s);
+  constexpr uint32_t NB = 1u << MAX_BIN_BITS;
+  uint32_t* err = ar.get<uint32_t>(4);
+  // [0] groups [1] pairs [2] direct candidates [3] large-bucket records
+  // [4] records appended [5] survivors [6] rows
+  uint64_t* ctr = ar.get<uint64_t>(8);
+  uint32_t* bins = ar.get<uint32_t>(NB);
+  XTN_ALLOC_OK(ar);
+  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(cudaMemsetAsync(ctr, 0, 64, s));
+  XTN_CK(cudaMemsetAsync(bins, 0, NB * 4, s));
+  DevSeqs in;
+  rc = stage_seqs(seqs, offsets, n, ar, s, &in);
+  if (rc) return rc;
+  uint32_t* seq_rep = nullptr;
+  if (rep_offsets) {
+    seq_rep = ar.get<uint32_t>(n);
+    XTN_ALLOC_OK(ar);
+    rc = stage_reps(rep_offsets, n_rep, n, &ar, s, seq_rep);
+    if (rc) return rc;
+  }
+  Encoded e;
+  rc = encode_and_count(in, d, ar, err, s, &e, true);
+  if (rc) return rc;
+  const uint32_t id_bits = bits_for((uint64_t)n);
+  const uint32_t* salt_rep = between ? nullptr : seq_rep;
+
+  // records per bin
+  BinSel sel;
+  sel.shift = id_bits;
+  sel.mask = NB - 1u;
+  sel.bin_count = bins;
+  launch_expand(e.keys, e.lens, e.eqprev, e.rec_off, n, d, salt_rep, id_bits, nullptr, e.n_rec,
+                nullptr, 0, 8, sms, err, s, &sel);
+  XTN_CK(cudaGetLastError());
+  std::vector<uint32_t> hb(NB);
+  uint32_t herr = 0;
+  XTN_CK(cudaMemcpyAsync(hb.data(), bins, NB * 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(host_sync(s));
+  if (herr) return map_device_err(herr);
+  std::vector<uint64_t> pre(NB + 1, 0);  // records of bins [0, b)
+  for (uint32_t b = 0; b < NB; ++b) pre[b + 1] = pre[b] + hb[b];
+  if (pre[NB] != e.n_rec) return XTN_ERR_CUDA;  // the two expansions disagree
+
+  // Next-Fit over consecutive bins
+  const uint64_t limit = (1ull << 32) - (1ull << 20);
+  const uint64_t R = std::min<uint64_t>(max_pass > 0 ? (uint64_t)max_pass : default_pass_records(),
+                                        limit);
+  std::vector<std::pair<uint32_t, uint32_t>> work;  // bin ranges, run from the back
+  for (uint32_t b0 = 0, b = 0; b <= NB; ++b) {
+    if (b == NB || (pre[b] > pre[b0] && pre[b + 1] - pre[b0] > R)) {
+      if (pre[b] > pre[b0]) work.emplace_back(b0, b);
+      b0 = b;
+    }
+  }
+  std::reverse(work.begin(), work.end());
+  uint64_t P = 0;  // records of the largest pass
+  for (auto& w : work) P = std::max(P, pre[w.second] - pre[w.first]);
+  if (P >= limit) return XTN_ERR_TOO_LARGE;  // one bin beyond a pass
+
+  // buffers for the largest pass
+  const int hs = choose_hash_bits(P, id_bits);
+  const int lo = 64 - hs;
+  const int cfg = g_cfg_records.load();
+  const int cfg_pairs = g_cfg_pairs.load();
+  const int mode0 = g_grouping.load();
+  const uint64_t g_cap = P / 2 + 1;
+  uint64_t* A = ar.get<uint64_t>(P + 8);
+  uint64_t* B = ar.get<uint64_t>(P + 8);
+  uint32_t* hist = ar.get<uint32_t>(MAX_PASSES * RADIX);
+  uint32_t* phist = ar.get<uint32_t>(MAX_PASSES * RADIX);  // survivors, over all passes
+  uint64_t* digit_base = ar.get<uint64_t>(MAX_PASSES * RADIX);
+  uint64_t* status = ar.get<uint64_t>(radix_status_bytes(P, cfg) / 8 + 1);
+  GroupScratch gs0;
+  gs0.bucket_start = ar.get<uint64_t>(bucket_start_words(P, hs, 0));
+  gs0.flags = ar.get<uint64_t>(group_flag_words((int64_t)P));
+  gs0.gstatus = ar.get<uint64_t>(
+      std::max(group_status_bytes((int64_t)P), scan_status_bytes((int64_t)g_cap)) / 8 + 1);
+  uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
+  XTN_ALLOC_OK(ar);
+  GrowBuf cand(s), surv(s);
+  if (!cand.reserve(std::max<uint64_t>(P / 2, 1u << 20), 0) ||
+      !surv.reserve(std::max<uint64_t>((uint64_t)n, 1u << 20), 0))
+    return XTN_ERR_OOM;
+  XTN_CK(cudaMemsetAsync(phist, 0, MAX_PASSES * RADIX * 4, s));
+  launch_peq(e.keys, e.lens, n, peq, s);
+  const uint32_t pair_bits = 2 * id_bits;
+
+  int64_t passes_run = 0;
+  while (!work.empty()) {
+    const auto w = work.back();
+    work.pop_back();
+    const uint64_t np = pre[w.second] - pre[w.first];
+    int mode = mode0;
+    bool split = false;
+    for (;;) {  // at most twice: the tuned grouping, then all-global
+      XTN_CK(cudaMemsetAsync(ctr, 0, 40, s));
+      XTN_CK(cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, s));
+      sel.lo = w.first;
+      sel.hi = w.second;
+      sel.bin_count = nullptr;
+      sel.append = reinterpret_cast<unsigned long long*>(ctr + 4);
+      GroupScratch gs = gs0;
+      if (mode != 1) {
+        gs.cand = cand.p;
+        gs.cand_cap = cand.cap;
+        gs.cand_count = ctr + 2;
+      }
+      uint64_t* sorted = nullptr;
+      XTN_CK(expand_sort_launch(e.keys, e.lens, e.eqprev, e.rec_off, n, d, salt_rep, id_bits, A,
+                                B, np, lo, hist, digit_base, status, cfg, g_record_hist.load(),
+                                mode, gs, sms, err, s, nullptr, &sorted, &sel));
+      struct {
+        uint64_t direct, large, appended, survivors;
+        uint64_t groups, pairs;
+        uint32_t err;
+      } h{0, 0, 0, 0, 0, 0, 0};
+      XTN_CK(cudaMemcpyAsync(&h.direct, ctr + 2, 32, cudaMemcpyDeviceToHost, s));
+      XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+      XTN_CK(host_sync(s));
+      if (mode != 1 && (h.err & DERR_CAPACITY)) {
+        XTN_CK(cudaMemsetAsync(err, 0, 4, s));
+        mode = 1;
+        continue;
+      }
+      if (h.err) return map_device_err(h.err);
+      if (h.appended != np) return XTN_ERR_CUDA;  // the two expansions disagree
+      uint32_t* S = reinterpret_cast<uint32_t*>(sorted == A ? B : A);
+      uint32_t* E = S + g_cap;
+      uint64_t* pair_off = reinterpret_cast<uint64_t*>(E + g_cap);
+      if (mode == 1 || h.large > 0) {
+        launch_group_finish(gs.flags, (int64_t)np, nullptr, S, E, g_cap, gs.gstatus, err, ctr, s);
+        launch_scan_group_pairs(S, E, (int64_t)g_cap, ctr, pair_off, gs.gstatus, err, s);
+        k_pair_total<<<1, 1, 0, s>>>(pair_off, ctr, ctr + 1);
+        XTN_CK(cudaGetLastError());
+        XTN_CK(cudaMemcpyAsync(&h.groups, ctr, 16, cudaMemcpyDeviceToHost, s));
+        XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+        XTN_CK(host_sync(s));
+        if (h.err) return map_device_err(h.err);
+      }
+      const uint64_t n_pairs = h.direct + h.pairs;
+      if (mode != 1 && n_pairs > cand.cap) {
+        mode = 1;
+        continue;
+      }
+      if (n_pairs >= limit || !cand.reserve(n_pairs, 0) ||
+          !surv.reserve(h.survivors + n_pairs, h.survivors)) {
+        if (w.second - w.first < 2) return n_pairs >= limit ? XTN_ERR_TOO_LARGE : XTN_ERR_OOM;
+        const uint32_t mid = w.first + (w.second - w.first) / 2;
+        work.emplace_back(mid, w.second);
+        work.emplace_back(w.first, mid);
+        split = true;
+        break;
+      }
+      if (h.pairs)
+        launch_emit_pairs(sorted, np, S, pair_off, (int64_t)h.groups, nullptr, h.pairs, id_bits,
+                          cand.p + h.direct, nullptr, nullptr, sms, err, s);
+      if (n_pairs)
+        launch_verify_candidates(cand.p, n_pairs, nullptr, id_bits, peq, e.lens, (uint64_t)n,
+                                 e.keys, e.lens, (uint64_t)n, seq_rep, between ? 2 : 1, d, metric,
+                                 surv.p, surv.cap, ctr + 5, phist, (int)pair_bits, sms, err, s);
+      XTN_CK(cudaGetLastError());
+      break;
+    }
+    if (!split) ++passes_run;
+  }
+  if (n_passes) *n_passes = passes_run;
+
+  // the survivors of every pass: sort, drop repeats, write rows
+  struct {
+    uint64_t survivors;
+    uint32_t err;
+  } f{0, 0};
+  XTN_CK(cudaMemcpyAsync(&f.survivors, ctr + 5, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&f.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(host_sync(s));
+  if (f.err) return map_device_err(f.err);
+  if (f.survivors == 0) return XTN_OK;
+  GrowBuf tmp(s);
+  if (!tmp.reserve(f.survivors, 0)) return XTN_ERR_OOM;
+  uint64_t* pstatus = ar.get<uint64_t>(back_status_bytes(f.survivors, cfg_pairs) / 8 + 1);
+  XTN_ALLOC_OK(ar);
+  OutRows o;
+  rc = prepare_out(out, cap, f.survivors, ar, &o);
+  if (rc) return rc;
+  rc = launch_sort_unique(surv.p, tmp.p, f.survivors, nullptr, pair_bits, id_bits, phist,
+                          digit_base, pstatus, peq, e.lens, (uint64_t)n, e.keys, e.lens,
+                          (uint64_t)n, metric, o.dev, o.dev_cap, err, ctr + 6, s, cfg_pairs);
+  if (rc) return rc;
+  uint64_t rows = 0;
+  XTN_CK(cudaMemcpyAsync(&rows, ctr + 6, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&f.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(host_sync(s));
+  if (f.err) return map_device_err(f.err);
+  return finish_out(o, out, cap, rows, s, n_out);
+}
+
 // mode: grouping mode (see g_grouping), -1 = the tuned one.  metric: 0 =
 // Levenshtein, 1 = Hamming (the Hamming variant: the same candidates, the
 // last step filters by Hamming distance).  between: report the pairs between
@@ -696,6 +988,11 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   // front: encode (read back the record count), expand, sort, group, offsets
   Encoded e;
   rc = encode_and_count(in, d, ar, err, s, &e);
+  if (rc == XTN_ERR_TOO_LARGE) {  // 2^32 records or more: search in passes
+    ar.release();
+    return search_stream_impl(seqs, offsets, n, d, rep_offsets, n_rep, metric, between, 0, out,
+                              cap, n_out, nullptr, s);
+  }
   if (rc) return rc;
   Sorted so;
   const uint64_t g_cap = e.n_rec / 2 + 1;
@@ -746,7 +1043,11 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   }
   const uint64_t n_pairs = h.direct + h.pairs;
   if (n_pairs == 0) return XTN_OK;
-  if (n_pairs >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  if (n_pairs >= (1ull << 32)) {  // candidate words past 2^32: search in passes
+    ar.release();
+    return search_stream_impl(seqs, offsets, n, d, rep_offsets, n_rep, metric, between, 0, out,
+                              cap, n_out, nullptr, s);
+  }
   if (mode != 1 && n_pairs > direct.cand_cap) {
     ar.release();
     return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
@@ -1262,6 +1563,16 @@ int xtn_search_between(const uint8_t* seqs, const int64_t* offsets, int64_t n, i
   xtn::HostSpan span("host_call_search_between");
   return xtn::search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out,
                                reinterpret_cast<cudaStream_t>(stream), -1, metric, true);
+}
+
+int xtn_search_self_streaming(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
+                              const int64_t* rep_offsets, int64_t n_rep, int metric, int between,
+                              int64_t max_pass_records, xtn_triple* out, int64_t cap,
+                              int64_t* n_out, int64_t* n_passes, xtn_stream_t stream) {
+  xtn::HostSpan span("host_call_search_streaming");
+  return xtn::search_stream_impl(seqs, offsets, n, d, rep_offsets, n_rep, metric, between != 0,
+                                 max_pass_records, out, cap, n_out, n_passes,
+                                 reinterpret_cast<cudaStream_t>(stream));
 }
 
 int xtn_index_build(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,

@@ -122,16 +122,62 @@ __device__ __forceinline__ void count_digits(uint32_t* s_hist, uint64_t rec, int
   }
 }
 
+// Where a finished record goes (all lanes of the warp call this together;
+// `valid` says whether this lane holds a record):
+//   SEL_ALL    out[pos], its digits counted for the sort
+//   SEL_COUNT  only its fingerprint bin counted (s_hist holds the bins)
+//   SEL_APPEND appended to out when its bin lies in [sel.lo, sel.hi), one
+//              atomic per warp; its digits counted
+static_assert((1 << MAX_BIN_BITS) <= MAX_PASSES * RADIX, "bins share the digit histogram");
+
+template <int SEL>
+__device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t pos,
+                                             uint64_t* __restrict__ out, uint64_t n_rec,
+                                             uint32_t* s_hist, int hist_lo, int hist_passes,
+                                             uint32_t last_mask, const BinSel& sel, uint32_t lane,
+                                             uint32_t* __restrict__ err) {
+  if constexpr (SEL == SEL_ALL) {
+    if (valid) {
+      out[pos] = rec;
+      count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+    }
+  } else {
+    const uint32_t bin = (uint32_t)(rec >> sel.shift) & sel.mask;
+    if constexpr (SEL == SEL_COUNT) {
+      if (valid) atomicAdd(&s_hist[bin], 1u);
+    } else {
+      const bool keep = valid && bin >= sel.lo && bin < sel.hi;
+      const uint32_t bal = __ballot_sync(FULL_MASK, keep);
+      if (!bal) return;
+      const uint32_t leader = (uint32_t)(__ffs(bal) - 1);
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(sel.append, (unsigned long long)__popc(bal));
+      base = __shfl_sync(FULL_MASK, base, leader);
+      if (keep) {
+        const uint64_t slot = base + __popc(bal & ((1u << lane) - 1u));
+        if (slot < n_rec) {
+          out[slot] = rec;
+          count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+        } else {
+          atomicOr(err, DERR_RANGE);
+        }
+      }
+    }
+  }
+}
+
+template <int SEL>
 __global__ void __launch_bounds__(EXPAND_THREADS)
     k_expand(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens,
              const uint32_t* __restrict__ eqprev, const uint64_t* __restrict__ rec_off, int64_t n,
              int d, const uint32_t* __restrict__ seq_rep, uint32_t id_bits,
              uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist, int hist_lo,
-             int hist_passes, int hist_hi, uint32_t* __restrict__ err) {
+             int hist_passes, int hist_hi, BinSel sel, uint32_t* __restrict__ err) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   __shared__ VariantTables s_tab;
   __shared__ WarpVariants s_warp[EXPAND_THREADS / 32];
-  for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  const int n_hist = SEL == SEL_COUNT ? (int)sel.mask + 1 : hist_passes * RADIX;
+  for (int k = threadIdx.x; k < n_hist; k += blockDim.x) s_hist[k] = 0;
   init_variant_tables(&s_tab);
   __syncthreads();
   WarpVariants* w = &s_warp[threadIdx.x >> 5];
@@ -165,7 +211,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
       const uint32_t eq = __shfl_sync(FULL_MASK, mEq, j);
       const uint64_t base = __shfl_sync(FULL_MASK, mBase, j);
       uint32_t cnt = (uint32_t)(__shfl_sync(FULL_MASK, mEnd, j) - base);
-      if (base + cnt > n_rec) {
+      if (SEL == SEL_ALL && base + cnt > n_rec) {
         if (lane == 0) atomicOr(err, DERR_RANGE);
         cnt = 0;
       }
@@ -177,11 +223,13 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
           if (lane == 0) atomicOr(err, DERR_RANGE);
           total = 0;
         }
-        for (uint32_t v = lane; v < total; v += 32) {
-          const uint64_t rec =
-              (canonical_fingerprint_d2(w, &s_tab, sh, v, salt) & ~idmask) | (uint64_t)s;
-          out[base + v] = rec;
-          count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+        for (uint32_t v0 = 0; v0 < total; v0 += 32) {
+          const uint32_t v = v0 + lane;
+          uint64_t rec = 0;
+          if (v < total)
+            rec = (canonical_fingerprint_d2(w, &s_tab, sh, v, salt) & ~idmask) | (uint64_t)s;
+          place_record<SEL>(rec, v < total, base + v, out, n_rec, s_hist, hist_lo, hist_passes,
+                            last_mask, sel, lane, err);
         }
       } else {
         // every subset with <= d deletions, canonical ones kept (ballot compaction)
@@ -197,11 +245,11 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
           }
           const uint32_t bal = __ballot_sync(FULL_MASK, keep);
           const uint32_t slot = written + __popc(bal & lt_mask);
-          if (keep && slot < cnt) {
-            const uint64_t rec = (subset_fingerprint(w, L, ss, salt) & ~idmask) | (uint64_t)s;
-            out[base + slot] = rec;
-            count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
-          }
+          const bool ok = keep && slot < cnt;
+          uint64_t rec = 0;
+          if (ok) rec = (subset_fingerprint(w, L, ss, salt) & ~idmask) | (uint64_t)s;
+          place_record<SEL>(rec, ok, base + slot, out, n_rec, s_hist, hist_lo, hist_passes,
+                            last_mask, sel, lane, err);
           written += __popc(bal);
         }
         if (written != cnt && lane == 0) atomicOr(err, DERR_RANGE);
@@ -209,8 +257,9 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x)
-    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+  uint32_t* dst = SEL == SEL_COUNT ? sel.bin_count : hist;
+  for (int k = threadIdx.x; k < n_hist; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&dst[k], s_hist[k]);
 }
 
 // Packed expansion for d <= 2.  A warp takes PACK_SEQS consecutive
@@ -235,16 +284,19 @@ struct PackedSeqs {
   uint8_t ds[PACK_SEQS][XTN_MAX_LEN / 2 + 1];
 };
 
+template <int SEL>
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_expand_packed(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens,
                     const uint32_t* __restrict__ eqprev, const uint64_t* __restrict__ rec_off,
                     int64_t n, int d, const uint32_t* __restrict__ seq_rep, uint32_t id_bits,
                     uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist,
-                    int hist_lo, int hist_passes, int hist_hi, uint32_t* __restrict__ err) {
+                    int hist_lo, int hist_passes, int hist_hi, BinSel sel,
+                    uint32_t* __restrict__ err) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   __shared__ VariantTables s_tab;
   __shared__ PackedSeqs s_seq[PACK_WARPS];
-  for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x) s_hist[k] = 0;
+  const int n_hist = SEL == SEL_COUNT ? (int)sel.mask + 1 : hist_passes * RADIX;
+  for (int k = threadIdx.x; k < n_hist; k += blockDim.x) s_hist[k] = 0;
   init_variant_tables(&s_tab);
   __syncthreads();
   PackedSeqs* ps = &s_seq[threadIdx.x >> 5];
@@ -291,7 +343,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
       for (uint32_t i = 0; runs; ++i, runs &= runs - 1) ps->rs[lane][i] = (uint8_t)(__ffs(runs) - 1);
       for (uint32_t i = 0; dbl; ++i, dbl &= dbl - 1) ps->ds[lane][i] = (uint8_t)(__ffs(dbl) - 1);
       total = canonical_total_d2(SeqShape{L, R, nD}, d);
-      if (total != cnt || base + cnt > n_rec) {
+      if (total != cnt || (SEL == SEL_ALL && base + cnt > n_rec)) {
         atomicOr(err, DERR_RANGE);
         total = 0;
       }
@@ -321,6 +373,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
       const uint32_t Rj = __shfl_sync(FULL_MASK, R, (int)j);
       const uint32_t Dj = __shfl_sync(FULL_MASK, nD, (int)j);
       const uint64_t saltj = __shfl_sync(FULL_MASK, salt, (int)j);
+      uint64_t rec = 0;
       if (t < T) {
         const uint32_t v = t - sj;
         // canonical variant v of sequence j (numbering of canonical_fingerprint_d2)
@@ -340,16 +393,17 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
         };
         const uint64_t h = P(p1) + HASH_BINV * ((P(p2) - P(p1 + 1)) +
                                                 HASH_BINV * (P(Lj) - P(p2 + 1)));
-        const uint64_t rec = (mix64(h ^ saltj) & ~idmask) | (uint64_t)(s0 + j);
-        out[base0 + t] = rec;
-        count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+        rec = (mix64(h ^ saltj) & ~idmask) | (uint64_t)(s0 + j);
       }
+      place_record<SEL>(rec, t < T, base0 + t, out, n_rec, s_hist, hist_lo, hist_passes,
+                        last_mask, sel, lane, err);
     }
     __syncwarp();  // the next batch overwrites the tables
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x)
-    if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+  uint32_t* dst = SEL == SEL_COUNT ? sel.bin_count : hist;
+  for (int k = threadIdx.x; k < n_hist; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&dst[k], s_hist[k]);
 }
 
 // Match vectors: peq[i * PEQ_STRIDE + c - 1] = {positions p of sequence i with code c}.
@@ -412,25 +466,46 @@ void launch_encode(const uint8_t* seqs, const int64_t* off, int64_t n, int d, Ke
   prof_end(s);
 }
 
-void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
-                   const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
-                   uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
-                   int hist_hi, int sms, uint32_t* err, cudaStream_t s) {
-  if (n <= 0) return;
-  const int passes = (hist_hi - hist_lo + 7) / 8;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-  if (blocks < 1) blocks = 1;
-  prof_begin(s, "k_expand", (double)n_rec * 8.0 + (double)n * 29.0);
+template <int SEL>
+static void expand_launch(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
+                          const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
+                          uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist,
+                          int hist_lo, int passes, int hist_hi, const BinSel& sel, int sms,
+                          uint32_t* err, cudaStream_t s) {
   if (d <= 2) {
     const int pblocks = (int)std::min<int64_t>(
         (n + PACK_WARPS * PACK_SEQS - 1) / (PACK_WARPS * PACK_SEQS), (int64_t)sms * 8);
-    k_expand_packed<<<pblocks > 0 ? pblocks : 1, PACK_WARPS * 32, 0, s>>>(
+    k_expand_packed<SEL><<<pblocks > 0 ? pblocks : 1, PACK_WARPS * 32, 0, s>>>(
         keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec, hist, hist_lo, passes,
-        hist_hi, err);
+        hist_hi, sel, err);
   } else {
-    k_expand<<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, eqprev, rec_off, n, d, seq_rep,
-                                               id_bits, out, n_rec, hist, hist_lo, passes, hist_hi,
-                                               err);
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    if (blocks < 1) blocks = 1;
+    k_expand<SEL><<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, eqprev, rec_off, n, d, seq_rep,
+                                                    id_bits, out, n_rec, hist, hist_lo, passes,
+                                                    hist_hi, sel, err);
+  }
+}
+
+void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
+                   const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
+                   uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
+                   int hist_hi, int sms, uint32_t* err, cudaStream_t s, const BinSel* sel) {
+  if (n <= 0) return;
+  const int passes = (hist_hi - hist_lo + 7) / 8;
+  const BinSel none{};
+  if (!sel) {
+    prof_begin(s, "k_expand", (double)n_rec * 8.0 + (double)n * 29.0);
+    expand_launch<SEL_ALL>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec, hist,
+                           hist_lo, passes, hist_hi, none, sms, err, s);
+  } else if (sel->append) {
+    prof_begin(s, "k_expand_bins", (double)n_rec * 8.0 + (double)n * 29.0);
+    expand_launch<SEL_APPEND>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec,
+                              hist, hist_lo, passes, hist_hi, *sel, sms, err, s);
+  } else {
+    prof_begin(s, "k_expand_count", (double)n * 29.0);
+    expand_launch<SEL_COUNT>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec,
+                             hist, hist_lo, passes, hist_hi, *sel, sms, err, s);
   }
   prof_end(s);
 }

@@ -25,10 +25,26 @@ std::atomic<int>& cfg_pairs();
 void launch_encode(const uint8_t* seqs, const int64_t* off, int64_t n, int d, Key128* keys,
                    uint8_t* lens, uint32_t* eqprev, uint32_t* vcount, uint32_t* err,
                    cudaStream_t s);
+// Record selection by fingerprint bin, bin = (record >> shift) & mask, for
+// searches that take the records in several passes.  With `append` null the
+// expand kernel only counts records per bin into bin_count[0 .. mask] (mask
+// < 2048) and writes nothing; otherwise it appends the records whose bin lies
+// in [lo, hi) to out[0, n_rec), counting them in *append.
+enum { SEL_ALL = 0, SEL_COUNT = 1, SEL_APPEND = 2 };
+struct BinSel {
+  uint32_t shift = 0, mask = 0;
+  uint32_t lo = 0, hi = 0;
+  uint32_t* bin_count = nullptr;
+  unsigned long long* append = nullptr;
+};
+constexpr int MAX_BIN_BITS = 11;
+
+// sel null: every record of sequence i goes to out[rec_off[i] ...].
 void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
                    const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
                    uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
-                   int hist_hi, int sms, uint32_t* err, cudaStream_t s);
+                   int hist_hi, int sms, uint32_t* err, cudaStream_t s,
+                   const BinSel* sel = nullptr);
 void launch_peq(const Key128* keys, const uint8_t* lens, int64_t n, uint32_t* peq,
                 cudaStream_t s);
 void launch_seq_rep(const int64_t* rep_off, int64_t n_rep, uint32_t* seq_rep, int64_t n,

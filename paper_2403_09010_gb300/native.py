@@ -42,6 +42,8 @@ SIGNATURES = {
     "xtn_search_self": (_I, [_P, _P, _I64, _I, _P, _I64, _P, _I64, _P, _P]),
     "xtn_search_self_hamming": (_I, [_P, _P, _I64, _I, _P, _I64, _P, _I64, _P, _P]),
     "xtn_search_between": (_I, [_P, _P, _I64, _I, _P, _I64, _I, _P, _I64, _P, _P]),
+    "xtn_search_self_streaming": (_I, [_P, _P, _I64, _I, _P, _I64, _I, _I, _I64, _P, _I64, _P,
+                                       _P, _P]),
     "xtn_index_build": (_I, [_P, _P, _I64, _I, _P, _P]),
     "xtn_index_free": (_I, [_P]),
     "xtn_index_info": (_I, [_P, _P, _P, _P, _P]),

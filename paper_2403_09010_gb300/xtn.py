@@ -119,6 +119,34 @@ def search_between(seqs, offsets, d: int, rep_offsets, cap: int | None = None,
     return _call_with_rows(fn, cap, seqs, "xtn_search_between")
 
 
+def search_self_streaming(seqs, offsets, d: int, rep_offsets=None, metric: str = "levenshtein",
+                          between: bool = False, max_pass_records: int = 0,
+                          cap: int | None = None):
+    """The self-search in passes over fingerprint bins (xtn_search_self_streaming).
+    Returns (rows, passes run)."""
+    if metric not in _METRICS:
+        raise ValueError(f"unknown metric {metric!r}")
+    if between and rep_offsets is None:
+        raise ValueError("between needs rep_offsets")
+    n = _n_items(offsets)
+    sp, sk, _ = _ptr(seqs, np.uint8)
+    op, ok, _ = _ptr(offsets, np.int64)
+    rp, rk, _ = _ptr(rep_offsets, np.int64)
+    n_rep = 0 if rep_offsets is None else int(rep_offsets.shape[0]) - 1
+    stream = _stream(seqs)
+    if cap is None:
+        cap = 4 * n + 4096
+    passes = ctypes.c_int64(0)
+
+    def fn(optr, c, nref):
+        return native.lib().xtn_search_self_streaming(
+            sp, op, n, int(d), rp, n_rep, _METRICS[metric], int(bool(between)),
+            int(max_pass_records), optr, c, nref, ctypes.byref(passes), stream)
+
+    rows = _call_with_rows(fn, cap, seqs, "xtn_search_self_streaming")
+    return rows, int(passes.value)
+
+
 class Index:
     """Device-resident deletion-variant index of a reference set."""
 

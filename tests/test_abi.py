@@ -77,6 +77,10 @@ def test_argument_checks_before_device_work(lib):
     assert lib.xtn_search_between(seq, off, 1, 1, None, 0, 0, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_search_between(seq, off, 1, 1, rep, 1, 2, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_search_between(seq, off, 0, 1, rep, 1, 1, None, 0, ctypes.byref(n_out), None) == native.XTN_OK
+    # search in passes: metric 0 or 1, between needs repertoires
+    assert lib.xtn_search_self_streaming(seq, off, 1, 1, None, 0, 2, 0, 0, None, 0, ctypes.byref(n_out), None, None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_self_streaming(seq, off, 1, 1, None, 0, 0, 1, 0, None, 0, ctypes.byref(n_out), None, None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_self_streaming(seq, off, 0, 1, None, 0, 0, 0, 0, None, 0, ctypes.byref(n_out), None, None) == native.XTN_OK
 
 
 def test_tuning_knobs(lib):

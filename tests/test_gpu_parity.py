@@ -609,3 +609,92 @@ def test_selfsearch_n1e6_d2_sampled(xtn):
         ca = np.bincount(np.frombuffer(sa, np.uint8), minlength=128)
         cb = np.bincount(np.frombuffer(sb, np.uint8), minlength=128)
         assert np.linalg.norm(ca - cb) <= np.sqrt(2) * dd + 1e-9
+
+
+# ------------------------------------------------------ search in passes ---
+def _variant_records(off, d):
+    # deletion subsets of <= d positions (canonical ones are fewer): budgets
+    # below are fractions of this, and each test checks the passes it ran
+    L = np.diff(off).astype(np.int64)
+    return int((1 + L + (L * (L - 1) // 2 if d >= 2 else 0)).sum())
+
+
+@pytest.mark.parametrize("d,metric", [(1, "levenshtein"), (2, "levenshtein"), (2, "hamming")])
+def test_streaming_matches_oracle(xtn, d, metric):
+    seqs, off = gen.workload(gen.SELF_1M, 20_000)
+    want = oracle.symdel_self(seqs, off, d, metric)
+    budget = _variant_records(off, d) // 12
+    rows, passes = xtn.search_self_streaming(seqs, off, d, metric=metric, max_pass_records=budget)
+    assert passes >= 4
+    assert np.array_equal(_rows(rows), want)
+
+
+def test_streaming_batched_and_between(xtn):
+    n = 20_000
+    seqs, off = gen.workload(gen.SELF_1M, n)
+    cuts = np.sort(np.random.default_rng(45).choice(np.arange(1, n), 5, replace=False))
+    rep = np.concatenate([[0], cuts, [n]]).astype(np.int64)
+    budget = _variant_records(off, 2) // 10
+    rows, passes = xtn.search_self_streaming(seqs, off, 2, rep_offsets=rep, between=True,
+                                             max_pass_records=budget)
+    assert passes >= 4
+    assert np.array_equal(_rows(rows), oracle.symdel_cross(seqs, off, rep, 2))
+    rows, _ = xtn.search_self_streaming(seqs, off, 2, rep_offsets=rep, max_pass_records=budget)
+    got = _rows(rows)
+    want = oracle.symdel_batched(seqs, off, rep, 2)
+    rep_of = np.searchsorted(rep, got[:, 0], side="right") - 1
+    local = np.stack([rep_of, got[:, 0] - rep[rep_of], got[:, 1] - rep[rep_of], got[:, 2]], 1)
+    assert np.array_equal(local.astype(np.uint32), want)
+
+
+def test_streaming_d3_and_small_alphabet(xtn):
+    seqs, off = gen.workload(gen.SELF_1M, 3_000)
+    rows, passes = xtn.search_self_streaming(seqs, off, 3, max_pass_records=200_000)
+    assert passes >= 4
+    assert np.array_equal(_rows(rows), oracle.symdel_self(seqs, off, 3))
+    # two letters: buckets far larger than shared memory, repeated residues,
+    # one bin per pass at the smallest budget
+    strs = _rand_strings(np.random.default_rng(71), 3000, "AC", 0, 10)
+    s2, o2 = gen.from_strings(strs)
+    want = oracle.bruteforce_self(s2, o2, 2)
+    for budget in (1, 2_000, 10_000):
+        rows, passes = xtn.search_self_streaming(s2, o2, 2, max_pass_records=budget)
+        assert passes >= 2
+        assert np.array_equal(_rows(rows), want)
+
+
+def test_streaming_1m_equals_one_pass(xtn):
+    seqs, off = gen.workload(gen.SELF_1M)
+    ds, do = _dev(seqs, off)
+    whole = _rows(xtn.search_self(ds, do, 2))
+    rows, passes = xtn.search_self_streaming(ds, do, 2, max_pass_records=30_000_000)
+    assert passes >= 4
+    assert np.array_equal(_rows(rows), whole)
+    rows, passes = xtn.search_self_streaming(ds, do, 2)
+    assert passes == 1 and np.array_equal(_rows(rows), whole)
+
+
+def test_search_beyond_2_32_records(xtn):
+    # 9M sequences at d <= 3 give about 5e9 variant records: the self-search
+    # takes them in passes.  Rows among the first 1M sequences must be those
+    # of the one-pass search of that prefix; sampled rows are checked
+    # against the edit distance.
+    n = 9_000_000
+    seqs, off = gen.generate(n, 17, 0.15, 0.01)
+    ds, do = _dev(seqs, off)
+    rows, passes = xtn.search_self_streaming(ds, do, 3)
+    assert passes >= 2
+    got = _rows(rows)
+    auto = _rows(xtn.search_self(ds, do, 3))
+    assert np.array_equal(auto, got)
+    m = 1_000_000
+    prefix = _rows(xtn.search_self(ds[: int(off[m])], do[: m + 1], 3))
+    inside = got[got[:, 1] < m]
+    assert np.array_equal(inside, prefix)
+    assert np.all(got[:, 0] < got[:, 1]) and np.all(got[:, 2] <= 3)
+    key = got[:, 0].astype(np.uint64) << np.uint64(32) | got[:, 1].astype(np.uint64)
+    assert np.all(np.diff(key.astype(np.int64)) > 0)
+    strs_at = lambda i: bytes(seqs[off[i]:off[i + 1]]).decode()
+    rng = np.random.default_rng(6)
+    for r in got[rng.choice(got.shape[0], 300, replace=False)]:
+        assert oracle.levenshtein(strs_at(r[0]), strs_at(r[1])) == r[2]
