@@ -408,6 +408,34 @@ def run_between(reps: int = 10, n_rep: int = 8):
     return out
 
 
+def run_streaming(reps: int = 3):
+    """Searches in passes over fingerprint bins: the 1M d<=2 search forced into
+    four passes (against its one-pass time), and 9M sequences at d<=3 (about
+    5e9 variant records, past what one pass indexes) with the default budget."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    cur = torch.cuda.current_stream()
+    seqs, off = gen.workload(WORKLOAD)
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    out = {}
+    rows, passes = xtn.search_self_streaming(ds, do, 2, max_pass_records=30_000_000)
+    ms = _events_ms(lambda: xtn.search_self_streaming(ds, do, 2, max_pass_records=30_000_000),
+                    reps, cur)
+    out["n1e6_d2_4passes"] = {"passes": passes, "pairs": int(rows.shape[0]), "search_ms": ms}
+    n = 9_000_000
+    seqs, off = gen.generate(n, 17, 0.15, 0.01)
+    ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+    L = np.diff(off).astype(np.int64)
+    subsets = int((1 + L + L * (L - 1) // 2 + L * (L - 1) * (L - 2) // 6).sum())
+    rows, passes = xtn.search_self_streaming(ds, do, 3)
+    ms = _events_ms(lambda: xtn.search_self_streaming(ds, do, 3), reps, cur)
+    out["n9e6_d3"] = {"passes": passes, "deletion_subsets": subsets, "pairs": int(rows.shape[0]),
+                      "search_ms": ms, "pairs_per_s": rows.shape[0] / (ms / 1e3)}
+    del ds, do
+    xtn.scratch_trim()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,8 +444,8 @@ def main():
     ap.add_argument("--impl", default="xtn", choices=["xtn", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched / served / TCRdist / Hamming / overlap side "
-                         "measurements")
+                    help="skip the batched / served / TCRdist / Hamming / overlap / "
+                         "streaming side measurements")
     ap.add_argument("--n", type=int, default=None,
                     help="use only the first n sequences (small cases for profiling)")
     args = ap.parse_args()
@@ -559,6 +587,7 @@ def main():
         line["tcrdist_retention"] = run_retention()
         line["d3"] = run_d3()
         line["between"] = run_between()
+        line["streaming"] = run_streaming()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
