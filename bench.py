@@ -204,6 +204,23 @@ def cpu_baseline():
                       f"{rows.shape[0]:,} pairs"}
 
 
+def cpu_all_cores():
+    """The oracle with its variant keys split over every host core, on the same
+    sample as cpu_baseline (context beside the single-thread figure)."""
+    import oracle
+    oracle.build()
+    seqs, off = gen.workload(WORKLOAD, CPU_SAMPLE_N)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    rows = oracle.symdel_self_sharded(seqs, off, WORKLOAD.d, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": rows.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle, keys "
+            "partitioned by hash over threads",
+            "sample": f"first {CPU_SAMPLE_N:,} sequences of the {WORKLOAD.n:,}-sequence "
+                      f"d={WORKLOAD.d} workload, {cores} threads, {dt:.1f} s, "
+                      f"{rows.shape[0]:,} pairs"}
+
+
 def _events_ms(fn, reps, stream):
     import torch
     times = []
@@ -590,6 +607,7 @@ def main():
         line["streaming"] = run_streaming()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_all_cores"] = cpu_all_cores()
     print(json.dumps(line))
     return 0
 

@@ -11,6 +11,7 @@ ctypes. Every function returns numpy arrays of uint32 rows:
 * ``symdel_self``      (i, j, dist), i < j          -- Appendix, SymDel steps 0-4
 * ``symdel_batched``   (rep, i, j, dist)            -- the same per repertoire
 * ``symdel_cross``     (i, j, dist)                 -- pairs between repertoires
+* ``symdel_self_sharded`` (i, j, dist)              -- symdel_self on several threads
 * ``symdel_query``     (q, r, dist)                 -- steps 1-2 on the reference,
                                                        step 3 with the queries
 * ``bruteforce_self`` / ``bruteforce_query``        -- exhaustive search (pin)
@@ -45,8 +46,8 @@ def build(force: bool = False) -> str:
              or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp],
-                       check=True)
+        subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", _SRC, "-o",
+                        tmp], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,6 +62,9 @@ def _load():
         getattr(lib, name).restype = _P
     lib.xo_bruteforce_self_metric.argtypes = [_P, _P, _I64, ctypes.c_int, ctypes.c_int]
     lib.xo_bruteforce_self_metric.restype = _P
+    lib.xo_symdel_self_sharded.argtypes = [_P, _P, _I64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int]
+    lib.xo_symdel_self_sharded.restype = _P
     lib.xo_symdel_batched.argtypes = [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
     lib.xo_symdel_batched.restype = _P
     lib.xo_symdel_cross.argtypes = [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
@@ -132,6 +136,15 @@ def symdel_batched(seqs, offsets, rep_offsets, d: int, metric: str = "levenshtei
     r = np.ascontiguousarray(rep_offsets, dtype=np.int64)
     return _take(_load().xo_symdel_batched(_ptr(s), _ptr(o), _ptr(r), r.size - 1, d,
                                            _METRICS[metric]))
+
+
+def symdel_self_sharded(seqs, offsets, d: int, metric: str = "levenshtein",
+                        threads: int = 0) -> np.ndarray:
+    """symdel_self with the variant keys partitioned over threads (0: all of
+    the host's hardware threads); the same rows."""
+    s, o = _prep(seqs, offsets)
+    return _take(_load().xo_symdel_self_sharded(_ptr(s), _ptr(o), o.size - 1, d,
+                                                _METRICS[metric], int(threads)))
 
 
 def symdel_cross(seqs, offsets, rep_offsets, d: int, metric: str = "levenshtein") -> np.ndarray:

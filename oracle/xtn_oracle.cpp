@@ -33,6 +33,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -149,6 +150,57 @@ std::vector<std::vector<uint32_t>> symdel_self_range(const uint8_t* seqs, const 
   return rows;
 }
 
+// The same self-search with the variant keys partitioned over T threads by
+// a hash of the key: thread t keeps the map of the keys of its part, pairs
+// up the ids of every key it holds, and verifies those candidates; the rows
+// of all threads are merged and deduplicated.  Only the bookkeeping differs
+// from symdel_self_range (equal variants always fall in one part), so the
+// rows are the same.  It exists to time the oracle on every host core.
+std::vector<std::vector<uint32_t>> symdel_self_sharded(const uint8_t* seqs, const int64_t* off,
+                                                       int64_t n, int d, int metric, int T) {
+  if (T < 1) T = 1;
+  std::vector<std::string> s(n);
+  for (int64_t i = 0; i < n; ++i) s[i] = seq_at(seqs, off, i);
+  // step 1, every sequence's variants, split over the threads by sequence
+  std::vector<std::vector<std::string>> x(n);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < T; ++t)
+    pool.emplace_back([&, t] {
+      for (int64_t i = t; i < n; i += T) {
+        auto v = deletion_variants(s[i], d);
+        x[i].assign(v.begin(), v.end());
+      }
+    });
+  for (auto& th : pool) th.join();
+  pool.clear();
+  // steps 2-4 per part of the key space
+  std::vector<std::vector<std::vector<uint32_t>>> part(T);
+  for (int t = 0; t < T; ++t)
+    pool.emplace_back([&, t] {
+      std::hash<std::string> h;
+      std::unordered_map<std::string, std::vector<uint32_t>> table;
+      for (int64_t i = 0; i < n; ++i)
+        for (const std::string& v : x[i])
+          if ((int)(h(v) % (size_t)T) == t) table[v].push_back(static_cast<uint32_t>(i));
+      std::vector<std::pair<uint32_t, uint32_t>> y;
+      for (auto& kv : table)
+        for (size_t a = 0; a < kv.second.size(); ++a)
+          for (size_t b = a + 1; b < kv.second.size(); ++b)
+            y.emplace_back(kv.second[a], kv.second[b]);  // ids ascend within a key
+      std::sort(y.begin(), y.end());
+      y.erase(std::unique(y.begin(), y.end()), y.end());
+      for (auto& c : y) {
+        const int dist = distance(s[c.first], s[c.second], metric);
+        if (dist <= d) part[t].push_back({c.first, c.second, static_cast<uint32_t>(dist)});
+      }
+    });
+  for (auto& th : pool) th.join();
+  std::vector<std::vector<uint32_t>> rows;
+  for (auto& p : part) rows.insert(rows.end(), p.begin(), p.end());
+  sort_unique(rows);
+  return rows;
+}
+
 // ---- BLOSUM62 (Henikoff & Henikoff 1992), rows/cols in the order below. ----
 const char kB62Order[] = "ARNDCQEGHILKMFPSTWYV";
 const int kB62[20][20] = {
@@ -245,6 +297,15 @@ int xo_tcrdist(const uint8_t* a, int la, const uint8_t* b, int lb) {
 // SymDel self-search: rows (i, j, dist), i < j, sorted.
 void* xo_symdel_self(const uint8_t* seqs, const int64_t* off, int64_t n, int d) {
   auto rows = symdel_self_range(seqs, off, 0, n, d);
+  return pack(rows, 3);
+}
+
+// The self-search with its keys partitioned over `threads` threads (0: the
+// host's hardware threads).  metric: 0 = Levenshtein, 1 = Hamming.
+void* xo_symdel_self_sharded(const uint8_t* seqs, const int64_t* off, int64_t n, int d,
+                             int metric, int threads) {
+  if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
+  auto rows = symdel_self_sharded(seqs, off, n, d, metric, threads);
   return pack(rows, 3);
 }
 

@@ -375,3 +375,19 @@ def test_cross_and_within_partition_the_whole_search(metric):
     r_of = lambda i: np.searchsorted(rep, i, side="right") - 1
     assert np.all(r_of(cross[:, 0]) != r_of(cross[:, 1]))
     assert cross.shape[0] >= 10 and within.shape[0] >= 10
+
+
+# ------------------------------------------------------ sharded oracle ---
+@pytest.mark.parametrize("metric", ["levenshtein", "hamming"])
+def test_sharded_search_is_the_brute_force(metric):
+    # keys split over threads: any thread count gives the brute-force rows
+    rng = np.random.default_rng(90)
+    strs = ["".join(rng.choice(list("ACD"), size=k)) for k in rng.integers(0, 9, 400)]
+    seqs, off = gen.from_strings(strs)
+    want = oracle.bruteforce_self(seqs, off, 2, metric)
+    assert want.shape[0] > 100
+    for threads in (1, 2, 3, 7):
+        assert np.array_equal(oracle.symdel_self_sharded(seqs, off, 2, metric, threads), want)
+    seqs, off = gen.workload(gen.SELF_1M, 2_000)
+    assert np.array_equal(oracle.symdel_self_sharded(seqs, off, 2, metric, 4),
+                          oracle.bruteforce_self(seqs, off, 2, metric))
