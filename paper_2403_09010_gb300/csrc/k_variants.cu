@@ -122,20 +122,51 @@ __device__ __forceinline__ void count_digits(uint32_t* s_hist, uint64_t rec, int
   }
 }
 
+static_assert((1 << MAX_BIN_BITS) <= MAX_PASSES * RADIX, "bins share the digit histogram");
+
+// Appended records (SEL_APPEND) collect per warp in shared memory and go out
+// STAGE_FLUSH or more at a time: a warp reserves output space once per
+// batch, not once per round (rounds keep a record in nearly every warp
+// whatever the share of bins selected, and every reservation is an atomic
+// on one counter), and the stores are contiguous runs.
+constexpr uint32_t STAGE_FLUSH = 128;
+constexpr uint32_t STAGE_CAP = STAGE_FLUSH + 32;
+struct WarpStage {
+  uint64_t* buf;  // STAGE_CAP words of this warp
+  uint32_t n;     // staged records (the same in every lane)
+};
+
+__device__ __forceinline__ void flush_stage(WarpStage& st, uint64_t* __restrict__ out,
+                                            uint64_t n_rec, const BinSel& sel, uint32_t lane,
+                                            uint32_t* __restrict__ err) {
+  if (st.n == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(sel.append, (unsigned long long)st.n);
+  base = __shfl_sync(FULL_MASK, base, 0);
+  __syncwarp();  // every lane's staged records are visible
+  for (uint32_t k = lane; k < st.n; k += 32) {
+    const uint64_t slot = base + k;
+    if (slot < n_rec)
+      out[slot] = st.buf[k];
+    else
+      atomicOr(err, DERR_RANGE);
+  }
+  __syncwarp();  // read before the stage fills again
+  st.n = 0;
+}
+
 // Where a finished record goes (all lanes of the warp call this together;
 // `valid` says whether this lane holds a record):
 //   SEL_ALL    out[pos], its digits counted for the sort
 //   SEL_COUNT  only its fingerprint bin counted (s_hist holds the bins)
-//   SEL_APPEND appended to out when its bin lies in [sel.lo, sel.hi), one
-//              atomic per warp; its digits counted
-static_assert((1 << MAX_BIN_BITS) <= MAX_PASSES * RADIX, "bins share the digit histogram");
-
+//   SEL_APPEND staged for appending when its bin lies in [sel.lo, sel.hi);
+//              its digits counted
 template <int SEL>
 __device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t pos,
                                              uint64_t* __restrict__ out, uint64_t n_rec,
                                              uint32_t* s_hist, int hist_lo, int hist_passes,
                                              uint32_t last_mask, const BinSel& sel, uint32_t lane,
-                                             uint32_t* __restrict__ err) {
+                                             WarpStage& st, uint32_t* __restrict__ err) {
   if constexpr (SEL == SEL_ALL) {
     if (valid) {
       out[pos] = rec;
@@ -148,20 +179,12 @@ __device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t 
     } else {
       const bool keep = valid && bin >= sel.lo && bin < sel.hi;
       const uint32_t bal = __ballot_sync(FULL_MASK, keep);
-      if (!bal) return;
-      const uint32_t leader = (uint32_t)(__ffs(bal) - 1);
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(sel.append, (unsigned long long)__popc(bal));
-      base = __shfl_sync(FULL_MASK, base, leader);
       if (keep) {
-        const uint64_t slot = base + __popc(bal & ((1u << lane) - 1u));
-        if (slot < n_rec) {
-          out[slot] = rec;
-          count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
-        } else {
-          atomicOr(err, DERR_RANGE);
-        }
+        st.buf[st.n + __popc(bal & ((1u << lane) - 1u))] = rec;  // st.n + 32 <= STAGE_CAP
+        count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
       }
+      st.n += __popc(bal);
+      if (st.n >= STAGE_FLUSH) flush_stage(st, out, n_rec, sel, lane, err);
     }
   }
 }
@@ -176,6 +199,9 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   __shared__ VariantTables s_tab;
   __shared__ WarpVariants s_warp[EXPAND_THREADS / 32];
+  constexpr int STAGE_WARPS = SEL == SEL_APPEND ? EXPAND_THREADS / 32 : 1;
+  __shared__ uint64_t s_stage[STAGE_WARPS][SEL == SEL_APPEND ? STAGE_CAP : 1];
+  WarpStage st{s_stage[SEL == SEL_APPEND ? threadIdx.x >> 5 : 0], 0u};
   const int n_hist = SEL == SEL_COUNT ? (int)sel.mask + 1 : hist_passes * RADIX;
   for (int k = threadIdx.x; k < n_hist; k += blockDim.x) s_hist[k] = 0;
   init_variant_tables(&s_tab);
@@ -229,7 +255,7 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
           if (v < total)
             rec = (canonical_fingerprint_d2(w, &s_tab, sh, v, salt) & ~idmask) | (uint64_t)s;
           place_record<SEL>(rec, v < total, base + v, out, n_rec, s_hist, hist_lo, hist_passes,
-                            last_mask, sel, lane, err);
+                            last_mask, sel, lane, st, err);
         }
       } else {
         // every subset with <= d deletions, canonical ones kept (ballot compaction)
@@ -249,13 +275,14 @@ __global__ void __launch_bounds__(EXPAND_THREADS)
           uint64_t rec = 0;
           if (ok) rec = (subset_fingerprint(w, L, ss, salt) & ~idmask) | (uint64_t)s;
           place_record<SEL>(rec, ok, base + slot, out, n_rec, s_hist, hist_lo, hist_passes,
-                            last_mask, sel, lane, err);
+                            last_mask, sel, lane, st, err);
           written += __popc(bal);
         }
         if (written != cnt && lane == 0) atomicOr(err, DERR_RANGE);
       }
     }
   }
+  if constexpr (SEL == SEL_APPEND) flush_stage(st, out, n_rec, sel, lane, err);
   __syncthreads();
   uint32_t* dst = SEL == SEL_COUNT ? sel.bin_count : hist;
   for (int k = threadIdx.x; k < n_hist; k += blockDim.x)
@@ -295,6 +322,9 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   __shared__ VariantTables s_tab;
   __shared__ PackedSeqs s_seq[PACK_WARPS];
+  constexpr int STAGE_WARPS = SEL == SEL_APPEND ? PACK_WARPS : 1;
+  __shared__ uint64_t s_stage[STAGE_WARPS][SEL == SEL_APPEND ? STAGE_CAP : 1];
+  WarpStage st{s_stage[SEL == SEL_APPEND ? threadIdx.x >> 5 : 0], 0u};
   const int n_hist = SEL == SEL_COUNT ? (int)sel.mask + 1 : hist_passes * RADIX;
   for (int k = threadIdx.x; k < n_hist; k += blockDim.x) s_hist[k] = 0;
   init_variant_tables(&s_tab);
@@ -396,10 +426,11 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
         rec = (mix64(h ^ saltj) & ~idmask) | (uint64_t)(s0 + j);
       }
       place_record<SEL>(rec, t < T, base0 + t, out, n_rec, s_hist, hist_lo, hist_passes,
-                        last_mask, sel, lane, err);
+                        last_mask, sel, lane, st, err);
     }
     __syncwarp();  // the next batch overwrites the tables
   }
+  if constexpr (SEL == SEL_APPEND) flush_stage(st, out, n_rec, sel, lane, err);
   __syncthreads();
   uint32_t* dst = SEL == SEL_COUNT ? sel.bin_count : hist;
   for (int k = threadIdx.x; k < n_hist; k += blockDim.x)
