@@ -872,7 +872,7 @@ int search_stream_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, i
       XTN_CK(cudaMemcpyAsync(&h.direct, ctr + 2, 32, cudaMemcpyDeviceToHost, s));
       XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
       XTN_CK(host_sync(s));
-      if (mode != 1 && (h.err & DERR_CAPACITY)) {
+      if (mode != 1 && h.err == DERR_CAPACITY) {  // direct candidates overflowed, nothing else
         XTN_CK(cudaMemsetAsync(err, 0, 4, s));
         mode = 1;
         continue;
