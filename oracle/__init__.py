@@ -23,6 +23,7 @@ ctypes. Every function returns numpy arrays of uint32 rows:
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -56,7 +57,25 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    _lib = _configure(ctypes.CDLL(build()))
+    return _lib
+
+
+@contextlib.contextmanager
+def built_from(path: str):
+    """Within the block, every function of this module calls the library at
+    `path`, a build of a copy of xtn_oracle.cpp (tests plant mistakes in such
+    copies to check that the pins catch them)."""
+    global _lib
+    saved = _load()
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _configure(lib):
     for name in ("xo_symdel_self", "xo_symdel_self_hamming", "xo_bruteforce_self"):
         getattr(lib, name).argtypes = [_P, _P, _I64, ctypes.c_int]
         getattr(lib, name).restype = _P
@@ -94,7 +113,6 @@ def _load():
     lib.xo_count_variants.restype = _I64
     lib.xo_blosum62.argtypes = [ctypes.c_char, ctypes.c_char]
     lib.xo_blosum62.restype = ctypes.c_int
-    _lib = lib
     return lib
 
 

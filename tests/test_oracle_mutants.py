@@ -1,0 +1,167 @@
+"""Planted mistakes in the oracle: each plausible slip in its arithmetic must
+fail one of the pin checks below.
+
+Every mutant is a copy of oracle/xtn_oracle.cpp with one edit, built on the
+CPU into a temporary library that the oracle module is pointed at.  The
+checks restate the pins of test_oracle_pins.py in a compact form: textbook
+edit distances, the worked variant count of Sec. 2.1, the search against
+exhaustive comparison, the special case d = 0, Hamming textbook values and
+lengths, the hand-worked TCRdist scores of tests/golden/tcrdist_hand.txt and
+the within/between partition of the batched search.  The unmutated source
+passes every check.
+"""
+import concurrent.futures
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import cdr3_synth as gen
+import oracle
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "xtn_oracle.cpp")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "tcrdist_hand.txt")
+
+# (what the slip is, text in the source, replacement); every text occurs once
+MUTANTS = [
+    ("equal letters cost a substitution", "(a[x - 1] == b[y - 1] ? 0 : 1)", "1"),
+    ("insertions are free", "int ins = D[x * w + (y - 1)] + 1;", "int ins = D[x * w + (y - 1)] + 0;"),
+    ("first DP column left at zero", "for (size_t x = 0; x <= la; ++x) D[x * w] = static_cast<int>(x);",
+     "for (size_t x = 0; x <= la; ++x) D[x * w] = 0;"),
+    ("one deletion fewer", "for (int k = 1; k <= d; ++k) {\n    std::unordered_set<std::string> next;",
+     "for (int k = 1; k < d; ++k) {\n    std::unordered_set<std::string> next;"),
+    ("the string itself is not a variant", "std::unordered_set<std::string> all{s};",
+     "std::unordered_set<std::string> all;"),
+    ("only the first residue is ever deleted", "std::string u = t.substr(0, p) + t.substr(p + 1);",
+     "std::string u = t.substr(1);"),
+    ("a sequence paired with itself", "    if (c.first >= c.second) continue;",
+     "    if (c.first > c.second) continue;"),
+    ("the threshold is strict",
+     "    if (dist <= d) rows.push_back({c.first, c.second, static_cast<uint32_t>(dist)});",
+     "    if (dist < d) rows.push_back({c.first, c.second, static_cast<uint32_t>(dist)});"),
+    ("Hamming counts agreeing positions", "h += a[p] != b[p];", "h += a[p] == b[p];"),
+    ("Hamming compares unequal lengths by their difference",
+     "if (a.size() != b.size()) return NOT_NEIGHBOURS;",
+     "if (a.size() != b.size()) return (int)(a.size() > b.size() ? a.size() - b.size() : b.size() - a.size());"),
+    ("TCRdist gap costs 3", "sum += 4 * static_cast<int>(g);", "sum += 3 * static_cast<int>(g);"),
+    ("TCRdist weight 2", "return 3 * sum;", "return 2 * sum;"),
+    ("TCRdist gaps one position later", "const size_t p = m / 2;", "const size_t p = (m + 1) / 2;"),
+    ("TCRdist mismatch cost uncapped", "sum += std::min(4, 4 - blosum62(x, y));",
+     "sum += 4 - blosum62(x, y);"),
+    ("pairs within a repertoire reported as between",
+     "if (rep_of(row[0]) != rep_of(row[1])) keep.push_back(row);",
+     "if (rep_of(row[0]) == rep_of(row[1])) keep.push_back(row);"),
+]
+
+
+# ------------------------------------------------------------- the checks ---
+def check_textbook_distances():
+    for a, b, want in [("kitten", "sitting", 3), ("flaw", "lawn", 2), ("", "CAS", 3),
+                       ("CAS", "", 3), ("intention", "execution", 5), ("CASSF", "CASSF", 0)]:
+        assert oracle.levenshtein(a, b) == want
+
+
+def check_worked_variant_count():
+    # Sec. 2.1: 56 variants with up to two deletions of a length-10 string
+    # of distinct residues; 11 with up to one
+    assert oracle.count_variants("ACDEFGHIKL", 2) == 56
+    assert oracle.count_variants("ACDEFGHIKL", 1) == 11
+
+
+def _small_sets():
+    rng = np.random.default_rng(5)
+    strs = ["".join(rng.choice(list("AC"), size=k)) for k in rng.integers(0, 8, 150)]
+    yield gen.from_strings(strs)
+    yield gen.workload(gen.SELF_1M, 800)
+
+
+def check_search_equals_exhaustive():
+    for seqs, off in _small_sets():
+        for d in (1, 2):
+            want = oracle.bruteforce_self(seqs, off, d)
+            assert want.shape[0] > 0
+            assert np.array_equal(oracle.symdel_self(seqs, off, d), want)
+
+
+def check_d0_is_duplicate_grouping():
+    strs = ["CASSF", "CASSF", "CAS", "", "", "CASSF", "CAT"]
+    seqs, off = gen.from_strings(strs)
+    want = [[i, j, 0] for i in range(len(strs)) for j in range(i + 1, len(strs))
+            if strs[i] == strs[j]]
+    assert oracle.symdel_self(seqs, off, 0).tolist() == want
+
+
+def check_hamming():
+    assert oracle.hamming("KAROLIN", "KATHRIN") == 3
+    assert oracle.hamming("CASSF", "CASSF") == 0
+    seqs, off = gen.from_strings(["CAS", "CASS", "CAT", "CA"])
+    # only CAS-CAT has equal lengths
+    assert oracle.symdel_self(seqs, off, 2, "hamming").tolist() == [[0, 2, 1]]
+
+
+def check_tcrdist_hand_worked():
+    for line in open(GOLDEN):
+        line = line.split("#")[0].split()
+        if line:
+            assert oracle.tcrdist(line[0], line[1]) == int(line[2])
+
+
+def check_between_and_within_partition():
+    seqs, off = gen.workload(gen.SELF_1M, 1000)
+    rep = np.array([0, 300, 310, 700, 1000], dtype=np.int64)
+    whole = oracle.bruteforce_self(seqs, off, 2)
+    cross = oracle.symdel_cross(seqs, off, rep, 2)
+    within = oracle.symdel_batched(seqs, off, rep, 2)
+    glob = np.stack([within[:, 1] + rep[within[:, 0]], within[:, 2] + rep[within[:, 0]],
+                     within[:, 3]], 1).astype(np.uint32)
+    both = np.concatenate([cross, glob])
+    both = both[np.lexsort((both[:, 1], both[:, 0]))]
+    assert np.array_equal(both, whole)
+
+
+CHECKS = [check_textbook_distances, check_worked_variant_count, check_search_equals_exhaustive,
+          check_d0_is_duplicate_grouping, check_hamming, check_tcrdist_hand_worked,
+          check_between_and_within_partition]
+
+
+def _failing(path):
+    failed = []
+    with oracle.built_from(path):
+        for check in CHECKS:
+            try:
+                check()
+            except AssertionError:
+                failed.append(check.__name__)
+    return failed
+
+
+def _build(text, path):
+    with open(path + ".cpp", "w") as f:
+        f.write(text)
+    subprocess.run(["g++", "-O1", "-std=c++17", "-pthread", "-shared", "-fPIC", path + ".cpp",
+                    "-o", path], check=True)
+    return path
+
+
+@pytest.fixture(scope="module")
+def builds(tmp_path_factory):
+    src = open(SRC).read()
+    d = tmp_path_factory.mktemp("mutants")
+    jobs = {"original": src}
+    for k, (what, old, new) in enumerate(MUTANTS):
+        assert src.count(old) == 1, what
+        jobs[what] = src.replace(old, new)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as pool:
+        futs = {what: pool.submit(_build, text, str(d / f"m{k}.so"))
+                for k, (what, text) in enumerate(jobs.items())}
+        return {what: f.result() for what, f in futs.items()}
+
+
+def test_unmutated_source_passes_every_check(builds):
+    assert _failing(builds["original"]) == []
+
+
+@pytest.mark.parametrize("what", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(builds, what):
+    assert _failing(builds[what]), f"no pin catches: {what}"
