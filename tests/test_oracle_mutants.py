@@ -52,10 +52,43 @@ MUTANTS = [
     ("pairs within a repertoire reported as between",
      "if (rep_of(row[0]) != rep_of(row[1])) keep.push_back(row);",
      "if (rep_of(row[0]) == rep_of(row[1])) keep.push_back(row);"),
+    ("queries look up one deletion fewer", "for (const std::string& v : deletion_variants(s, d)) {",
+     "for (const std::string& v : deletion_variants(s, d > 0 ? d - 1 : 0)) {"),
+    ("query threshold strict",
+     "if (dist <= d) rows.push_back({static_cast<uint32_t>(q), r, static_cast<uint32_t>(dist)});",
+     "if (dist < d) rows.push_back({static_cast<uint32_t>(q), r, static_cast<uint32_t>(dist)});"),
+    ("batched rows keep global indices",
+     "all.push_back({static_cast<uint32_t>(r), row[0], row[1], row[2]});",
+     "all.push_back({static_cast<uint32_t>(r), row[0] + (uint32_t)rep_off[r], "
+     "row[1] + (uint32_t)rep_off[r], row[2]});"),
+    ("exhaustive search pairs a sequence with itself",
+     "for (int64_t j = i + 1; j < n; ++j) {\n      int dist = distance(s[i], s[j], metric);",
+     "for (int64_t j = i; j < n; ++j) {\n      int dist = distance(s[i], s[j], metric);"),
+    ("exhaustive query threshold strict",
+     "      if (dist <= d)\n        rows.push_back({static_cast<uint32_t>(q), static_cast<uint32_t>(r),",
+     "      if (dist < d)\n        rows.push_back({static_cast<uint32_t>(q), static_cast<uint32_t>(r),"),
+    ("one sequence's neighbours include itself", "    if (j == i) continue;\n", ""),
+    ("TCRdist filter threshold strict",
+     "seq_at(seqs, off, j)) <= max_score)", "seq_at(seqs, off, j)) < max_score)"),
+    ("all-pairs scorer threshold strict", "if (score > max_score) continue;",
+     "if (score >= max_score) continue;"),
+    ("sharded search pairs an id with itself",
+     "for (size_t b = a + 1; b < kv.second.size(); ++b)",
+     "for (size_t b = a; b < kv.second.size(); ++b)"),
 ]
 
 
 # ------------------------------------------------------------- the checks ---
+_PREFIX = {}
+
+
+def _prefix(n):
+    """The first n <= 1500 sequences of the 1M workload (generated once)."""
+    if not _PREFIX:
+        _PREFIX["all"] = gen.workload(gen.SELF_1M, 1500)
+    seqs, off = _PREFIX["all"]
+    return seqs[: off[n]], off[: n + 1]
+
 def check_textbook_distances():
     for a, b, want in [("kitten", "sitting", 3), ("flaw", "lawn", 2), ("", "CAS", 3),
                        ("CAS", "", 3), ("intention", "execution", 5), ("CASSF", "CASSF", 0)]:
@@ -73,7 +106,7 @@ def _small_sets():
     rng = np.random.default_rng(5)
     strs = ["".join(rng.choice(list("AC"), size=k)) for k in rng.integers(0, 8, 150)]
     yield gen.from_strings(strs)
-    yield gen.workload(gen.SELF_1M, 800)
+    yield _prefix(800)
 
 
 def check_search_equals_exhaustive():
@@ -108,7 +141,7 @@ def check_tcrdist_hand_worked():
 
 
 def check_between_and_within_partition():
-    seqs, off = gen.workload(gen.SELF_1M, 1000)
+    seqs, off = _prefix(1000)
     rep = np.array([0, 300, 310, 700, 1000], dtype=np.int64)
     whole = oracle.bruteforce_self(seqs, off, 2)
     cross = oracle.symdel_cross(seqs, off, rep, 2)
@@ -120,12 +153,61 @@ def check_between_and_within_partition():
     assert np.array_equal(both, whole)
 
 
-CHECKS = [check_textbook_distances, check_worked_variant_count, check_search_equals_exhaustive,
-          check_d0_is_duplicate_grouping, check_hamming, check_tcrdist_hand_worked,
+def check_query_equals_exhaustive():
+    rs, ro = _prefix(600)
+    strs = gen.to_strings(rs, ro)
+    qs, qo = gen.from_strings(strs[:40] + [s[1:] + "A" for s in strs[40:80]])
+    for d in (1, 2):
+        want = oracle.bruteforce_query(rs, ro, qs, qo, d)
+        assert want.shape[0] > 40
+        assert np.array_equal(oracle.symdel_query(rs, ro, qs, qo, d), want)
+
+
+def check_batched_is_per_repertoire():
+    seqs, off = _prefix(600)
+    rep = np.array([0, 250, 600], dtype=np.int64)
+    want = []
+    for r in range(2):
+        a, b = int(rep[r]), int(rep[r + 1])
+        for row in oracle.bruteforce_self(seqs[off[a]:off[b]], off[a:b + 1] - off[a], 2).tolist():
+            want.append([r] + row)
+    assert oracle.symdel_batched(seqs, off, rep, 2).tolist() == sorted(want)
+
+
+def check_neighbours_of_one_sequence():
+    seqs, off = _prefix(600)
+    rows = oracle.bruteforce_self(seqs, off, 2)
+    for i in (int(rows[0, 0]), int(rows[-1, 1])):
+        want = sorted([[int(r[1]) if r[0] == i else int(r[0]), int(r[2])]
+                       for r in rows if i in (r[0], r[1])])
+        assert oracle.neighbors_of(seqs, off, i, 2).tolist() == want
+
+
+def check_sharded_equals_exhaustive():
+    seqs, off = _prefix(600)
+    assert np.array_equal(oracle.symdel_self_sharded(seqs, off, 2, threads=3),
+                          oracle.bruteforce_self(seqs, off, 2))
+
+
+def check_tcrdist_filter_and_scorer():
+    seqs, off = _prefix(1500)
+    lev = oracle.bruteforce_self(seqs, off, 2)
+    kept = oracle.tcrdist_filter(seqs, off, lev, 24)
+    full = oracle.tcrdist_allpairs(seqs, off, 2, 24)
+    assert (full[:, 3] == 24).any()       # a score on the threshold itself
+    assert np.array_equal(kept, full[:, :3])
+
+
+# cheapest first: a mutant stops at its first failing check
+CHECKS = [check_textbook_distances, check_worked_variant_count, check_hamming,
+          check_tcrdist_hand_worked, check_d0_is_duplicate_grouping,
+          check_search_equals_exhaustive, check_query_equals_exhaustive,
+          check_batched_is_per_repertoire, check_neighbours_of_one_sequence,
+          check_sharded_equals_exhaustive, check_tcrdist_filter_and_scorer,
           check_between_and_within_partition]
 
 
-def _failing(path):
+def _failing(path, first_only):
     failed = []
     with oracle.built_from(path):
         for check in CHECKS:
@@ -133,6 +215,8 @@ def _failing(path):
                 check()
             except AssertionError:
                 failed.append(check.__name__)
+                if first_only:
+                    break
     return failed
 
 
@@ -159,9 +243,9 @@ def builds(tmp_path_factory):
 
 
 def test_unmutated_source_passes_every_check(builds):
-    assert _failing(builds["original"]) == []
+    assert _failing(builds["original"], first_only=False) == []
 
 
 @pytest.mark.parametrize("what", [m[0] for m in MUTANTS])
 def test_planted_mistake_fails_a_pin(builds, what):
-    assert _failing(builds[what]), f"no pin catches: {what}"
+    assert _failing(builds[what], first_only=True), f"no pin catches: {what}"
