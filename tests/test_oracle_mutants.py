@@ -4,11 +4,12 @@ fail one of the pin checks below.
 Every mutant is a copy of oracle/xtn_oracle.cpp with one edit, built on the
 CPU into a temporary library that the oracle module is pointed at.  The
 checks restate the pins of test_oracle_pins.py in a compact form: textbook
-edit distances, the worked variant count of Sec. 2.1, the search against
-exhaustive comparison, the special case d = 0, Hamming textbook values and
-lengths, the hand-worked TCRdist scores of tests/golden/tcrdist_hand.txt and
-the within/between partition of the batched search.  The unmutated source
-passes every check.
+edit distances, the worked variant count of Sec. 2.1, the special case
+d = 0, Hamming textbook values and lengths, the hand-worked TCRdist scores of
+tests/golden/tcrdist_hand.txt, the self, query, batched and sharded searches
+against exhaustive comparison, one sequence's neighbours, the TCRdist filter
+against the all-pairs scorer, and the within/between partition of the
+batched search.  The unmutated source passes every check.
 """
 import concurrent.futures
 import os
@@ -88,6 +89,7 @@ def _prefix(n):
         _PREFIX["all"] = gen.workload(gen.SELF_1M, 1500)
     seqs, off = _PREFIX["all"]
     return seqs[: off[n]], off[: n + 1]
+
 
 def check_textbook_distances():
     for a, b, want in [("kitten", "sitting", 3), ("flaw", "lawn", 2), ("", "CAS", 3),
