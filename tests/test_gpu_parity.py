@@ -663,6 +663,21 @@ def test_streaming_d3_and_small_alphabet(xtn):
         assert np.array_equal(_rows(rows), want)
 
 
+def test_streaming_edge_cases(xtn):
+    # empty input, one sequence, empty strings, maximum length, repeats, and
+    # d = 0, each at a budget of one record per pass (one bin per pass)
+    seqs, off = gen.from_strings([])
+    rows, passes = xtn.search_self_streaming(seqs, off, 2, max_pass_records=1)
+    assert rows.shape[0] == 0 and passes == 0
+    for strs, d in [(["CASSF"], 2), (["", "", "A"], 1), (["W" * 25, "W" * 24, "Y" * 25], 1),
+                    (["A" * 25, "A" * 24], 3), (["CASSF", "CASSF", "CAS", "", ""], 0),
+                    (["ACDEFGHIKLMNPQRSTVWYACDEF", "CDEFGHIKLMNPQRSTVWYACDEFA"], 2)]:
+        seqs, off = gen.from_strings(strs)
+        rows, passes = xtn.search_self_streaming(seqs, off, d, max_pass_records=1)
+        assert passes >= 1
+        assert np.array_equal(_rows(rows), oracle.bruteforce_self(seqs, off, d)), strs
+
+
 def test_streaming_1m_equals_one_pass(xtn):
     seqs, off = gen.workload(gen.SELF_1M)
     ds, do = _dev(seqs, off)
