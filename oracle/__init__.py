@@ -93,6 +93,9 @@ def _configure(lib):
     for name in ("xo_symdel_query", "xo_bruteforce_query"):
         getattr(lib, name).argtypes = [_P, _P, _I64, _P, _P, _I64, ctypes.c_int]
         getattr(lib, name).restype = _P
+    for name in ("xo_symdel_query_metric", "xo_bruteforce_query_metric"):
+        getattr(lib, name).argtypes = [_P, _P, _I64, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
+        getattr(lib, name).restype = _P
     lib.xo_neighbors_of.argtypes = [_P, _P, _I64, _I64, ctypes.c_int]
     lib.xo_neighbors_of.restype = _P
     lib.xo_tcrdist_filter.argtypes = [_P, _P, _P, _I64, ctypes.c_int]
@@ -173,11 +176,12 @@ def symdel_cross(seqs, offsets, rep_offsets, d: int, metric: str = "levenshtein"
                                          _METRICS[metric]))
 
 
-def symdel_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int) -> np.ndarray:
+def symdel_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int,
+                 metric: str = "levenshtein") -> np.ndarray:
     rs, ro = _prep(ref_seqs, ref_offsets)
     qs, qo = _prep(q_seqs, q_offsets)
-    return _take(_load().xo_symdel_query(_ptr(rs), _ptr(ro), ro.size - 1,
-                                         _ptr(qs), _ptr(qo), qo.size - 1, d))
+    return _take(_load().xo_symdel_query_metric(_ptr(rs), _ptr(ro), ro.size - 1, _ptr(qs),
+                                                _ptr(qo), qo.size - 1, d, _METRICS[metric]))
 
 
 def bruteforce_self(seqs, offsets, d: int, metric: str = "levenshtein") -> np.ndarray:
@@ -186,11 +190,13 @@ def bruteforce_self(seqs, offsets, d: int, metric: str = "levenshtein") -> np.nd
                                                    _METRICS[metric]))
 
 
-def bruteforce_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int) -> np.ndarray:
+def bruteforce_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int,
+                     metric: str = "levenshtein") -> np.ndarray:
     rs, ro = _prep(ref_seqs, ref_offsets)
     qs, qo = _prep(q_seqs, q_offsets)
-    return _take(_load().xo_bruteforce_query(_ptr(rs), _ptr(ro), ro.size - 1,
-                                             _ptr(qs), _ptr(qo), qo.size - 1, d))
+    return _take(_load().xo_bruteforce_query_metric(_ptr(rs), _ptr(ro), ro.size - 1, _ptr(qs),
+                                                    _ptr(qo), qo.size - 1, d,
+                                                    _METRICS[metric]))
 
 
 def neighbors_of(seqs, offsets, i: int, d: int) -> np.ndarray:

@@ -346,10 +346,12 @@ void* xo_symdel_cross(const uint8_t* seqs, const int64_t* off, const int64_t* re
   return pack(keep, 3);
 }
 
-// SymDel query-vs-reference: rows (q, r, dist) with Lev <= d, sorted by (q, r).
-// Steps 1-2 on the reference, step 3 with the queries' own variants.
-void* xo_symdel_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,
-                      const uint8_t* q_seqs, const int64_t* q_off, int64_t n_q, int d) {
+// SymDel query-vs-reference: rows (q, r, dist) with dist <= d, sorted by
+// (q, r).  Steps 1-2 on the reference, step 3 with the queries' own variants.
+// metric: 0 = Levenshtein, 1 = Hamming.
+void* xo_symdel_query_metric(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,
+                             const uint8_t* q_seqs, const int64_t* q_off, int64_t n_q, int d,
+                             int metric) {
   std::vector<std::string> ref(n_ref);
   std::unordered_map<std::string, std::vector<uint32_t>> table;
   for (int64_t r = 0; r < n_ref; ++r) {
@@ -368,7 +370,7 @@ void* xo_symdel_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     for (uint32_t r : cand) {
-      int dist = lev_full(s, ref[r]);
+      int dist = distance(s, ref[r], metric);
       if (dist <= d) rows.push_back({static_cast<uint32_t>(q), r, static_cast<uint32_t>(dist)});
     }
   }
@@ -397,22 +399,34 @@ void* xo_bruteforce_self(const uint8_t* seqs, const int64_t* off, int64_t n, int
   return xo_bruteforce_self_metric(seqs, off, n, d, 0);
 }
 
-// All (q, r) with Lev <= d by exhaustive comparison.
-void* xo_bruteforce_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,
-                          const uint8_t* q_seqs, const int64_t* q_off, int64_t n_q, int d) {
+void* xo_symdel_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,
+                      const uint8_t* q_seqs, const int64_t* q_off, int64_t n_q, int d) {
+  return xo_symdel_query_metric(ref_seqs, ref_off, n_ref, q_seqs, q_off, n_q, d, 0);
+}
+
+// All (q, r) with dist <= d by exhaustive comparison.  metric: 0 =
+// Levenshtein, 1 = Hamming.
+void* xo_bruteforce_query_metric(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,
+                                 const uint8_t* q_seqs, const int64_t* q_off, int64_t n_q, int d,
+                                 int metric) {
   std::vector<std::string> ref(n_ref);
   for (int64_t r = 0; r < n_ref; ++r) ref[r] = seq_at(ref_seqs, ref_off, r);
   std::vector<std::vector<uint32_t>> rows;
   for (int64_t q = 0; q < n_q; ++q) {
     std::string s = seq_at(q_seqs, q_off, q);
     for (int64_t r = 0; r < n_ref; ++r) {
-      int dist = lev_full(s, ref[r]);
+      int dist = distance(s, ref[r], metric);
       if (dist <= d)
         rows.push_back({static_cast<uint32_t>(q), static_cast<uint32_t>(r),
                         static_cast<uint32_t>(dist)});
     }
   }
   return pack(rows, 3);
+}
+
+void* xo_bruteforce_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64_t n_ref,
+                          const uint8_t* q_seqs, const int64_t* q_off, int64_t n_q, int d) {
+  return xo_bruteforce_query_metric(ref_seqs, ref_off, n_ref, q_seqs, q_off, n_q, d, 0);
 }
 
 // Every j != i with Lev(s_i, s_j) <= d: rows (j, dist), sorted by j. This is

@@ -391,3 +391,20 @@ def test_sharded_search_is_the_brute_force(metric):
     seqs, off = gen.workload(gen.SELF_1M, 2_000)
     assert np.array_equal(oracle.symdel_self_sharded(seqs, off, 2, metric, 4),
                           oracle.bruteforce_self(seqs, off, 2, metric))
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_hamming_query_equals_bruteforce(d):
+    rs, ro = gen.generate(1200, 60 + d, 0.2, 0.01)
+    strs = gen.to_strings(rs, ro)
+    # one substitution in 60 reference entries, plus fresh queries
+    subst = [s[:2] + ("W" if s[2] != "W" else "Y") + s[3:] for s in strs[:60] if len(s) > 3]
+    qs, qo = gen.from_strings(subst + gen.to_strings(*gen.generate(200, 70 + d, 0.0, 0.0)))
+    got = oracle.symdel_query(rs, ro, qs, qo, d, "hamming")
+    assert np.array_equal(got, oracle.bruteforce_query(rs, ro, qs, qo, d, "hamming"))
+    assert got.shape[0] >= len(subst)
+    lens_r, lens_q = np.diff(ro), np.diff(qo)
+    assert np.array_equal(lens_q[got[:, 0]], lens_r[got[:, 1]])
+    lev = oracle.symdel_query(rs, ro, qs, qo, d)
+    key = lambda r: r[:, 0].astype(np.int64) << 32 | r[:, 1].astype(np.int64)
+    assert np.isin(key(got), key(lev)).all()
