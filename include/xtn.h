@@ -215,6 +215,17 @@ XTN_API int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const 
                      xtn_stream_t stream);
 
 /*
+ * The Hamming variant of the query search (Results, comparison with
+ * CompAIRR): the same candidates from the index, the last step filtering by
+ * Hamming distance.  Rows are {q, r, dist} with equal lengths and dist = the
+ * number of differing positions <= d (the index's d), sorted by (q, r).
+ * Arguments and errors as xtn_search_query.
+ */
+XTN_API int xtn_search_query_hamming(const xtn_index* idx, const uint8_t* q_seqs,
+                                     const int64_t* q_offsets, int64_t n_q, xtn_triple* out,
+                                     int64_t cap, int64_t* n_out, xtn_stream_t stream);
+
+/*
  * TCRdist post-filter of neighbour rows (Results, "SymDel lookup can be
  * combined with more advanced similarity metrics").  For each input row
  * {i, j, dist} the score of sequences i and j is computed as: with m the

@@ -1167,8 +1167,12 @@ int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   return XTN_OK;
 }
 
+// metric: 0 = Levenshtein, 1 = Hamming (the index's candidates serve both:
+// Hamming neighbours within d share the string left after deleting the
+// differing positions).
 int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
-                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out, cudaStream_t s) {
+                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out, cudaStream_t s,
+                      int metric = 0) {
   if (!n_out) return XTN_ERR_INVALID_ARG;
   *n_out = 0;
   if (!idx || n_q < 0 || cap < 0 || !q_offsets) return XTN_ERR_INVALID_ARG;
@@ -1230,7 +1234,7 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
   if (rc) return rc;
   rc = launch_back(b, n_cand, nullptr, pair_bits, idx->id_bits, peq, e.lens, (uint64_t)n_q,
                    idx->keys, idx->lens, (uint64_t)idx->n, nullptr, 0, idx->d, o.dev, o.dev_cap,
-                   sms, err, s, cfg_pairs);
+                   sms, err, s, cfg_pairs, metric);
   if (rc) return rc;
   struct {
     uint64_t rows;
@@ -1606,6 +1610,14 @@ int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t*
   xtn::HostSpan span("host_call_search_query");
   return xtn::search_query_impl(idx, q_seqs, q_offsets, n_q, out, cap, n_out,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_search_query_hamming(const xtn_index* idx, const uint8_t* q_seqs,
+                             const int64_t* q_offsets, int64_t n_q, xtn_triple* out, int64_t cap,
+                             int64_t* n_out, xtn_stream_t stream) {
+  xtn::HostSpan span("host_call_search_query");
+  return xtn::search_query_impl(idx, q_seqs, q_offsets, n_q, out, cap, n_out,
+                                reinterpret_cast<cudaStream_t>(stream), 1);
 }
 
 int xtn_tcrdist_filter(const uint8_t* seqs, const int64_t* offsets, int64_t n,

@@ -48,6 +48,7 @@ SIGNATURES = {
     "xtn_index_free": (_I, [_P]),
     "xtn_index_info": (_I, [_P, _P, _P, _P, _P]),
     "xtn_search_query": (_I, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
+    "xtn_search_query_hamming": (_I, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
     "xtn_tcrdist_filter": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
     "xtn_tcrdist_filter_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
     "xtn_plan_create": (_I, [_P, _I64, _I, _P, _I64, _I64, _P]),

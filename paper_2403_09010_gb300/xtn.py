@@ -288,8 +288,13 @@ def index_build(seqs, offsets, d: int) -> Index:
     return Index(h)
 
 
-def search_query(index: Index, q_seqs, q_offsets, cap: int | None = None, stream=None):
-    """All (q, r) with Lev(query q, reference r) <= d; see xtn_search_query."""
+def search_query(index: Index, q_seqs, q_offsets, cap: int | None = None, stream=None,
+                 metric: str = "levenshtein"):
+    """All (q, r) with Lev(query q, reference r) <= d; see xtn_search_query.
+    metric "hamming" calls xtn_search_query_hamming (equal lengths)."""
+    if metric not in _METRICS:
+        raise ValueError(f"unknown metric {metric!r}")
+    entry = "xtn_search_query_hamming" if metric == "hamming" else "xtn_search_query"
     n_q = _n_items(q_offsets)
     sp, sk, _ = _ptr(q_seqs, np.uint8)
     op, ok, _ = _ptr(q_offsets, np.int64)
@@ -298,9 +303,9 @@ def search_query(index: Index, q_seqs, q_offsets, cap: int | None = None, stream
         cap = 8 * n_q + 1024
 
     def fn(optr, c, nref):
-        return native.lib().xtn_search_query(index.handle, sp, op, n_q, optr, c, nref, st)
+        return getattr(native.lib(), entry)(index.handle, sp, op, n_q, optr, c, nref, st)
 
-    return _call_with_rows(fn, cap, q_seqs, "xtn_search_query")
+    return _call_with_rows(fn, cap, q_seqs, entry)
 
 
 def tcrdist_filter(seqs, offsets, rows, max_score: int = 24):

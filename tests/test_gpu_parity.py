@@ -522,6 +522,24 @@ def test_query_matches_oracle(xtn, d):
     idx.free()
 
 
+def test_query_hamming_matches_oracle(xtn):
+    rs, ro, reqs = gen.served(ref_n=40_000, n_req=4, max_req=3000)
+    idx = xtn.index_build(rs, ro, 2)
+    for r in reqs:
+        want = oracle.symdel_query(rs, ro, r.seqs, r.offsets, 2, "hamming")
+        got = _rows(xtn.search_query(idx, r.seqs, r.offsets, metric="hamming"))
+        assert np.array_equal(got, want)
+    # two letters: equal-length near-copies and repeated residues
+    rng = np.random.default_rng(72)
+    ref, qs = _rand_strings(rng, 400, "AC", 0, 9), _rand_strings(rng, 150, "AC", 0, 9)
+    (a, ao), (b, bo) = gen.from_strings(ref), gen.from_strings(qs)
+    small = xtn.index_build(a, ao, 2)
+    assert np.array_equal(_rows(xtn.search_query(small, b, bo, metric="hamming")),
+                          oracle.bruteforce_query(a, ao, b, bo, 2, "hamming"))
+    small.free()
+    idx.free()
+
+
 def test_query_small_reference_bruteforce(xtn):
     rng = np.random.default_rng(8)
     ref = _rand_strings(rng, 300, "ACD", 0, 7)
