@@ -69,6 +69,7 @@ def test_argument_checks_before_device_work(lib):
     assert n_out.value == 0
     assert lib.xtn_index_build(seq, off, 0, 1, None, None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_search_query(None, seq, off, 1, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_query_hamming(None, seq, off, 1, None, 0, ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_index_free(None) == native.XTN_OK
     assert lib.xtn_index_info(None, None, None, None, None) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_tcrdist_filter(seq, off, 1, None, 0, 24, None, ctypes.byref(n_out), None) == native.XTN_OK
