@@ -14,7 +14,9 @@ ctypes. Every function returns numpy arrays of uint32 rows:
 * ``symdel_self_sharded`` (i, j, dist)              -- symdel_self on several threads
 * ``symdel_query``     (q, r, dist)                 -- steps 1-2 on the reference,
                                                        step 3 with the queries
-* ``bruteforce_self`` / ``bruteforce_query``        -- exhaustive search (pin)
+* ``bruteforce_self`` / ``bruteforce_query``        -- exhaustive search (pin);
+                                                       ``threads=`` splits the
+                                                       references over threads
 * ``hamming``; ``metric="hamming"`` of ``symdel_self`` / ``symdel_batched`` /
   ``bruteforce_self``  -- the Hamming variant (the last step filters by
   Hamming distance; unequal lengths are never neighbours)
@@ -96,6 +98,9 @@ def _configure(lib):
     for name in ("xo_symdel_query_metric", "xo_bruteforce_query_metric"):
         getattr(lib, name).argtypes = [_P, _P, _I64, _P, _P, _I64, ctypes.c_int, ctypes.c_int]
         getattr(lib, name).restype = _P
+    lib.xo_bruteforce_query_threaded.argtypes = [_P, _P, _I64, _P, _P, _I64, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int]
+    lib.xo_bruteforce_query_threaded.restype = _P
     lib.xo_neighbors_of.argtypes = [_P, _P, _I64, _I64, ctypes.c_int]
     lib.xo_neighbors_of.restype = _P
     lib.xo_tcrdist_filter.argtypes = [_P, _P, _P, _I64, ctypes.c_int]
@@ -191,9 +196,16 @@ def bruteforce_self(seqs, offsets, d: int, metric: str = "levenshtein") -> np.nd
 
 
 def bruteforce_query(ref_seqs, ref_offsets, q_seqs, q_offsets, d: int,
-                     metric: str = "levenshtein") -> np.ndarray:
+                     metric: str = "levenshtein", threads: int = 1) -> np.ndarray:
+    """Every (q, r, dist) with dist <= d by comparing each query with each
+    reference; threads != 1 splits the references over that many threads
+    (0: all hardware threads), with the same rows."""
     rs, ro = _prep(ref_seqs, ref_offsets)
     qs, qo = _prep(q_seqs, q_offsets)
+    if threads != 1:
+        return _take(_load().xo_bruteforce_query_threaded(
+            _ptr(rs), _ptr(ro), ro.size - 1, _ptr(qs), _ptr(qo), qo.size - 1, d,
+            _METRICS[metric], int(threads)))
     return _take(_load().xo_bruteforce_query_metric(_ptr(rs), _ptr(ro), ro.size - 1, _ptr(qs),
                                                     _ptr(qo), qo.size - 1, d,
                                                     _METRICS[metric]))

@@ -429,6 +429,40 @@ void* xo_bruteforce_query(const uint8_t* ref_seqs, const int64_t* ref_off, int64
   return xo_bruteforce_query_metric(ref_seqs, ref_off, n_ref, q_seqs, q_off, n_q, d, 0);
 }
 
+// The same exhaustive comparison with the references cut into `threads`
+// contiguous ranges (0: the host's hardware threads), one per thread: each
+// thread compares every query with every reference of its range.  Only the
+// split of the reference loop differs from xo_bruteforce_query_metric, so the
+// rows are the same; it lets a test check a few queries against references
+// of millions of sequences in seconds.
+void* xo_bruteforce_query_threaded(const uint8_t* ref_seqs, const int64_t* ref_off,
+                                   int64_t n_ref, const uint8_t* q_seqs, const int64_t* q_off,
+                                   int64_t n_q, int d, int metric, int threads) {
+  if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::string> q(n_q);
+  for (int64_t k = 0; k < n_q; ++k) q[k] = seq_at(q_seqs, q_off, k);
+  std::vector<std::vector<std::vector<uint32_t>>> part(threads);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < threads; ++t)
+    pool.emplace_back([&, t] {
+      const int64_t lo = n_ref * t / threads, hi = n_ref * (t + 1) / threads;
+      for (int64_t r = lo; r < hi; ++r) {
+        const std::string s = seq_at(ref_seqs, ref_off, r);
+        for (int64_t k = 0; k < n_q; ++k) {
+          const int dist = distance(q[k], s, metric);
+          if (dist <= d)
+            part[t].push_back({static_cast<uint32_t>(k), static_cast<uint32_t>(r),
+                               static_cast<uint32_t>(dist)});
+        }
+      }
+    });
+  for (auto& th : pool) th.join();
+  std::vector<std::vector<uint32_t>> rows;
+  for (auto& p : part) rows.insert(rows.end(), p.begin(), p.end());
+  sort_unique(rows);
+  return pack(rows, 3);
+}
+
 // Every j != i with Lev(s_i, s_j) <= d: rows (j, dist), sorted by j. This is
 // the plain definition evaluated for one sequence, for sampled checks of
 // outputs too large to recompute in full.

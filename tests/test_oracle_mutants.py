@@ -7,7 +7,8 @@ checks restate the pins of test_oracle_pins.py in a compact form: textbook
 edit distances, the worked variant count of Sec. 2.1, the special case
 d = 0, Hamming textbook values and lengths, the hand-worked TCRdist scores of
 tests/golden/tcrdist_hand.txt, the self, query, batched and sharded searches
-against exhaustive comparison, one sequence's neighbours, the TCRdist filter
+against exhaustive comparison, the threaded exhaustive query against the
+single-thread one, one sequence's neighbours, the TCRdist filter
 against the all-pairs scorer, and the within/between partition of the
 batched search.  The unmutated source passes every check.
 """
@@ -76,6 +77,11 @@ MUTANTS = [
     ("sharded search pairs an id with itself",
      "for (size_t b = a + 1; b < kv.second.size(); ++b)",
      "for (size_t b = a; b < kv.second.size(); ++b)"),
+    ("threaded exhaustive query skips the last reference of each range",
+     "for (int64_t r = lo; r < hi; ++r) {", "for (int64_t r = lo; r + 1 < hi; ++r) {"),
+    ("threaded exhaustive query threshold strict",
+     "          if (dist <= d)\n            part[t].push_back(",
+     "          if (dist < d)\n            part[t].push_back("),
 ]
 
 
@@ -185,6 +191,17 @@ def check_neighbours_of_one_sequence():
         assert oracle.neighbors_of(seqs, off, i, 2).tolist() == want
 
 
+def check_threaded_query_equals_exhaustive():
+    rs, ro = _prefix(600)
+    strs = gen.to_strings(rs, ro)
+    # the last reference of each of the three ranges is some query's neighbour
+    qs, qo = gen.from_strings(strs[::37] + [s[1:] for s in strs[::41]]
+                              + [strs[199], strs[399], strs[599]])
+    want = oracle.bruteforce_query(rs, ro, qs, qo, 2)
+    assert want.shape[0] > 20
+    assert np.array_equal(oracle.bruteforce_query(rs, ro, qs, qo, 2, threads=3), want)
+
+
 def check_sharded_equals_exhaustive():
     seqs, off = _prefix(600)
     assert np.array_equal(oracle.symdel_self_sharded(seqs, off, 2, threads=3),
@@ -205,7 +222,8 @@ CHECKS = [check_textbook_distances, check_worked_variant_count, check_hamming,
           check_tcrdist_hand_worked, check_d0_is_duplicate_grouping,
           check_search_equals_exhaustive, check_query_equals_exhaustive,
           check_batched_is_per_repertoire, check_neighbours_of_one_sequence,
-          check_sharded_equals_exhaustive, check_tcrdist_filter_and_scorer,
+          check_sharded_equals_exhaustive, check_threaded_query_equals_exhaustive,
+          check_tcrdist_filter_and_scorer,
           check_between_and_within_partition]
 
 

@@ -408,3 +408,25 @@ def test_hamming_query_equals_bruteforce(d):
     lev = oracle.symdel_query(rs, ro, qs, qo, d)
     key = lambda r: r[:, 0].astype(np.int64) << 32 | r[:, 1].astype(np.int64)
     assert np.isin(key(got), key(lev)).all()
+
+
+# ------------------------------------------- threaded exhaustive query ---
+@pytest.mark.parametrize("metric", ["levenshtein", "hamming"])
+def test_threaded_bruteforce_query_is_the_brute_force(metric):
+    # references split over threads: every thread count, including more
+    # threads than references, gives the single-thread exhaustive rows
+    rs, ro = gen.generate(700, 81, 0.2, 0.01)
+    strs = gen.to_strings(rs, ro)
+    qs, qo = gen.from_strings(strs[::97] + strs[-3:] + gen.to_strings(*gen.generate(40, 82)))
+    want = oracle.bruteforce_query(rs, ro, qs, qo, 2, metric)
+    assert want.shape[0] >= 10
+    assert np.array_equal(want, oracle.symdel_query(rs, ro, qs, qo, 2, metric))
+    for threads in (2, 3, 7, 0):
+        got = oracle.bruteforce_query(rs, ro, qs, qo, 2, metric, threads=threads)
+        assert np.array_equal(got, want), threads
+    tiny_s, tiny_o = gen.from_strings(["CASSF", "CASF", "CAS"])
+    q_s, q_o = gen.from_strings(["CASF", "CAF"])
+    want = oracle.bruteforce_query(tiny_s, tiny_o, q_s, q_o, 1, metric)
+    for threads in (1, 2, 5, 9):
+        assert np.array_equal(
+            oracle.bruteforce_query(tiny_s, tiny_o, q_s, q_o, 1, metric, threads=threads), want)
