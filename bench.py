@@ -11,7 +11,7 @@ the sequences and device->host copy of the result rows inside every step).
 Under torchrun each rank runs an independent replica (the search has no
 exchange step on one GPU), the slowest rank's time is used and `value` counts
 the pairs of all ranks.  `--impl reference` times the CPU oracle instead, on
-a bounded prefix of the same workload.
+every host core, on a bounded prefix of the same workload.
 """
 from __future__ import annotations
 
@@ -152,31 +152,36 @@ class Clocks:
 
 
 def run_oracle_arm(args):
-    """--impl reference: the CPU oracle, as it stands, on a bounded prefix."""
+    """--impl reference: the CPU oracle, as it stands, on every host core (its
+    variant keys split over threads by hash), each step a bounded prefix of
+    the same workload sized so that warm-up plus timed steps take about three
+    minutes."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     seqs, off = gen.workload(WORKLOAD)
-    # size the per-step sample so warm-up + timed steps take ~2.5 minutes
+    cores = os.cpu_count() or 1
+    probe = 20_000
     t0 = time.perf_counter()
-    oracle.symdel_self(seqs[: off[5000]], off[:5001], WORKLOAD.d)
-    per_seq = max((time.perf_counter() - t0) / 5000, 1e-7)
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    n_s = int(min(CPU_SAMPLE_N, max(2000, budget / per_seq)))
+    oracle.symdel_self_sharded(seqs[: off[probe]], off[: probe + 1], WORKLOAD.d, threads=cores)
+    per_seq = max((time.perf_counter() - t0) / probe, 1e-8)
+    budget = 170.0 / max(1, args.steps + args.warmup)
+    n_s = int(min(WORKLOAD.n, max(probe, budget / per_seq)))
     s_seqs, s_off = seqs[: off[n_s]], off[: n_s + 1]
     for _ in range(args.warmup):
-        oracle.symdel_self(s_seqs, s_off, WORKLOAD.d)
+        oracle.symdel_self_sharded(s_seqs, s_off, WORKLOAD.d, threads=cores)
     times, pairs = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        rows = oracle.symdel_self(s_seqs, s_off, WORKLOAD.d)
+        rows = oracle.symdel_self_sharded(s_seqs, s_off, WORKLOAD.d, threads=cores)
         times.append(time.perf_counter() - t0)
         pairs = rows.shape[0]
     total = sum(times)
     value = pairs * args.steps / total
-    sample = f"first {n_s:,} sequences of the {WORKLOAD.n:,}-sequence d={WORKLOAD.d} workload"
+    sample = (f"first {n_s:,} sequences of the {WORKLOAD.n:,}-sequence d={WORKLOAD.d} workload, "
+              f"{cores} threads, {pairs:,} pairs per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -184,7 +189,8 @@ def run_oracle_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD.name, "n": WORKLOAD.n, "d": WORKLOAD.d,
                    "sample_n": n_s, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "kind": "oracle, keys partitioned by hash over threads",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -192,6 +198,26 @@ def run_oracle_arm(args):
 
 
 def cpu_baseline():
+    """The oracle on every host core (variant keys split over threads by
+    hash) on the whole benchmarked workload: all 1,000,000 sequences."""
+    import oracle
+    oracle.build()
+    seqs, off = gen.workload(WORKLOAD)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    rows = oracle.symdel_self_sharded(seqs, off, WORKLOAD.d, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": rows.shape[0] / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle, keys partitioned by hash over threads",
+            "sample": f"the whole {WORKLOAD.n:,}-sequence d={WORKLOAD.d} workload (n = "
+                      f"{off.size - 1:,}), {cores} threads, {dt:.1f} s, "
+                      f"{rows.shape[0]:,} pairs", "seconds": dt, "pairs": int(rows.shape[0])}
+
+
+def cpu_single_thread_prefix():
+    """The single-thread oracle on the first 100,000 sequences: a labelled
+    extra beside the all-core baseline (pairs grow faster than the work with
+    the prefix length, so this rate is not the rate on the whole workload)."""
     import oracle
     oracle.build()
     seqs, off = gen.workload(WORKLOAD, CPU_SAMPLE_N)
@@ -201,23 +227,6 @@ def cpu_baseline():
     return {"value": rows.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {CPU_SAMPLE_N:,} sequences of the {WORKLOAD.n:,}-sequence "
                       f"d={WORKLOAD.d} workload, single thread, {dt:.1f} s, "
-                      f"{rows.shape[0]:,} pairs"}
-
-
-def cpu_all_cores():
-    """The oracle with its variant keys split over every host core, on the same
-    sample as cpu_baseline (context beside the single-thread figure)."""
-    import oracle
-    oracle.build()
-    seqs, off = gen.workload(WORKLOAD, CPU_SAMPLE_N)
-    cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    rows = oracle.symdel_self_sharded(seqs, off, WORKLOAD.d, threads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": rows.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle, keys "
-            "partitioned by hash over threads",
-            "sample": f"first {CPU_SAMPLE_N:,} sequences of the {WORKLOAD.n:,}-sequence "
-                      f"d={WORKLOAD.d} workload, {cores} threads, {dt:.1f} s, "
                       f"{rows.shape[0]:,} pairs"}
 
 
@@ -453,6 +462,43 @@ def run_streaming(reps: int = 3):
     return out
 
 
+def run_profile_case(args):
+    """Small cases of the query search (a resident index of n reference
+    sequences, default 2,000,000, and one request of 20,000 queries, half of
+    them one-deletion mutants of reference entries) and of the TCRdist filter (the d<=2 rows of the
+    first n sequences of the TCRdist workload, default 1,000,000), run warm-up
+    plus `steps` times; for ncu captures of their kernels."""
+    import torch
+    import paper_2403_09010_gb300 as xtn
+    xtn.build()
+    cur = torch.cuda.current_stream()
+    if args.case == "query":
+        rs, ro = gen.generate(args.n or 2_000_000, 41, 0.15, 0.01)
+        qs, qo = gen.generate(10_000, 42, 0.0, 0.0)
+        strs = gen.to_strings(rs[: ro[10_000]], ro[: 10_001])
+        rng = np.random.default_rng(43)
+        mut = [s[:k] + s[k + 1:] for s, k in zip(strs, rng.integers(0, 8, len(strs)))]
+        qs, qo = gen.from_strings(gen.to_strings(qs, qo) + mut)
+        idx = xtn.index_build(rs, ro, 2)
+        dq, dqo = torch.from_numpy(qs).cuda(), torch.from_numpy(qo).cuda()
+        rows = xtn.search_query(idx, dq, dqo)
+        ms_q = _events_ms(lambda: xtn.search_query(idx, dq, dqo),
+                          args.warmup + args.steps, cur)
+        out = {"case": "query", "ref_n": int(ro.size - 1), "queries": int(qo.size - 1),
+               "rows": int(rows.shape[0]), "search_ms": ms_q}
+        idx.free()
+    else:
+        seqs, off = gen.workload(gen.TCRDIST_1M, args.n)
+        ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
+        rows = xtn.search_self(ds, do, 2)
+        ms_f = _events_ms(lambda: xtn.tcrdist_filter(ds, do, rows, 24),
+                          args.warmup + args.steps, cur)
+        out = {"case": "tcrdist", "n": int(off.size - 1), "rows": int(rows.shape[0]),
+               "filter_ms": ms_f}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,11 +511,16 @@ def main():
                          "streaming side measurements")
     ap.add_argument("--n", type=int, default=None,
                     help="use only the first n sequences (small cases for profiling)")
+    ap.add_argument("--case", default="self", choices=["self", "query", "tcrdist"],
+                    help="query / tcrdist: a small case of the query search or of the TCRdist "
+                         "filter, for profiling (prints one JSON line of timings)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_oracle_arm(args)
+    if args.case != "self":
+        return run_profile_case(args)
 
     import torch
     world, rank, local = _dist()
@@ -570,7 +621,9 @@ def main():
                     "traffic": (tpr * n_rec_per_launch) if tpr and n_rec_per_launch else None,
                     "algorithmic_bytes_per_launch": nbytes / nl,
                     "launches_in_timed_region": nl, "avg_launch_ms": ms / nl}
-    kernels = {k: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None,
+    kernels = {k: {"launches": v[0], "ms": v[1],
+                   "GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] else None,
+                   "frac": (v[2] / (v[1] / 1e3) / 1e9 / peak) if v[1] else None,
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
 
     if rank != 0:
@@ -607,7 +660,7 @@ def main():
         line["streaming"] = run_streaming()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-        line["cpu_all_cores"] = cpu_all_cores()
+        line["cpu_single_thread_prefix"] = cpu_single_thread_prefix()
     print(json.dumps(line))
     return 0
 

@@ -28,8 +28,11 @@
  * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Kernels
  *   and copies are issued on it; every call returns only after the stream has
  *   finished the call's work, because the result count is read back.
- *   Scratch memory is taken from the device's stream-ordered pool
- *   (cudaMallocAsync) and returned before the call ends.
+ *   Scratch memory is carved from a per-device cache of device blocks that
+ *   calls take and give back (see xtn_scratch_trim); only a call that needs
+ *   more than its block holds allocates the rest from the device's
+ *   stream-ordered pool (cudaMallocAsync), and the block grows to that size
+ *   the next time it is taken.
  * - Output rows are `xtn_triple {i, j, dist}` sorted ascending by (i, j),
  *   without duplicates.  `*n_out` always receives the exact number of rows of
  *   the full result.  If it exceeds `cap`, the first `cap` rows are written
@@ -283,22 +286,28 @@ XTN_API int xtn_plan_free(xtn_plan* plan);
 
 /*
  * xtn_tcrdist_filter_noalloc: xtn_tcrdist_filter for callers that cannot
- * allocate device memory -- processes held to a fixed memory budget or run
- * under an allocator they do not control, and code that records its work
- * while allocation is not permitted.  The paper has no counterpart to this
- * entry point; it computes exactly what xtn_tcrdist_filter computes.
+ * allocate device memory -- a process that must stay inside a fixed
+ * device-memory budget, or a library loaded into a host application whose
+ * own allocator owns the device memory, where an allocation of ours could
+ * fail or take memory the host application counted on.  The paper has no
+ * counterpart to this entry point; it computes exactly what
+ * xtn_tcrdist_filter computes.
  *   - It allocates nothing: its scratch (encoded sequences, look-back status,
  *     counters) lives in one fixed array of about 6.3 MiB of device memory
  *     that every GPU loading the library holds until the process exits.
  *   - Limits: n <= XTN_NOALLOC_MAX_SEQS sequences and n_in <=
  *     XTN_NOALLOC_MAX_ROWS rows; larger inputs return XTN_ERR_TOO_LARGE.
- *   - seqs, offsets, in and out must be device pointers of the current device
- *     (a host buffer would need a device copy); otherwise XTN_ERR_INVALID_ARG.
- *     n_out is a host pointer; the call waits for its stream.
+ *   - seqs, offsets, in and out must be device pointers of the current
+ *     device, or managed memory (a host buffer would need a device copy);
+ *     otherwise XTN_ERR_INVALID_ARG.  n_out is a host pointer.
+ *   - The call reads the row count back, so it returns only after its stream
+ *     has finished the call's work.
  *   - The first call on a device looks the array's device address up (once
  *     per device); make that first call before any stream capture.
- *   - All calls share the one array: calls that overlap on the GPU (other
- *     streams, other host threads) race and must be serialised by the caller.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (the call clears its counters itself): calls that overlap on the GPU
+ *     (other streams, other host threads) race and must be serialised by
+ *     the caller.
  * Errors: as xtn_tcrdist_filter, plus TOO_LARGE.
  */
 #define XTN_NOALLOC_MAX_SEQS (1 << 18)
@@ -354,6 +363,20 @@ XTN_API int xtn_tune_count(int knob);
 XTN_API int xtn_scratch_trim(void);
 
 /*
+ * Bounded device waits.  A kernel that waits for another block's status word
+ * (the decoupled look-back of the scans, sorts and row compaction) polls it
+ * at most 2^20 times, about a second, and then gives up: the call returns
+ * XTN_ERR_DEVICE_TIMEOUT instead of waiting without bound, and every index a
+ * kernel computes from the incomplete sums is range-checked before use.
+ * xtn_set_wait_limit(polls) sets that limit for the calls that start
+ * afterwards (process-wide; 0 restores the default).  A small limit makes a
+ * wait give up while its predecessors are still working, which exercises the
+ * give-up path; the search results of such a call are not defined.
+ * Errors: INVALID_ARG for polls < 0 or > 2^20.
+ */
+XTN_API int xtn_set_wait_limit(int64_t polls);
+
+/*
  * Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by CUDA events on its stream and tagged with the algorithmic
  * bytes it must move.  xtn_profile_report() synchronises those events and
@@ -361,7 +384,8 @@ XTN_API int xtn_scratch_trim(void);
  * into buf (NUL-terminated, truncated to buf_len); it returns the number of
  * lines, and clears the records.  Enabling costs two event records per launch.
  * Host-side spans are reported the same way, with zero bytes and wall-clock
- * milliseconds: host_call_search_self / _between / _query (the whole call),
+ * milliseconds: host_call_search_self / _between / _query /
+ * _query_hamming (the whole call),
  * host_scratch_alloc (each scratch allocation outside the cache) and
  * host_stream_wait (each wait for the stream to drain).
  */

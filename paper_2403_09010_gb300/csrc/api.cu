@@ -297,6 +297,24 @@ int map_device_err(uint32_t e) {
     if ((ar).failed()) return XTN_ERR_OOM; \
   } while (0)
 
+// Poll limit of bounded device waits for calls that start from now on (0 =
+// the kernels' default); see xtn_set_wait_limit.
+std::atomic<uint32_t> g_wait_limit{0};
+
+__global__ void k_set_word(uint32_t* p, uint32_t v) { *p = v; }
+
+// Zero a call's error words (4 x u32) and, when a wait limit is set, put it
+// in the second word, where the look-back waits read it.
+int init_err(uint32_t* err, cudaStream_t s) {
+  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  const uint32_t lim = g_wait_limit.load();
+  if (lim) {
+    k_set_word<<<1, 1, 0, s>>>(err + 1, lim);
+    XTN_CK(cudaGetLastError());
+  }
+  return XTN_OK;
+}
+
 // Read n elements of device memory into host memory and wait for the stream.
 template <class T>
 int read_back(T* host, const T* dev, size_t n, cudaStream_t s) {
@@ -361,11 +379,11 @@ int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar
   int64_t total = 0;
   if (is_device_ptr(offsets)) {
     out->off = offsets;
-    int rc = read_back(&total, offsets + n, 1, s);
-    if (rc) return rc;
+    // both ends of the offsets in one wait for the stream
     int64_t first = 0;
-    rc = read_back(&first, offsets, 1, s);
-    if (rc) return rc;
+    XTN_CK(cudaMemcpyAsync(&first, offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    XTN_CK(cudaMemcpyAsync(&total, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    XTN_CK(host_sync(s));
     if (first != 0 || total < 0) return XTN_ERR_INVALID_ARG;
   } else {
     int rc = check_host_offsets(offsets, n);
@@ -759,7 +777,7 @@ int search_stream_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, i
   uint64_t* ctr = ar.get<uint64_t>(8);
   uint32_t* bins = ar.get<uint32_t>(NB);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(init_err(err, s));
   XTN_CK(cudaMemsetAsync(ctr, 0, 64, s));
   XTN_CK(cudaMemsetAsync(bins, 0, NB * 4, s));
   DevSeqs in;
@@ -972,7 +990,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   uint32_t* err = ar.get<uint32_t>(4);
   uint64_t* counters = ar.get<uint64_t>(4);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(init_err(err, s));
   XTN_CK(cudaMemsetAsync(counters, 0, 32, s));
   DevSeqs in;
   rc = stage_seqs(seqs, offsets, n, ar, s, &in);
@@ -1022,7 +1040,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     XTN_CK(cudaMemcpyAsync(&h.direct, counters + 2, 16, cudaMemcpyDeviceToHost, s));
     XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
     XTN_CK(host_sync(s));
-    if (h.err & DERR_CAPACITY) {
+    if (h.err == DERR_CAPACITY) {  // candidate overflow alone: regroup sized exactly
       ar.release();
       return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
                               metric, between);
@@ -1119,7 +1137,7 @@ int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   Arena ar(s);
   uint32_t* err = ar.get<uint32_t>(4);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(init_err(err, s));
   DevSeqs in;
   rc = stage_seqs(seqs, offsets, n, ar, s, &in);
   if (rc) return rc;
@@ -1184,7 +1202,7 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
   Arena ar(s);
   uint32_t* err = ar.get<uint32_t>(4);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(init_err(err, s));
   DevSeqs in;
   rc = stage_seqs(q_seqs, q_offsets, n_q, ar, s, &in);
   if (rc) return rc;
@@ -1261,7 +1279,7 @@ int tcrdist_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, const x
   Arena ar(s);
   uint32_t* err = ar.get<uint32_t>(4);
   XTN_ALLOC_OK(ar);
-  XTN_CK(cudaMemsetAsync(err, 0, 16, s));
+  XTN_CK(init_err(err, s));
   DevSeqs in;
   rc = stage_seqs(seqs, offsets, n, ar, s, &in);
   if (rc) return rc;
@@ -1454,7 +1472,7 @@ int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return XTN_ERR_INVALID_ARG;
   const int64_t n = p->n;
   const int lo = 64 - p->hs;
-  XTN_CK(cudaMemsetAsync(p->err, 0, 16, s));
+  XTN_CK(init_err(p->err, s));
   XTN_CK(cudaMemsetAsync(p->counters, 0, 32, s));
   XTN_CK(cudaMemsetAsync(p->hist, 0, MAX_PASSES * RADIX * 4, s));
   launch_encode(seqs, p->off, n, p->d, p->keys, p->lens, p->eqprev, p->vcount, p->err, s);
@@ -1615,7 +1633,7 @@ int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t*
 int xtn_search_query_hamming(const xtn_index* idx, const uint8_t* q_seqs,
                              const int64_t* q_offsets, int64_t n_q, xtn_triple* out, int64_t cap,
                              int64_t* n_out, xtn_stream_t stream) {
-  xtn::HostSpan span("host_call_search_query");
+  xtn::HostSpan span("host_call_search_query_hamming");
   return xtn::search_query_impl(idx, q_seqs, q_offsets, n_q, out, cap, n_out,
                                 reinterpret_cast<cudaStream_t>(stream), 1);
 }
@@ -1706,6 +1724,12 @@ int xtn_tune_count(int knob) {
 }
 
 int xtn_scratch_trim(void) { return xtn::trim_scratch(); }
+
+int xtn_set_wait_limit(int64_t polls) {
+  if (polls < 0 || polls > (int64_t)xtn::SPIN_LIMIT) return XTN_ERR_INVALID_ARG;
+  xtn::g_wait_limit.store((uint32_t)polls);
+  return XTN_OK;
+}
 
 int xtn_profile_enable(int on) {
   xtn::g_prof_on.store(on != 0);

@@ -35,6 +35,7 @@ namespace xtn {
 constexpr int VER_THREADS = 256;
 constexpr int VER_ITEMS = 8;
 constexpr int VER_TILE = VER_THREADS * VER_ITEMS;
+static_assert(VER_TILE == VERIFY_TILE, "status sizing in xtn_kernels.h assumes this tile");
 
 // Levenshtein distance between pattern (match vectors peq, length m) and the
 // text held in packed key t (length n <= XTN_MAX_LEN).  All match vectors the
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(VER_THREADS)
   }
 }
 
-size_t verify_status_bytes(int64_t n) { return (size_t)((n + VER_TILE - 1) / VER_TILE) * 8 + 16; }
+size_t verify_status_bytes(int64_t n) { return verify_status_bytes_for(n); }
 
 void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_dev,
                             uint32_t j_bits,

@@ -1,10 +1,11 @@
 // xtn_tcrdist_filter_noalloc: the TCRdist post-filter with every piece of
 // scratch memory in one fixed, file-scope device array, for callers that
-// cannot allocate device memory (a process working inside a fixed memory
-// budget or under an allocator it does not control, code that must not grow
-// the device pool, or code that records its launches while allocation is not
-// permitted).  The same kernels as xtn_tcrdist_filter run; only the place
-// their scratch lives differs.
+// cannot allocate device memory: a process that must stay inside a fixed
+// device-memory budget, or a library loaded into a host application whose
+// own allocator owns the device memory, so that a cudaMalloc of ours could
+// fail or take memory the host application counted on.  The same kernels as
+// xtn_tcrdist_filter run; only the place their scratch lives differs.  The
+// call reads the row count back, so it waits for its stream.
 #include <mutex>
 
 #include "xtn_common.cuh"
@@ -23,7 +24,7 @@ constexpr size_t OFF_LENS = align256(OFF_KEYS + 16 * (size_t)NA_MAX_SEQS);   // 
 constexpr size_t OFF_EQ = align256(OFF_LENS + (size_t)NA_MAX_SEQS);          // uint32_t[]
 constexpr size_t OFF_VCOUNT = align256(OFF_EQ + 4 * (size_t)NA_MAX_SEQS);    // uint32_t[]
 constexpr size_t OFF_STATUS = align256(OFF_VCOUNT + 4 * (size_t)NA_MAX_SEQS);
-constexpr size_t STATUS_BYTES = align256(((size_t)NA_MAX_ROWS / 2048 + 1) * 8 + 16);
+constexpr size_t STATUS_BYTES = align256(verify_status_bytes_for(NA_MAX_ROWS));
 constexpr size_t OFF_COUNTERS = OFF_STATUS + STATUS_BYTES;                    // err, total
 constexpr size_t NA_BYTES = OFF_COUNTERS + 256;
 
@@ -62,13 +63,18 @@ int noalloc_scratch(unsigned char** out) {
   return XTN_OK;
 }
 
+// Device memory of the current device (or managed memory, which any device
+// may reach): a buffer of another GPU would be read through this device's
+// launch, so it is refused like a host buffer.
 bool on_device(const void* p) {
   cudaPointerAttributes a;
-  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+  int dev = -1;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int map_err(uint32_t e) {

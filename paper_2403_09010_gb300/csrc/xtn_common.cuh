@@ -24,8 +24,15 @@ enum : uint32_t {
 
 // A spin on a predecessor's status word gives up after this many polls
 // (each poll sleeps ~0.25-1 us), sets DERR_TIMEOUT and carries on, so a kernel
-// never waits without bound.
+// never waits without bound.  The error word array (4 words, zeroed by the
+// host before a call's first kernel) carries an override in its second word:
+// a non-zero err[1] replaces this limit (xtn_set_wait_limit).
 constexpr uint32_t SPIN_LIMIT = 1u << 20;
+
+__device__ __forceinline__ uint32_t spin_limit(const uint32_t* err) {
+  const uint32_t v = err[1];
+  return v ? v : SPIN_LIMIT;
+}
 
 // ----------------------------------------------------------- status words ---
 // Tile status for decoupled look-back: 2 flag bits + 62 value bits in one
@@ -75,6 +82,7 @@ __device__ __forceinline__ uint64_t warp_lookback(uint64_t* status, uint32_t til
   uint64_t excl = 0;
   int64_t top = (int64_t)tile - 1;
   uint32_t spins = 0;
+  const uint32_t limit = spin_limit(err);
   while (true) {
     const int64_t idx = top - (int64_t)lane;
     const uint64_t w = idx >= 0 ? ld_status(&status[idx]) : (ST_INC | 0);
@@ -84,7 +92,7 @@ __device__ __forceinline__ uint64_t warp_lookback(uint64_t* status, uint32_t til
     const uint32_t first_inc = inc ? (uint32_t)(__ffs(inc) - 1) : 32u;
     const uint32_t needed = first_inc >= 31 ? FULL_MASK : ((2u << first_inc) - 1u);
     if (not_ready & needed) {
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > limit) {
         if (lane == 0) atomicOr(err, DERR_TIMEOUT);
         break;
       }
@@ -106,11 +114,12 @@ __device__ __forceinline__ uint64_t thread_lookback(const uint64_t* status, uint
   uint64_t excl = 0;
   int64_t j = (int64_t)tile - 1;
   uint32_t spins = 0;
+  const uint32_t limit = spin_limit(err);
   while (j >= 0) {
     const uint64_t w = ld_status(&status[(uint64_t)j * stride]);
     const uint64_t flag = w >> 62;
     if (flag == 0) {
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > limit) {
         atomicOr(err, DERR_TIMEOUT);
         break;
       }

@@ -133,6 +133,12 @@ void launch_emit_pairs(const uint64_t* keys, uint64_t n_keys, const uint32_t* S,
                        cudaStream_t s);
 
 // k_verify.cu --------------------------------------------------------------
+// Rows per tile of the verify, dedup and TCRdist kernels, and the look-back
+// status those kernels need for n rows (one word per tile plus a tile counter).
+constexpr int VERIFY_TILE = 2048;
+constexpr size_t verify_status_bytes_for(int64_t n) {
+  return (size_t)((n + VERIFY_TILE - 1) / VERIFY_TILE) * 8 + 16;
+}
 // metric: 0 = Levenshtein, 1 = Hamming (pairs of equal length only).
 // self_mode: 0 = query vs reference, 1 = self-search (pairs within a
 // repertoire when seq_rep is given), 2 = self-search keeping only pairs

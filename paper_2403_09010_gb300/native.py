@@ -61,6 +61,7 @@ SIGNATURES = {
     "xtn_tune_get": (_I, [_I]),
     "xtn_tune_count": (_I, [_I]),
     "xtn_scratch_trim": (_I, []),
+    "xtn_set_wait_limit": (_I, [_I64]),
     "xtn_profile_enable": (_I, [_I]),
     "xtn_profile_report": (_I, [ctypes.c_char_p, _I64]),
 }

@@ -331,6 +331,12 @@ def scratch_trim() -> None:
     check(native.lib().xtn_scratch_trim(), "xtn_scratch_trim")
 
 
+def set_wait_limit(polls: int) -> None:
+    """Poll limit of bounded device waits for later calls (0 = the default);
+    see xtn_set_wait_limit."""
+    check(native.lib().xtn_set_wait_limit(int(polls)), "xtn_set_wait_limit")
+
+
 def profile_enable(on: bool = True) -> None:
     native.lib().xtn_profile_enable(1 if on else 0)
 

@@ -112,3 +112,11 @@ def test_tuning_applied_restores_knobs(lib):
     with xtn.tuning_applied({"pairs_cfg": 2}):   # keys left out stay as they are
         assert [lib.xtn_tune_get(k) for k in knobs] == before[:3] + [2]
     assert [lib.xtn_tune_get(k) for k in knobs] == before
+
+
+def test_wait_limit_range(lib):
+    # a host-side setting: negative and above-default limits are refused
+    assert lib.xtn_set_wait_limit(-1) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_set_wait_limit((1 << 20) + 1) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_set_wait_limit(5) == native.XTN_OK
+    assert lib.xtn_set_wait_limit(0) == native.XTN_OK

@@ -1,9 +1,10 @@
 """xtn_tcrdist_filter_noalloc: the TCRdist filter for callers that cannot
-allocate device memory (fixed memory budgets, allocators they do not control,
-work recorded while allocation is not permitted).  Its scratch lives in one
-fixed device array, so it must give exactly the rows of xtn_tcrdist_filter,
-call after call, without the device's free memory changing.  This file is
-collected last so a failure here never hides the other tests."""
+allocate device memory -- a process held to a fixed device-memory budget, or
+a library running inside a host application whose own allocator owns the
+device memory.  Its scratch lives in one fixed device array, so it must give
+exactly the rows of xtn_tcrdist_filter, call after call, without the device's
+free memory changing.  This file is collected last so a failure here never
+hides the other tests."""
 import ctypes
 
 import numpy as np
