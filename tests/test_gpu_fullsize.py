@@ -112,7 +112,7 @@ def test_served_ref1e7_small_requests_against_oracle(xtn):
     first = np.concatenate([[0], np.cumsum([r.offsets.size - 1 for r in small])])
     for k, r in enumerate(small):
         part = want[(want[:, 0] >= first[k]) & (want[:, 0] < first[k + 1])].copy()
-        part[:, 0] -= first[k]
+        part[:, 0] -= np.uint32(first[k])
         alone = _rows(xtn.search_query(idx, r.seqs, r.offsets))
         assert np.array_equal(alone, part), r.rid
         assert np.array_equal(_rows(in_mix[r.rid]), part), r.rid
