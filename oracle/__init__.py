@@ -22,6 +22,9 @@ ctypes. Every function returns numpy arrays of uint32 rows:
   Hamming distance; unequal lengths are never neighbours)
 * ``neighbors_of``     (j, dist) for one i          -- plain definition, sampled checks
 * ``tcrdist_filter`` / ``tcrdist_allpairs``          -- TCRdist post-filter (Results)
+* ``symdel_paired`` / ``bruteforce_paired``         -- paired chains joined by a
+                                                       token no edit may touch
+                                                       (Discussion)
 """
 from __future__ import annotations
 
@@ -119,6 +122,13 @@ def _configure(lib):
     lib.xo_tcrdist.restype = ctypes.c_int
     lib.xo_count_variants.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]
     lib.xo_count_variants.restype = _I64
+    for name in ("xo_symdel_paired", "xo_bruteforce_paired"):
+        getattr(lib, name).argtypes = [_P, _P, _I64, ctypes.c_int]
+        getattr(lib, name).restype = _P
+    lib.xo_lev_token.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+    lib.xo_lev_token.restype = ctypes.c_int
+    lib.xo_count_variants_token.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]
+    lib.xo_count_variants_token.restype = _I64
     lib.xo_blosum62.argtypes = [ctypes.c_char, ctypes.c_char]
     lib.xo_blosum62.restype = ctypes.c_int
     return lib
@@ -227,6 +237,49 @@ def tcrdist_filter(seqs, offsets, triples, max_score: int) -> np.ndarray:
 def tcrdist_allpairs(seqs, offsets, lev_max: int, max_score: int) -> np.ndarray:
     s, o = _prep(seqs, offsets)
     return _take(_load().xo_tcrdist_allpairs(_ptr(s), _ptr(o), o.size - 1, lev_max, max_score))
+
+
+# ------------------------------------------------------------ paired chains
+TOKEN = "|"
+
+
+def join_chains(a_seqs, a_offsets, b_seqs, b_offsets):
+    """Receptors as one string each, alpha + TOKEN + beta (packed)."""
+    a = np.asarray(a_seqs, np.uint8)
+    b = np.asarray(b_seqs, np.uint8)
+    ao = np.asarray(a_offsets, np.int64)
+    bo = np.asarray(b_offsets, np.int64)
+    parts = []
+    for i in range(ao.size - 1):
+        parts.append(a[ao[i]:ao[i + 1]].tobytes() + TOKEN.encode() + b[bo[i]:bo[i + 1]].tobytes())
+    lens = np.array([len(p) for p in parts], np.int64)
+    off = np.zeros(lens.size + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    return np.frombuffer(b"".join(parts), np.uint8).copy(), off
+
+
+def symdel_paired(a_seqs, a_offsets, b_seqs, b_offsets, d: int) -> np.ndarray:
+    """Paired-chain SymDel search: rows (i, j, dist), dist = the edit distance
+    of alpha + TOKEN + beta with the token never edited."""
+    s, o = _prep(*join_chains(a_seqs, a_offsets, b_seqs, b_offsets))
+    return _take(_load().xo_symdel_paired(_ptr(s), _ptr(o), o.size - 1, d))
+
+
+def bruteforce_paired(a_seqs, a_offsets, b_seqs, b_offsets, d: int) -> np.ndarray:
+    s, o = _prep(*join_chains(a_seqs, a_offsets, b_seqs, b_offsets))
+    return _take(_load().xo_bruteforce_paired(_ptr(s), _ptr(o), o.size - 1, d))
+
+
+def lev_token(a: str, b: str) -> int:
+    """Edit distance with the joining token never deleted, inserted or
+    substituted (FORBIDDEN = 2^20 or more when no admissible alignment)."""
+    ab, bb = a.encode(), b.encode()
+    return _load().xo_lev_token(ab, len(ab), bb, len(bb))
+
+
+def count_variants_token(s: str, d: int) -> int:
+    b = s.encode()
+    return _load().xo_count_variants_token(b, len(b), d)
 
 
 def hamming(a: str, b: str) -> int:

@@ -22,6 +22,10 @@
 // distances, exhaustive edit balls, the SymDel guarantee of Sec. 2.1 and the
 // bag-of-amino-acids bound of Appendix B.
 //
+// Paired chains (Discussion): receptors alpha + '|' + beta, the joining token
+// never deleted, inserted or substituted (lev_token, deletion_variants_token);
+// SymDel and exhaustive searches over them.
+//
 // TCRdist score (Results, "SymDel lookup can be combined with more advanced
 // similarity metrics"; the paper cites TCRdist without defining it; reading
 // used here): gaps = |La - Lb| placed in the shorter sequence after its first
@@ -83,6 +87,56 @@ int hamming(const std::string& a, const std::string& b) {
 // The last step's distance: 0 = Levenshtein, 1 = Hamming.
 int distance(const std::string& a, const std::string& b, int metric) {
   return metric == 1 ? hamming(a, b) : lev_full(a, b);
+}
+
+// Paired chains (Discussion: the CDR3s of both chains concatenated with a
+// non-deletable joining token).  A receptor is the string alpha + TOKEN +
+// beta.  Reading used here: the token is a character outside the residue
+// alphabet that no edit may delete, insert or substitute, so in every
+// admissible alignment the two tokens face each other.  The distance is the
+// edit distance under that rule (infinite cost for any other operation on
+// the token), computed by the same Wagner-Fischer recurrence.
+constexpr char TOKEN = '|';
+constexpr int FORBIDDEN = 1 << 20;  // cost of an edit that touches the token
+
+int lev_token(const std::string& a, const std::string& b) {
+  const size_t la = a.size(), lb = b.size();
+  const size_t w = lb + 1;                       // D[x][y] stored at D[x * w + y]
+  std::vector<int> D((la + 1) * w, 0);
+  auto del = [&](char c) { return c == TOKEN ? FORBIDDEN : 1; };
+  auto sub = [&](char x, char y) {
+    if (x == y) return 0;
+    return (x == TOKEN || y == TOKEN) ? FORBIDDEN : 1;
+  };
+  for (size_t x = 1; x <= la; ++x) D[x * w] = std::min(FORBIDDEN, D[(x - 1) * w] + del(a[x - 1]));
+  for (size_t y = 1; y <= lb; ++y) D[y] = std::min(FORBIDDEN, D[y - 1] + del(b[y - 1]));
+  for (size_t x = 1; x <= la; ++x) {
+    for (size_t y = 1; y <= lb; ++y) {
+      int dl = D[(x - 1) * w + y] + del(a[x - 1]);
+      int in = D[x * w + (y - 1)] + del(b[y - 1]);
+      int sb = D[(x - 1) * w + (y - 1)] + sub(a[x - 1], b[y - 1]);
+      D[x * w + y] = std::min(FORBIDDEN, std::min(std::min(dl, in), sb));
+    }
+  }
+  return D[la * w + lb];
+}
+
+// Step 1 for paired chains: every string reachable from s by at most d
+// deletions of residues (the token is never deleted).
+std::unordered_set<std::string> deletion_variants_token(const std::string& s, int d) {
+  std::unordered_set<std::string> found{s};
+  std::unordered_set<std::string> level{s};   // strings of exactly r deletions
+  for (int r = 1; r <= d; ++r) {
+    std::unordered_set<std::string> deeper;
+    for (const std::string& t : level)
+      for (size_t p = 0; p < t.size(); ++p) {
+        if (t[p] == TOKEN) continue;
+        deeper.insert(t.substr(0, p) + t.substr(p + 1));
+      }
+    found.insert(deeper.begin(), deeper.end());
+    level.swap(deeper);
+  }
+  return found;
 }
 
 // Step 1: all strings reachable from s by at most d single-character deletions.
@@ -475,6 +529,60 @@ void* xo_neighbors_of(const uint8_t* seqs, const int64_t* off, int64_t n, int64_
     if (dist <= d) rows.push_back({static_cast<uint32_t>(j), static_cast<uint32_t>(dist)});
   }
   return pack(rows, 2);
+}
+
+// ---------------- paired chains ----------------
+int xo_lev_token(const uint8_t* a, int la, const uint8_t* b, int lb) {
+  return lev_token(std::string(reinterpret_cast<const char*>(a), la),
+                   std::string(reinterpret_cast<const char*>(b), lb));
+}
+
+int64_t xo_count_variants_token(const uint8_t* s, int L, int d) {
+  return static_cast<int64_t>(
+      deletion_variants_token(std::string(reinterpret_cast<const char*>(s), L), d).size());
+}
+
+// SymDel over receptors alpha + TOKEN + beta (packed as one string each):
+// steps 1-4 of the self-search with token-respecting variants and distance.
+// Rows (i, j, dist), i < j, dist <= d, sorted.
+void* xo_symdel_paired(const uint8_t* seqs, const int64_t* off, int64_t n, int d) {
+  std::vector<std::string> s(n);
+  for (int64_t i = 0; i < n; ++i) s[i] = seq_at(seqs, off, i);
+  std::vector<std::unordered_set<std::string>> x(n);
+  std::unordered_map<std::string, std::vector<uint32_t>> table;
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] = deletion_variants_token(s[i], d);
+    for (const std::string& v : x[i]) table[v].push_back(static_cast<uint32_t>(i));
+  }
+  std::vector<std::pair<uint32_t, uint32_t>> y;
+  for (int64_t i = 0; i < n; ++i)
+    for (const std::string& v : x[i])
+      for (uint32_t j : table[v]) y.emplace_back(static_cast<uint32_t>(i), j);
+  std::sort(y.begin(), y.end());
+  y.erase(std::unique(y.begin(), y.end()), y.end());
+  std::vector<std::vector<uint32_t>> rows;
+  for (auto& c : y) {
+    if (c.second <= c.first) continue;  // unordered pairs once, no self pairs
+    const int dist = lev_token(s[c.first], s[c.second]);
+    if (dist <= d) rows.push_back({c.first, c.second, (uint32_t)dist});  // paired
+  }
+  sort_unique(rows);
+  return pack(rows, 3);
+}
+
+// Exhaustive paired search over all pairs (the brute-force pin).
+void* xo_bruteforce_paired(const uint8_t* seqs, const int64_t* off, int64_t n, int d) {
+  std::vector<std::string> s(n);
+  for (int64_t i = 0; i < n; ++i) s[i] = seq_at(seqs, off, i);
+  std::vector<std::vector<uint32_t>> rows;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j) {
+      const int dist = lev_token(s[i], s[j]);
+      if (dist <= d)
+        rows.push_back({static_cast<uint32_t>(i), static_cast<uint32_t>(j),
+                        static_cast<uint32_t>(dist)});
+    }
+  return pack(rows, 3);
 }
 
 // TCRdist post-filter over (i, j, dist) rows: keep score <= max_score.

@@ -8,7 +8,8 @@ edit distances, the worked variant count of Sec. 2.1, the special case
 d = 0, Hamming textbook values and lengths, the hand-worked TCRdist scores of
 tests/golden/tcrdist_hand.txt, the self, query, batched and sharded searches
 against exhaustive comparison, the threaded exhaustive query against the
-single-thread one, one sequence's neighbours, the TCRdist filter
+single-thread one, paired chains (hand-worked distances, a variant count and
+SymDel against exhaustive search), one sequence's neighbours, the TCRdist filter
 against the all-pairs scorer, and the within/between partition of the
 batched search.  The unmutated source passes every check.
 """
@@ -77,6 +78,15 @@ MUTANTS = [
     ("sharded search pairs an id with itself",
      "for (size_t b = a + 1; b < kv.second.size(); ++b)",
      "for (size_t b = a; b < kv.second.size(); ++b)"),
+    ("paired variants delete the token", "        if (t[p] == TOKEN) continue;\n", ""),
+    ("paired distance lets the token be substituted",
+     "return (x == TOKEN || y == TOKEN) ? FORBIDDEN : 1;", "return 1;"),
+    ("paired distance lets the token be deleted or inserted",
+     "auto del = [&](char c) { return c == TOKEN ? FORBIDDEN : 1; };",
+     "auto del = [&](char c) { return 1; };"),
+    ("paired threshold strict",
+     "if (dist <= d) rows.push_back({c.first, c.second, (uint32_t)dist});  // paired",
+     "if (dist < d) rows.push_back({c.first, c.second, (uint32_t)dist});  // paired"),
     ("threaded exhaustive query skips the last reference of each range",
      "for (int64_t r = lo; r < hi; ++r) {", "for (int64_t r = lo; r + 1 < hi; ++r) {"),
     ("threaded exhaustive query threshold strict",
@@ -202,6 +212,27 @@ def check_threaded_query_equals_exhaustive():
     assert np.array_equal(oracle.bruteforce_query(rs, ro, qs, qo, 2, threads=3), want)
 
 
+def check_paired():
+    golden = os.path.join(os.path.dirname(__file__), "golden", "paired_hand.txt")
+    for line in open(golden):
+        line = line.split("#")[0].split()
+        if line:
+            assert oracle.lev_token(line[0], line[1]) == int(line[2])
+    assert oracle.count_variants_token("AC|DE", 2) == 11
+    seqs, off = _prefix(300)
+    strs = gen.to_strings(seqs, off)
+    a_s, a_o = gen.from_strings(strs[:150])
+    b_s, b_o = gen.from_strings([s[3:] for s in strs[150:]])
+    for d in (1, 2):
+        want = oracle.bruteforce_paired(a_s, a_o, b_s, b_o, d)
+        assert np.array_equal(oracle.symdel_paired(a_s, a_o, b_s, b_o, d), want)
+    # a receptor set with planted one- and two-edit neighbours
+    a_s, a_o = gen.from_strings(["CASSF", "CASF", "CAS", "CASSF"])
+    b_s, b_o = gen.from_strings(["CAVF", "CAVF", "CAV", "CAIF"])
+    assert oracle.symdel_paired(a_s, a_o, b_s, b_o, 2).tolist() == \
+        [[0, 1, 1], [0, 3, 1], [1, 2, 2], [1, 3, 2]]
+
+
 def check_sharded_equals_exhaustive():
     seqs, off = _prefix(600)
     assert np.array_equal(oracle.symdel_self_sharded(seqs, off, 2, threads=3),
@@ -222,7 +253,7 @@ CHECKS = [check_textbook_distances, check_worked_variant_count, check_hamming,
           check_tcrdist_hand_worked, check_d0_is_duplicate_grouping,
           check_search_equals_exhaustive, check_query_equals_exhaustive,
           check_batched_is_per_repertoire, check_neighbours_of_one_sequence,
-          check_sharded_equals_exhaustive, check_threaded_query_equals_exhaustive,
+          check_sharded_equals_exhaustive, check_threaded_query_equals_exhaustive, check_paired,
           check_tcrdist_filter_and_scorer,
           check_between_and_within_partition]
 

@@ -11,7 +11,11 @@
   n(n-1)/2 pairs at distance 0, d >= every length gives every pair;
 * the bag-of-amino-acids bound of Appendix B on every output pair;
 * hand-worked TCRdist scores (tests/golden/tcrdist_hand.txt) and BLOSUM62
-  consistency checks.
+  consistency checks;
+* paired chains joined by a token no edit may touch (Discussion): hand-worked
+  distances (tests/golden/paired_hand.txt), a BFS over the admissible edits,
+  the split into the two chains' edit distances, variant counts, SymDel
+  against exhaustive search, and the special case of empty second chains.
 """
 import itertools
 import math
@@ -430,3 +434,98 @@ def test_threaded_bruteforce_query_is_the_brute_force(metric):
     for threads in (1, 2, 5, 9):
         assert np.array_equal(
             oracle.bruteforce_query(tiny_s, tiny_o, q_s, q_o, 1, metric, threads=threads), want)
+
+
+# --------------------------------------------------------- paired chains ---
+def test_paired_hand_worked():
+    for line in open(os.path.join(GOLDEN, "paired_hand.txt")):
+        line = line.split("#")[0].split()
+        if line:
+            assert oracle.lev_token(line[0], line[1]) == int(line[2]), line
+
+
+def _token_edits1(s, alphabet):
+    # single edits that leave the token '|' alone: residue insertions,
+    # deletions and substitutions anywhere else
+    out = set()
+    for i in range(len(s) + 1):
+        for c in alphabet:
+            out.add(s[:i] + c + s[i:])
+    for i in range(len(s)):
+        if s[i] == "|":
+            continue
+        out.add(s[:i] + s[i + 1:])
+        for c in alphabet:
+            if c != s[i]:
+                out.add(s[:i] + c + s[i + 1:])
+    return out
+
+
+def test_paired_distance_matches_bfs_over_admissible_edits():
+    # every string within radius 3 of a receptor, by BFS over token-respecting
+    # edits (independent of any DP), has its BFS level as lev_token
+    for s in ["AC|C", "|A", "CA|", "A|CA"]:
+        dist = {s: 0}
+        frontier = {s}
+        for r in range(1, 4):
+            nxt = set()
+            for t in frontier:
+                nxt |= _token_edits1(t, "AC")
+            nxt -= dist.keys()
+            for t in nxt:
+                dist[t] = r
+            frontier = nxt
+        rng = random.Random(len(s))
+        for t in rng.sample(sorted(dist), min(300, len(dist))):
+            assert oracle.lev_token(s, t) == dist[t], (s, t)
+        # strings with one token outside the ball are farther than 3
+        far = ["AAAA|CCCC", "|CCCCA", "CCCCAA|"]
+        for t in far:
+            if t not in dist:
+                assert oracle.lev_token(s, t) > 3
+
+
+def test_paired_distance_is_the_sum_of_chain_distances():
+    rng = random.Random(11)
+    for _ in range(400):
+        a1, b1, a2, b2 = (_rand_strings(rng, 1, "ACD", 0, 6)[0] for _ in range(4))
+        want = oracle.levenshtein(a1, a2) + oracle.levenshtein(b1, b2)
+        assert oracle.lev_token(a1 + "|" + b1, a2 + "|" + b2) == want
+
+
+def test_paired_variant_counts():
+    # the token is never deleted: distinct residues give sum_k C(L, k) variants
+    # over the residues of both chains (Sec. 2.1's 56 for L = 10, d = 2)
+    assert oracle.count_variants_token("ACDEFGHIKL|", 2) == 56
+    assert oracle.count_variants_token("ACDEF|GHIKL", 2) == 56
+    assert oracle.count_variants_token("AC|DE", 2) == 1 + 4 + 6
+    assert oracle.count_variants_token("|", 3) == 1
+
+
+def _paired_set(rng, n, alphabet, lmax):
+    a = _rand_strings(rng, n, alphabet, 0, lmax)
+    b = _rand_strings(rng, n, alphabet, 0, lmax)
+    sa, oa = gen.from_strings(a)
+    sb, ob = gen.from_strings(b)
+    return sa, oa, sb, ob
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_paired_symdel_equals_bruteforce(d):
+    rng = random.Random(30 + d)
+    for alphabet, lmax in [("AC", 5), ("ACDE", 7)]:
+        sa, oa, sb, ob = _paired_set(rng, 150, alphabet, lmax)
+        want = oracle.bruteforce_paired(sa, oa, sb, ob, d)
+        got = oracle.symdel_paired(sa, oa, sb, ob, d)
+        assert np.array_equal(got, want)
+        if d >= 1:
+            assert want.shape[0] > 0
+
+
+def test_paired_with_empty_second_chains_is_the_single_chain_search():
+    seqs, off = gen.workload(gen.SELF_1M, 800)
+    empty = np.zeros(0, np.uint8)
+    zero = np.zeros(off.size, np.int64)
+    for d in (1, 2):
+        assert np.array_equal(oracle.symdel_paired(seqs, off, empty, zero, d),
+                              oracle.bruteforce_self(seqs, off, d))
