@@ -76,25 +76,28 @@ def _draw_residues(rng: np.random.Generator, shape) -> np.ndarray:
     return AA_BYTES[idx]
 
 
-def _draw_lengths(rng: np.random.Generator, n: int) -> np.ndarray:
+def _draw_lengths(rng: np.random.Generator, n: int, mean: float = LEN_MEAN, sd: float = LEN_SD,
+                  lo: int = LEN_MIN, hi: int = LEN_MAX) -> np.ndarray:
     out = np.empty(n, dtype=np.int64)
     todo = np.arange(n)
     while todo.size:
-        v = np.rint(rng.normal(LEN_MEAN, LEN_SD, size=todo.size)).astype(np.int64)
-        ok = (v >= LEN_MIN) & (v <= LEN_MAX)
+        v = np.rint(rng.normal(mean, sd, size=todo.size)).astype(np.int64)
+        ok = (v >= lo) & (v <= hi)
         out[todo[ok]] = v[ok]
         todo = todo[~ok]
     return out
 
 
-def _fresh(rng: np.random.Generator, n: int):
-    """n fresh sequences as a (n, WIDTH) ASCII matrix (0-padded) and lengths."""
+def _fresh(rng: np.random.Generator, n: int, prefix: bytes = b"CAS", lengths=None):
+    """n fresh sequences as a (n, WIDTH) ASCII matrix (0-padded) and lengths.
+    `lengths` = (mean, sd, lo, hi) of the length law (default: the CDR3-beta
+    law above); `prefix` = the conserved first residues."""
     mats, lens = [], []
     for start in range(0, n, _CHUNK):
         m = min(_CHUNK, n - start)
-        L = _draw_lengths(rng, m)
+        L = _draw_lengths(rng, m) if lengths is None else _draw_lengths(rng, m, *lengths)
         M = _draw_residues(rng, (m, WIDTH))
-        for pos, ch in enumerate(b"CAS"):
+        for pos, ch in enumerate(prefix):
             keep = rng.random(m) < FLANK_P
             M[keep, pos] = ch
         last = rng.random(m) < FLANK_P
@@ -276,3 +279,41 @@ def served(ref_n: int = SERVE_REF_N, n_req: int = SERVE_REQUESTS, max_req: int =
         s, o = _pack(Mq[perm], Lq[perm])
         reqs.append(Request(r, float(arrivals[r]), s, o))
     return ref_seqs, ref_off, reqs
+
+
+# ---------------------------------------------------------- paired chains ---
+# CDR3-alpha-like first chains: length ~ N(13.5, 2^2) on [7, 21], conserved
+# 'CAV' start and final F with probability 0.9 each (builder-chosen, like
+# FREQ); the second chain follows the CDR3-beta law above.
+ALPHA_LENGTHS = (13.5, 2.0, 7, 21)
+ALPHA_PREFIX = b"CAV"
+
+
+def paired(n: int, seed: int, derived_frac: float = 0.15, dup_frac: float = 0.01):
+    """n receptors (alpha chain, beta chain).  A derived receptor copies both
+    chains of an earlier fresh one and gets 1 or 2 edits in all, each in the
+    alpha or the beta chain with equal probability; a duplicate copies both
+    chains.  Returns (a_seqs, a_offsets, b_seqs, b_offsets)."""
+    rng = np.random.default_rng(seed)
+    Ma, La = _fresh(rng, n, ALPHA_PREFIX, ALPHA_LENGTHS)
+    Mb, Lb = _fresh(rng, n)
+    if n:
+        kind = rng.choice(3, size=n, p=[1.0 - derived_frac - dup_frac, derived_frac, dup_frac])
+        kind[0] = 0
+        fresh_idx = np.flatnonzero(kind == 0)
+        other = np.flatnonzero(kind != 0)
+        if other.size:
+            n_before = np.searchsorted(fresh_idx, other)
+            src = fresh_idx[np.floor(rng.random(other.size) * n_before).astype(np.int64)]
+            Ma[other], La[other] = Ma[src], La[src]
+            Mb[other], Lb[other] = Mb[src], Lb[src]
+            der = other[kind[other] == 1]
+            total = 1 + (rng.random(der.size) < 0.5)
+            in_a = rng.binomial(total, 0.5)
+            edits_a = np.zeros(n, dtype=np.int64)
+            edits_b = np.zeros(n, dtype=np.int64)
+            edits_a[der] = in_a
+            edits_b[der] = total - in_a
+            mutate(rng, Ma, La, edits_a)
+            mutate(rng, Mb, Lb, edits_b)
+    return _pack(Ma, La) + _pack(Mb, Lb)

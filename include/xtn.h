@@ -158,6 +158,25 @@ XTN_API int xtn_search_between(const uint8_t* seqs, const int64_t* offsets, int6
                                xtn_triple* out, int64_t cap, int64_t* n_out, xtn_stream_t stream);
 
 /*
+ * Paired-chain self-search (Discussion: the CDR3s of both chains joined by a
+ * non-deletable token).  Receptor k is the pair (alpha_k, beta_k): alpha_k
+ * delimited by a_offsets[k] .. a_offsets[k+1] in a_seqs, beta_k by b_offsets
+ * in b_seqs (both offset arrays have n+1 entries; either chain may be empty;
+ * each at most XTN_MAX_LEN residues).  Each receptor stands for the string
+ * alpha + token + beta whose deletion variants delete up to d residues and
+ * never the token; the distance of two receptors is the edit distance of
+ * those strings with the token never deleted, inserted or substituted, which
+ * equals Lev(alpha_i, alpha_j) + Lev(beta_i, beta_j).  Rows are {i, j, dist}
+ * with i < j and dist <= d, sorted by (i, j).  0 <= d <= 2.
+ * Other arguments as xtn_search_self (one repertoire).  Errors: as
+ * xtn_search_self; INVALID_ARG for d > 2 or a NULL b_offsets; TOO_LARGE
+ * for 2^32 variant records or candidate pairs or more (no search in passes).
+ */
+XTN_API int xtn_search_paired(const uint8_t* a_seqs, const int64_t* a_offsets,
+                              const uint8_t* b_seqs, const int64_t* b_offsets, int64_t n, int d,
+                              xtn_triple* out, int64_t cap, int64_t* n_out, xtn_stream_t stream);
+
+/*
  * The self-search in passes, for inputs whose variant records do not fit the
  * device at once (Sec. 2.3, "Overcoming memory bottlenecks"; Appendix A,
  * XTNeighbor-streaming).  A first expansion only counts the records of each
@@ -216,6 +235,21 @@ XTN_API int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_
 XTN_API int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out,
                      xtn_stream_t stream);
+
+/*
+ * Scratch estimate of a query search, for admission control of query
+ * batches: *bytes receives the device bytes xtn_search_query (or its Hamming
+ * variant) takes for n_q queries with these offsets (a host pointer, n_q+1
+ * entries; the letters are not needed), counting host input and output
+ * buffers.  The part set by the queries' lengths is an upper bound (every
+ * deletion subset of at most d positions); the candidate part is estimated
+ * from the candidates per query variant this index has produced in the
+ * searches so far (before any: its mean number of records per variant
+ * fingerprint), with a margin of 1.5x.  The call only reads host memory.
+ * Errors: INVALID_ARG, SEQ_TOO_LONG.
+ */
+XTN_API int xtn_search_query_scratch(const xtn_index* idx, const int64_t* q_offsets, int64_t n_q,
+                                     int64_t* bytes);
 
 /*
  * The Hamming variant of the query search (Results, comparison with
@@ -384,7 +418,7 @@ XTN_API int xtn_set_wait_limit(int64_t polls);
  * into buf (NUL-terminated, truncated to buf_len); it returns the number of
  * lines, and clears the records.  Enabling costs two event records per launch.
  * Host-side spans are reported the same way, with zero bytes and wall-clock
- * milliseconds: host_call_search_self / _between / _query /
+ * milliseconds: host_call_search_self / _between / _paired / _query /
  * _query_hamming (the whole call),
  * host_scratch_alloc (each scratch allocation outside the cache) and
  * host_stream_wait (each wait for the stream to drain).

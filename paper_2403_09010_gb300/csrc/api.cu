@@ -413,6 +413,11 @@ struct Encoded {
   uint32_t* eqprev = nullptr;
   uint64_t* rec_off = nullptr;
   uint64_t n_rec = 0;
+  // paired receptors: the second chains (keys, lens, eqprev above are the
+  // first chains); null for one chain
+  Key128* keys_b = nullptr;
+  uint8_t* lens_b = nullptr;
+  uint32_t* eq_b = nullptr;
 };
 
 // allow_large: return the count even when it is 2^32 or more (the caller
@@ -440,6 +445,39 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
   if (h.err) return map_device_err(h.err);
   e->n_rec = h.n_rec;
   if (!allow_large && h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
+  return XTN_OK;
+}
+
+// Paired receptors: both chains encoded, the canonical variant counts of the
+// joined strings (the token never deleted) and their record offsets.
+int encode_and_count_paired(const DevSeqs& a, const DevSeqs& b, int d, Arena& ar, uint32_t* err,
+                            cudaStream_t s, Encoded* e) {
+  const int64_t n = a.n;
+  e->keys = ar.get<Key128>(n);
+  e->lens = ar.get<uint8_t>(n);
+  e->eqprev = ar.get<uint32_t>(n);
+  e->keys_b = ar.get<Key128>(n);
+  e->lens_b = ar.get<uint8_t>(n);
+  e->eq_b = ar.get<uint32_t>(n);
+  uint32_t* vcount = ar.get<uint32_t>(n);
+  e->rec_off = ar.get<uint64_t>(n + 1);
+  uint64_t* status = ar.get<uint64_t>(scan_status_bytes(n) / 8 + 1);
+  XTN_ALLOC_OK(ar);
+  launch_encode(a.seqs, a.off, n, d, e->keys, e->lens, e->eqprev, vcount, err, s);
+  launch_encode(b.seqs, b.off, n, d, e->keys_b, e->lens_b, e->eq_b, vcount, err, s);
+  launch_paired_counts(e->lens, e->eqprev, e->lens_b, e->eq_b, n, d, vcount, s);
+  launch_scan_counts(vcount, n, e->rec_off, status, err, s);
+  XTN_CK(cudaGetLastError());
+  struct {
+    uint64_t n_rec;
+    uint32_t err;
+  } h{0, 0};
+  XTN_CK(cudaMemcpyAsync(&h.n_rec, e->rec_off + n, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(host_sync(s));
+  if (h.err) return map_device_err(h.err);
+  e->n_rec = h.n_rec;
+  if (h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
   return XTN_OK;
 }
 
@@ -491,15 +529,24 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
                        uint32_t* hist, uint64_t* digit_base, uint64_t* status, int cfg,
                        int hist_mode, int mode, const GroupScratch& gs, int sms, uint32_t* err,
                        cudaStream_t s, const uint64_t* n_rec_dev, uint64_t** sorted,
-                       const BinSel* sel = nullptr) {
+                       const BinSel* sel = nullptr, const Encoded* paired = nullptr) {
+  // the expansion: one chain, or paired receptors (no bin selection)
+  auto expand = [&](int hist_lo, int hist_hi) {
+    if (paired)
+      launch_expand_paired(paired->keys, paired->lens, paired->eqprev, paired->keys_b,
+                           paired->lens_b, paired->eq_b, rec_off, n, d, id_bits, A, rec_cap, hist,
+                           hist_lo, hist_hi, sms, err, s);
+    else
+      launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, hist_lo,
+                    hist_hi, sms, err, s, sel);
+  };
   if (mode == 1) {
     const bool in_passes = hist_mode == 1;
-    launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, lo,
-                  in_passes ? std::min(64, lo + 8) : 64, sms, err, s, sel);
+    expand(lo, in_passes ? std::min(64, lo + 8) : 64);
     XTN_CK(cudaGetLastError());
     XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
                              sorted, "k_onesweep_records", s, in_passes, n_rec_dev, nullptr,
-                             onesweep_unstable_config()));
+                             onesweep_unstable_config(cfg)));
     if (gs.flags) {
       XTN_CK(cudaMemsetAsync(gs.gstatus, 0, group_status_bytes((int64_t)rec_cap), s));
       launch_group_flags(*sorted, (int64_t)rec_cap, n_rec_dev, lo, gs.flags, gs.gstatus, s);
@@ -512,13 +559,12 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
   const bool in_passes = hist_mode == 1 && g.G > 8;
   if (g.G > 0)
     XTN_CK(cudaMemsetAsync(gs.bucket_start, 0xFF, ((size_t)1 << g.G) * 8, s));
-  launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, glo,
-                g.G == 0 ? glo : (in_passes ? glo + 8 : 64), sms, err, s, sel);
+  expand(glo, g.G == 0 ? glo : (in_passes ? glo + 8 : 64));
   XTN_CK(cudaGetLastError());
   uint64_t* X = A;
   XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, glo, 64, hist, digit_base, status, cfg, err,
                            &X, "k_onesweep_records", s, in_passes, n_rec_dev, gs.bucket_start,
-                           onesweep_unstable_config()));
+                           onesweep_unstable_config(cfg)));
   uint64_t* Y = X == A ? B : A;
   uint64_t* tile_counts = nullptr;
   if (gs.flags) {
@@ -568,7 +614,8 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
   uint64_t* sorted = nullptr;
   XTN_CK(expand_sort_launch(e.keys, e.lens, e.eqprev, e.rec_off, n, d, seq_rep, out->id_bits, A,
                             B, n_rec, lo, hist, digit_base, status, cfg, g_record_hist.load(), mode,
-                            gs, sms, err, s, nullptr, &sorted));
+                            gs, sms, err, s, nullptr, &sorted, nullptr,
+                            e.keys_b ? &e : nullptr));
   out->flags = gs.flags;
   out->gstatus = gs.gstatus;
   out->rec = sorted;
@@ -603,13 +650,14 @@ int launch_sort_unique(uint64_t* surv, uint64_t* tmp, uint64_t cap, const uint64
                        uint64_t* status, const uint32_t* peq_i, const uint8_t* lens_i,
                        uint64_t n_i, const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                        int metric, xtn_triple* rows, int64_t row_cap, uint32_t* err,
-                       uint64_t* n_rows, cudaStream_t s, int cfg) {
+                       uint64_t* n_rows, cudaStream_t s, int cfg,
+                       const SecondChain& sc = SecondChain()) {
   uint64_t* sorted = nullptr;
   XTN_CK(radix_sort_passes(surv, tmp, (int64_t)cap, 0, (int)pair_bits, hist, digit_base, status,
                            cfg, err, &sorted, "k_onesweep_pairs", s, false, n_dev, nullptr,
-                           onesweep_unstable_config()));
+                           onesweep_unstable_config(cfg)));
   launch_unique_finalize(sorted, (int64_t)cap, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
-                         n_j, metric, rows, row_cap, status, err, n_rows, s);
+                         n_j, metric, rows, row_cap, status, err, n_rows, s, sc);
   XTN_CK(cudaGetLastError());
   return XTN_OK;
 }
@@ -618,15 +666,16 @@ int launch_back(const BackStage& b, uint64_t cand_cap, const uint64_t* n_cand_de
                 uint32_t pair_bits, uint32_t j_bits, const uint32_t* peq_i, const uint8_t* lens_i,
                 uint64_t n_i, const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                 const uint32_t* seq_rep, int self_mode, int d, xtn_triple* rows, int64_t row_cap,
-                int sms, uint32_t* err, cudaStream_t s, int cfg, int metric = 0) {
+                int sms, uint32_t* err, cudaStream_t s, int cfg, int metric = 0,
+                const SecondChain& sc = SecondChain()) {
   XTN_CK(cudaMemsetAsync(b.hist, 0, MAX_PASSES * RADIX * 4, s));
   XTN_CK(cudaMemsetAsync(b.counters, 0, 16, s));
   launch_verify_candidates(b.P1, cand_cap, n_cand_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
                            n_j, seq_rep, self_mode, d, metric, b.P2, cand_cap, b.counters, b.hist,
-                           (int)pair_bits, sms, err, s);
+                           (int)pair_bits, sms, err, s, sc);
   return launch_sort_unique(b.P2, b.P1, cand_cap, b.counters, pair_bits, j_bits, b.hist,
                             b.digit_base, b.status, peq_i, lens_i, n_i, keys_j, lens_j, n_j, metric,
-                            rows, row_cap, err, b.counters + 1, s, cfg);
+                            rows, row_cap, err, b.counters + 1, s, cfg, sc);
 }
 
 // Result rows go to `out` directly when it is device memory; otherwise into
@@ -972,13 +1021,20 @@ int search_stream_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, i
 // last step filters by Hamming distance).  between: report the pairs between
 // different repertoires instead of those within one; the variants then carry
 // no repertoire salt, so that equal variants of different repertoires meet.
+// b_seqs / b_offsets (paired receptors, the paired-chain search): the second
+// chains; seqs / offsets then hold the first chains, d <= 2, one repertoire,
+// and the last step takes metric 2 (the sum of the two chains' distances).
 int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int d,
                      const int64_t* rep_offsets, int64_t n_rep, xtn_triple* out, int64_t cap,
                      int64_t* n_out, cudaStream_t s, int mode = -1, int metric = 0,
-                     bool between = false) {
+                     bool between = false, const uint8_t* b_seqs = nullptr,
+                     const int64_t* b_offsets = nullptr) {
   if (!n_out) return XTN_ERR_INVALID_ARG;
   *n_out = 0;
   if (n < 0 || d < 0 || d > XTN_MAX_D || cap < 0 || !offsets) return XTN_ERR_INVALID_ARG;
+  const bool paired = b_offsets != nullptr;
+  if (paired && (d > 2 || rep_offsets)) return XTN_ERR_INVALID_ARG;
+  if (paired) metric = 2;
   if (n >= (1ll << 32)) return XTN_ERR_TOO_LARGE;
   if (rep_offsets && n_rep < 1) return XTN_ERR_INVALID_ARG;
   if (between && !rep_offsets) return XTN_ERR_INVALID_ARG;
@@ -992,9 +1048,13 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   XTN_ALLOC_OK(ar);
   XTN_CK(init_err(err, s));
   XTN_CK(cudaMemsetAsync(counters, 0, 32, s));
-  DevSeqs in;
+  DevSeqs in, in_b;
   rc = stage_seqs(seqs, offsets, n, ar, s, &in);
   if (rc) return rc;
+  if (paired) {
+    rc = stage_seqs(b_seqs, b_offsets, n, ar, s, &in_b);
+    if (rc) return rc;
+  }
   uint32_t* seq_rep = nullptr;
   if (rep_offsets) {
     seq_rep = ar.get<uint32_t>(n);
@@ -1005,8 +1065,9 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
 
   // front: encode (read back the record count), expand, sort, group, offsets
   Encoded e;
-  rc = encode_and_count(in, d, ar, err, s, &e);
-  if (rc == XTN_ERR_TOO_LARGE) {  // 2^32 records or more: search in passes
+  rc = paired ? encode_and_count_paired(in, in_b, d, ar, err, s, &e)
+              : encode_and_count(in, d, ar, err, s, &e);
+  if (rc == XTN_ERR_TOO_LARGE && !paired) {  // 2^32 records or more: search in passes
     ar.release();
     return search_stream_impl(seqs, offsets, n, d, rep_offsets, n_rep, metric, between, 0, out,
                               cap, n_out, nullptr, s);
@@ -1043,7 +1104,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     if (h.err == DERR_CAPACITY) {  // candidate overflow alone: regroup sized exactly
       ar.release();
       return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
-                              metric, between);
+                              metric, between, b_seqs, b_offsets);
     }
     if (h.err) return map_device_err(h.err);
     flagged = h.large > 0;
@@ -1062,6 +1123,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   const uint64_t n_pairs = h.direct + h.pairs;
   if (n_pairs == 0) return XTN_OK;
   if (n_pairs >= (1ull << 32)) {  // candidate words past 2^32: search in passes
+    if (paired) return XTN_ERR_TOO_LARGE;
     ar.release();
     return search_stream_impl(seqs, offsets, n, d, rep_offsets, n_rep, metric, between, 0, out,
                               cap, n_out, nullptr, s);
@@ -1069,7 +1131,7 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   if (mode != 1 && n_pairs > direct.cand_cap) {
     ar.release();
     return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
-                            metric, between);
+                            metric, between, b_seqs, b_offsets);
   }
 
   // back: the remaining candidates, verify, sort survivors, dedup
@@ -1082,17 +1144,26 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   b.status = ar.get<uint64_t>(back_status_bytes(n_pairs, cfg_pairs) / 8 + 1);
   b.counters = ar.get<uint64_t>(2);
   uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
+  uint32_t* peq_b = paired ? ar.get<uint32_t>((size_t)n * PEQ_STRIDE) : nullptr;
   XTN_ALLOC_OK(ar);
   if (h.pairs)
     launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)h.groups, nullptr, h.pairs,
                       so.id_bits, b.P1 + h.direct, nullptr, nullptr, sms, err, s);
   launch_peq(e.keys, e.lens, n, peq, s);
+  SecondChain sc;
+  if (paired) {
+    launch_peq(e.keys_b, e.lens_b, n, peq_b, s);
+    sc.peq_i = peq_b;
+    sc.lens_i = e.lens_b;
+    sc.keys_j = e.keys_b;
+    sc.lens_j = e.lens_b;
+  }
   OutRows o;
   rc = prepare_out(out, cap, n_pairs, ar, &o);
   if (rc) return rc;
   rc = launch_back(b, n_pairs, nullptr, 2 * so.id_bits, so.id_bits, peq, e.lens, n, e.keys, e.lens,
                    n, seq_rep, between ? 2 : 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs,
-                   metric);
+                   metric, sc);
   if (rc) return rc;
   XTN_CK(cudaMemcpyAsync(&h.pairs, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
   XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
@@ -1120,6 +1191,9 @@ struct xtn_index {
   uint64_t* rec = nullptr;
   uint32_t* dir = nullptr;
   int64_t bytes = 0;
+  uint64_t n_groups = 0;  // distinct variant fingerprints in the index
+  // candidates and query variants of the searches so far (scratch estimates)
+  mutable std::atomic<uint64_t> seen_cand{0}, seen_qv{0};
 };
 
 namespace xtn {
@@ -1155,7 +1229,14 @@ int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   idx->n_rec = e.n_rec;
   idx->id_bits = so.id_bits;
   idx->hs = so.hs;
-  idx->dir_bits = std::min(20, so.hs);
+  // about one directory entry per 4 records (at most 2^28 entries, 1 GiB):
+  // a lookup's range then spans a cache line or two instead of a binary
+  // search through hundreds of records
+  {
+    int db = 10;
+    while (db < 28 && db < so.hs && ((uint64_t)1 << (db + 2)) < e.n_rec) ++db;
+    idx->dir_bits = db;
+  }
   const size_t b_keys = n * sizeof(Key128), b_lens = n, b_rec = e.n_rec * 8,
                b_dir = ((size_t(1) << idx->dir_bits) + 1) * 4;
   bool ok = cudaMalloc(&idx->keys, b_keys) == cudaSuccess &&
@@ -1171,16 +1252,28 @@ int index_build_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   bool cp = cudaMemcpyAsync(idx->keys, e.keys, b_keys, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync(idx->lens, e.lens, b_lens, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
             cudaMemcpyAsync(idx->rec, so.rec, b_rec, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
-  if (cp) launch_build_dir(idx->rec, idx->n_rec, idx->dir_bits, idx->dir, s);
-  uint32_t herr = 0;
-  if (!cp || cudaGetLastError() != cudaSuccess || read_back(&herr, err, 1, s) != XTN_OK) {
+  uint64_t* groups = ar.get<uint64_t>(1);
+  if (!groups) cp = false;
+  if (cp) cp = cudaMemsetAsync(groups, 0, 8, s) == cudaSuccess;
+  if (cp)
+    launch_build_dir(idx->rec, idx->n_rec, idx->dir_bits, 64 - idx->hs, idx->dir, groups, s);
+  struct {
+    uint64_t groups;
+    uint32_t err;
+  } h{0, 0};
+  if (!cp || cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&h.groups, groups, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      host_sync(s) != cudaSuccess) {
+    cudaGetLastError();
     xtn_index_free(idx);
     return XTN_ERR_CUDA;
   }
-  if (herr) {
+  if (h.err) {
     xtn_index_free(idx);
-    return map_device_err(herr);
+    return map_device_err(h.err);
   }
+  idx->n_groups = h.groups;
   *out = idx;
   return XTN_OK;
 }
@@ -1221,13 +1314,17 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
                       sms, err, s);
   launch_scan_counts(qv_cnt, (int64_t)n_qv, cand_off, status, err, s);
   XTN_CK(cudaGetLastError());
-  uint64_t n_cand = 0;
-  rc = read_back(&n_cand, cand_off + n_qv, 1, s);
-  if (rc) return rc;
-  uint32_t herr = 0;
-  rc = read_back(&herr, err, 1, s);
-  if (rc) return rc;
-  if (herr) return map_device_err(herr);
+  struct {
+    uint64_t cand;
+    uint32_t err;
+  } hc{0, 0};
+  XTN_CK(cudaMemcpyAsync(&hc.cand, cand_off + n_qv, 8, cudaMemcpyDeviceToHost, s));
+  XTN_CK(cudaMemcpyAsync(&hc.err, err, 4, cudaMemcpyDeviceToHost, s));
+  XTN_CK(host_sync(s));
+  if (hc.err) return map_device_err(hc.err);
+  const uint64_t n_cand = hc.cand;
+  idx->seen_cand += n_cand;
+  idx->seen_qv += n_qv;
   if (n_cand == 0) return XTN_OK;
   if (n_cand >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
   const uint32_t q_bits = bits_for((uint64_t)n_q);
@@ -1622,12 +1719,64 @@ int xtn_index_info(const xtn_index* idx, int64_t* n, int* d, int64_t* n_records,
   return XTN_OK;
 }
 
+int xtn_search_paired(const uint8_t* a_seqs, const int64_t* a_offsets, const uint8_t* b_seqs,
+                      const int64_t* b_offsets, int64_t n, int d, xtn_triple* out, int64_t cap,
+                      int64_t* n_out, xtn_stream_t stream) {
+  xtn::HostSpan span("host_call_search_paired");
+  if (!b_offsets) {
+    if (n_out) *n_out = 0;
+    return XTN_ERR_INVALID_ARG;
+  }
+  return xtn::search_self_impl(a_seqs, a_offsets, n, d, nullptr, 0, out, cap, n_out,
+                               reinterpret_cast<cudaStream_t>(stream), -1, 2, false, b_seqs,
+                               b_offsets);
+}
+
 int xtn_search_query(const xtn_index* idx, const uint8_t* q_seqs, const int64_t* q_offsets,
                      int64_t n_q, xtn_triple* out, int64_t cap, int64_t* n_out,
                      xtn_stream_t stream) {
   xtn::HostSpan span("host_call_search_query");
   return xtn::search_query_impl(idx, q_seqs, q_offsets, n_q, out, cap, n_out,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+int xtn_search_query_scratch(const xtn_index* idx, const int64_t* q_offsets, int64_t n_q,
+                             int64_t* bytes) {
+  using namespace xtn;
+  if (!bytes) return XTN_ERR_INVALID_ARG;
+  *bytes = 0;
+  if (!idx || n_q < 0 || (n_q > 0 && !q_offsets)) return XTN_ERR_INVALID_ARG;
+  if (n_q == 0) return XTN_OK;
+  if (q_offsets[0] != 0) return XTN_ERR_INVALID_ARG;
+  // query variants: every deletion subset of <= d positions (the canonical
+  // ones the search expands are at most that many)
+  uint64_t n_qv = 0;
+  for (int64_t q = 0; q < n_q; ++q) {
+    const int64_t L = q_offsets[q + 1] - q_offsets[q];
+    if (L < 0) return XTN_ERR_INVALID_ARG;
+    if (L > XTN_MAX_LEN) return XTN_ERR_SEQ_TOO_LONG;
+    n_qv += variant_count((uint32_t)L, (uint32_t)idx->d);
+  }
+  const uint64_t letters = (uint64_t)q_offsets[n_q];
+  // candidates per query variant: what this index has given so far, else
+  // its mean group size; 1.5x margin
+  const uint64_t sc = idx->seen_cand.load(), sq = idx->seen_qv.load();
+  double rate = sq ? (double)sc / (double)sq
+                   : (idx->n_groups ? (double)idx->n_rec / (double)idx->n_groups : 1.0);
+  const uint64_t n_cand = (uint64_t)(1.5 * rate * (double)n_qv) + 1024;
+  const int cfg = g_cfg_pairs.load();
+  const uint64_t n = (uint64_t)n_q;
+  const uint64_t per_buffer = 64 + 256;  // arena spare bytes and alignment
+  uint64_t b = 0;
+  b += 16 + letters + 8 * (n + 1);                                   // errors, staging
+  b += n * (16 + 1 + 4 + 4) + 8 * (n + 1) + scan_status_bytes((int64_t)n);  // encode
+  b += n_qv * 12 + 8 * (n_qv + 1) + scan_status_bytes((int64_t)n_qv);      // lookup
+  b += 16 * (n_cand + 8) + MAX_PASSES * RADIX * 12 + 16;             // candidate words
+  b += back_status_bytes(n_cand, cfg) + n * 4 * PEQ_STRIDE;          // sort, match vectors
+  b += 12 * n_cand;                                                  // rows for host output
+  b += 24 * per_buffer;
+  *bytes = (int64_t)b;
+  return XTN_OK;
 }
 
 int xtn_search_query_hamming(const xtn_index* idx, const uint8_t* q_seqs,

@@ -4,7 +4,9 @@
 //
 //   k_build_dir    : dir[t] = first index record whose top `dir_bits`
 //                    fingerprint bits are >= t, so a lookup starts from a
-//                    range of ~n_rec / 2^dir_bits records instead of all.
+//                    range of ~n_rec / 2^dir_bits records (a few, with the
+//                    directory sized at about one entry per 4 records)
+//                    instead of all.
 //   k_query_lookup : one warp per query, one lane per deletion variant (same
 //                    order as the self-search expansion): binary search of the
 //                    variant's fingerprint group inside its directory range;
@@ -20,28 +22,35 @@
 
 namespace xtn {
 
+// One thread per sorted position p in [0, n_rec]: the directory entries t
+// in (top(rec[p-1]), top(rec[p])] all start at p (top(rec[-1]) = -1,
+// top(rec[n_rec]) = 2^dir_bits), so every entry is written exactly once in
+// one coalesced pass over the records.
+// The same pass counts the groups (positions whose group key, the bits from
+// gshift up, differs from the previous record's) into *n_groups.
 __global__ void k_build_dir(const uint64_t* __restrict__ rec, uint64_t n_rec, int dir_bits,
-                            uint32_t* __restrict__ dir) {
-  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t n_dir = 1ull << dir_bits;
-  if (t > n_dir) return;
-  if (t == n_dir) {
-    dir[t] = (uint32_t)n_rec;
-    return;
+                            int gshift, uint32_t* __restrict__ dir,
+                            unsigned long long* __restrict__ n_groups) {
+  const int64_t n_dir = 1ll << dir_bits;
+  uint32_t heads = 0;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= n_rec;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = p == 0 ? -1 : (int64_t)(rec[p - 1] >> (64 - dir_bits));
+    const int64_t cur = p == n_rec ? n_dir : (int64_t)(rec[p] >> (64 - dir_bits));
+    for (int64_t t = prev + 1; t <= cur && t <= n_dir; ++t) dir[t] = (uint32_t)p;
+    if (p < n_rec && (p == 0 || (rec[p] >> gshift) != (rec[p - 1] >> gshift))) ++heads;
   }
-  uint64_t lo = 0, hi = n_rec;  // first position with top bits >= t
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if ((rec[mid] >> (64 - dir_bits)) < t) lo = mid + 1; else hi = mid;
-  }
-  dir[t] = (uint32_t)lo;
+  heads = (uint32_t)__reduce_add_sync(FULL_MASK, heads);
+  if (lane_id() == 0 && heads) atomicAdd(n_groups, (unsigned long long)heads);
 }
 
-void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_t* dir,
-                      cudaStream_t s) {
-  const uint64_t n = (1ull << dir_bits) + 1;
-  prof_begin(s, "k_build_dir", (double)n * 4.0);
-  k_build_dir<<<div_up_u32(n, 256), 256, 0, s>>>(rec, n_rec, dir_bits, dir);
+void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, int gshift,
+                      uint32_t* dir, uint64_t* n_groups, cudaStream_t s) {
+  const uint64_t n_dir = (1ull << dir_bits) + 1;
+  prof_begin(s, "k_build_dir", (double)n_rec * 8.0 + (double)n_dir * 4.0);
+  const uint32_t blocks = (uint32_t)std::min<uint64_t>((n_rec + 256) / 256, 152ull * 32);
+  k_build_dir<<<blocks, 256, 0, s>>>(rec, n_rec, dir_bits, gshift, dir,
+                                     reinterpret_cast<unsigned long long*>(n_groups));
   prof_end(s);
 }
 

@@ -103,6 +103,25 @@ __device__ __forceinline__ uint32_t pair_distance(int metric, int d,
   return edit_distance(peq, m, t, n);
 }
 
+// Distance of candidate (i, j) for the last step: pair_distance of the one
+// chain, or for paired receptors (metric 2) the sum of both chains' edit
+// distances (a pair with |dLa| + |dLb| > d gets d + 1).  d >= XTN_MAX_LEN
+// asks for the exact distance.
+__device__ __forceinline__ uint32_t cand_distance(int metric, int d,
+                                                  const uint32_t* __restrict__ peq_i,
+                                                  const uint8_t* __restrict__ lens_i,
+                                                  const Key128* __restrict__ keys_j,
+                                                  const uint8_t* __restrict__ lens_j,
+                                                  const SecondChain& sc, uint64_t i, uint64_t j) {
+  if (metric != 2)
+    return pair_distance(metric, d, peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]);
+  const uint32_t ma = lens_i[i], na = lens_j[j], mb = sc.lens_i[i], nb = sc.lens_j[j];
+  const uint32_t gap = (ma > na ? ma - na : na - ma) + (mb > nb ? mb - nb : nb - mb);
+  if (gap > (uint32_t)d) return (uint32_t)d + 1u;
+  return edit_distance(peq_i + i * PEQ_STRIDE, ma, keys_j[j], na) +
+         edit_distance(sc.peq_i + i * PEQ_STRIDE, mb, sc.keys_j[j], nb);
+}
+
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_w, uint32_t& excl) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -134,7 +153,7 @@ __global__ void __launch_bounds__(256)
                         const uint32_t* __restrict__ seq_rep, int self_mode, int d, int metric,
                         uint64_t* __restrict__ surv, uint64_t surv_cap,
                         unsigned long long* __restrict__ n_surv, uint32_t* __restrict__ hist,
-                        int hist_hi, uint32_t* __restrict__ err) {
+                        int hist_hi, uint32_t* __restrict__ err, SecondChain sc) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   const int passes = (hist_hi + 7) / 8;
   for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
@@ -157,8 +176,7 @@ __global__ void __launch_bounds__(256)
       if (self_mode) ok = ok && i != j;
       if (ok && seq_rep) ok = (seq_rep[i] == seq_rep[j]) == (self_mode != 2);
       if (ok)
-        ok = pair_distance(metric, d, peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j], lens_j[j]) <=
-             (uint32_t)d;
+        ok = cand_distance(metric, d, peq_i, lens_i, keys_j, lens_j, sc, i, j) <= (uint32_t)d;
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
     if (bal) {
@@ -192,13 +210,14 @@ void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* 
                               const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                               const uint32_t* seq_rep, int self_mode, int d, int metric,
                               uint64_t* surv, uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist,
-                              int hist_hi, int sms, uint32_t* err, cudaStream_t s) {
+                              int hist_hi, int sms, uint32_t* err, cudaStream_t s,
+                              const SecondChain& sc) {
   if (n == 0) return;
   const int blocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
   prof_begin(s, "k_verify_candidates", (double)n * (8.0 + 2 * 17.0 + 4.0 * 4));
   k_verify_candidates<<<blocks, 256, 0, s>>>(
       cand, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, seq_rep, self_mode, d, metric, surv,
-      surv_cap, reinterpret_cast<unsigned long long*>(n_surv), hist, hist_hi, err);
+      surv_cap, reinterpret_cast<unsigned long long*>(n_surv), hist, hist_hi, err, sc);
   prof_end(s);
 }
 
@@ -210,7 +229,8 @@ __global__ void __launch_bounds__(VER_THREADS)
                       const uint8_t* __restrict__ lens_j, uint64_t n_j,
                       int metric, xtn_triple* __restrict__ out, int64_t cap,
                       uint64_t* __restrict__ status, uint32_t* __restrict__ ctr,
-                      uint32_t* __restrict__ err, uint64_t* __restrict__ total_out) {
+                      uint32_t* __restrict__ err, uint64_t* __restrict__ total_out,
+                      SecondChain sc) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_w[VER_THREADS / 32];
   __shared__ uint64_t s_prefix;
@@ -246,8 +266,7 @@ __global__ void __launch_bounds__(VER_THREADS)
         ok = false;
       }
       if (ok)
-        dist[it] = pair_distance(metric, XTN_MAX_LEN, peq_i + i * PEQ_STRIDE, lens_i[i], keys_j[j],
-                                 lens_j[j]);
+        dist[it] = cand_distance(metric, 2 * XTN_MAX_LEN, peq_i, lens_i, keys_j, lens_j, sc, i, j);
       word[it] = w;
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
@@ -296,7 +315,8 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_
                             const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                             int metric, xtn_triple* out, int64_t cap, uint64_t* status,
-                            uint32_t* err, uint64_t* total, cudaStream_t s) {
+                            uint32_t* err, uint64_t* total, cudaStream_t s,
+                            const SecondChain& sc) {
   if (n <= 0) return;
   const size_t st = verify_status_bytes(n);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
@@ -304,7 +324,7 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_
   prof_begin(s, "k_unique_finalize", (double)n * 8.0);
   k_unique_finalize<<<std::min<uint32_t>(div_up_u32(n, VER_TILE), 152 * 8), VER_THREADS, 0, s>>>(
       pairs, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, metric, out, cap, status,
-      ctr, err, total);
+      ctr, err, total, sc);
   prof_end(s);
 }
 

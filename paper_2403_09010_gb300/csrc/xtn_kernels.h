@@ -73,7 +73,8 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
                               uint64_t** sorted, const char* tag, cudaStream_t s,
                               bool hist_in_passes = false, const uint64_t* n_dev = nullptr,
                               uint64_t* bucket_start = nullptr, int first_cfg = -1);
-int onesweep_unstable_config();
+// Unstable configuration with the same tile as cfg, for a sort's first pass.
+int onesweep_unstable_config(int cfg);
 
 // k_bucket.cu --------------------------------------------------------------
 // Positions per flag tile of the group-bound kernels (head/tail counts are
@@ -139,7 +140,18 @@ constexpr int VERIFY_TILE = 2048;
 constexpr size_t verify_status_bytes_for(int64_t n) {
   return (size_t)((n + VERIFY_TILE - 1) / VERIFY_TILE) * 8 + 16;
 }
-// metric: 0 = Levenshtein, 1 = Hamming (pairs of equal length only).
+// Second chains of paired receptors (metric 2, the sum of the two chains'
+// edit distances): match vectors of the i side, keys of the j side and both
+// sides' lengths.  All null for one chain.
+struct SecondChain {
+  const uint32_t* peq_i = nullptr;
+  const uint8_t* lens_i = nullptr;
+  const Key128* keys_j = nullptr;
+  const uint8_t* lens_j = nullptr;
+};
+// metric: 0 = Levenshtein, 1 = Hamming (pairs of equal length only), 2 =
+// paired chains (Levenshtein of the first chains plus that of the second,
+// which `sc` describes).
 // self_mode: 0 = query vs reference, 1 = self-search (pairs within a
 // repertoire when seq_rep is given), 2 = self-search keeping only pairs
 // between different repertoires.
@@ -150,20 +162,39 @@ void launch_verify_candidates(const uint64_t* cand, uint64_t n, const uint64_t* 
                               const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                               const uint32_t* seq_rep, int self_mode, int d, int metric,
                               uint64_t* surv, uint64_t surv_cap, uint64_t* n_surv, uint32_t* hist,
-                              int hist_hi, int sms, uint32_t* err, cudaStream_t s);
+                              int hist_hi, int sms, uint32_t* err, cudaStream_t s,
+                              const SecondChain& sc = SecondChain());
 void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_dev,
                             uint32_t j_bits,
                             const uint32_t* peq_i, const uint8_t* lens_i, uint64_t n_i,
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                             int metric, xtn_triple* out, int64_t cap, uint64_t* status,
-                            uint32_t* err, uint64_t* total, cudaStream_t s);
+                            uint32_t* err, uint64_t* total, cudaStream_t s,
+                            const SecondChain& sc = SecondChain());
 void launch_tcrdist_filter(const xtn_triple* in, int64_t n, const Key128* keys,
                            const uint8_t* lens, int64_t n_seq, int max_score, xtn_triple* out,
                            uint64_t* status, uint32_t* err, uint64_t* total, cudaStream_t s);
 
+// k_paired.cu --------------------------------------------------------------
+// Canonical deletion variants (d <= 2) of receptors alpha + token + beta,
+// the token never deleted: counts per receptor, and the expansion into
+// records fingerprint | receptor id at rec_off (digit histograms of the sort
+// passes over bits [hist_lo, hist_hi) on the way).
+void launch_paired_counts(const uint8_t* lens_a, const uint32_t* eq_a, const uint8_t* lens_b,
+                          const uint32_t* eq_b, int64_t n, int d, uint32_t* vcount,
+                          cudaStream_t s);
+void launch_expand_paired(const Key128* keys_a, const uint8_t* lens_a, const uint32_t* eq_a,
+                          const Key128* keys_b, const uint8_t* lens_b, const uint32_t* eq_b,
+                          const uint64_t* rec_off, int64_t n, int d, uint32_t id_bits,
+                          uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo, int hist_hi,
+                          int sms, uint32_t* err, cudaStream_t s);
+
 // k_query.cu ---------------------------------------------------------------
-void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, uint32_t* dir,
-                      cudaStream_t s);
+// Directory of the sorted index (entry t = first record whose top dir_bits
+// bits are >= t) and, added into *n_groups, the number of distinct group keys
+// (bits from gshift up).
+void launch_build_dir(const uint64_t* rec, uint64_t n_rec, int dir_bits, int gshift,
+                      uint32_t* dir, uint64_t* n_groups, cudaStream_t s);
 void launch_query_lookup(const Key128* qkeys, const uint8_t* qlens, const uint32_t* qeqprev,
                          const uint64_t* q_rec_off, int64_t n_q, uint64_t n_qv, int d,
                          const uint64_t* rec, uint64_t n_rec, const uint32_t* dir,

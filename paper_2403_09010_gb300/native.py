@@ -42,6 +42,7 @@ SIGNATURES = {
     "xtn_search_self": (_I, [_P, _P, _I64, _I, _P, _I64, _P, _I64, _P, _P]),
     "xtn_search_self_hamming": (_I, [_P, _P, _I64, _I, _P, _I64, _P, _I64, _P, _P]),
     "xtn_search_between": (_I, [_P, _P, _I64, _I, _P, _I64, _I, _P, _I64, _P, _P]),
+    "xtn_search_paired": (_I, [_P, _P, _P, _P, _I64, _I, _P, _I64, _P, _P]),
     "xtn_search_self_streaming": (_I, [_P, _P, _I64, _I, _P, _I64, _I, _I, _I64, _P, _I64, _P,
                                        _P, _P]),
     "xtn_index_build": (_I, [_P, _P, _I64, _I, _P, _P]),
@@ -49,6 +50,7 @@ SIGNATURES = {
     "xtn_index_info": (_I, [_P, _P, _P, _P, _P]),
     "xtn_search_query": (_I, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
     "xtn_search_query_hamming": (_I, [_P, _P, _P, _I64, _P, _I64, _P, _P]),
+    "xtn_search_query_scratch": (_I, [_P, _P, _I64, _P]),
     "xtn_tcrdist_filter": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
     "xtn_tcrdist_filter_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I, _P, _P, _P]),
     "xtn_plan_create": (_I, [_P, _I64, _I, _P, _I64, _I64, _P]),

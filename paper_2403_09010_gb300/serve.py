@@ -2,20 +2,25 @@
 batching (the fuzzy database lookup of the paper's Discussion, served).
 
 Requests (each a packed batch of query sequences) arrive over time.  A
-scheduler thread keeps up to `slots` micro-batches on the GPU at once, each on
-its own CUDA stream and worker thread (the C ABI releases the GIL, so the
-searches overlap on the device).  Whenever a slot is free, every request that
-has arrived and fits the memory budget is merged into one micro-batch: its
-queries are concatenated, searched with one xtn_search_query call against the
-resident index, and the rows are split back per request (query indices local
-to the request).  Requests that arrive while others are running join the next
-micro-batch as soon as a slot and memory free up -- batching is continuous,
-not a fixed queue drain.
+scheduler thread keeps up to `slots` micro-batches on the GPU at once.  Each
+slot has its own CUDA stream, its own worker thread (started once; the C ABI
+releases the GIL, so the searches overlap on the device) and its own pinned
+host buffers: the batch's queries are concatenated straight into pinned
+memory and the rows come back into pinned memory, so the library's
+host<->device copies are asynchronous DMA.  Whenever a slot is free, every
+request that has arrived and fits the memory budget is merged into one
+micro-batch: one xtn_search_query call against the resident index, rows split
+back per request (query indices local to the request).  Requests that arrive
+while others are running join the next micro-batch as soon as a slot and
+memory free up -- batching is continuous, not a fixed queue drain.
 
-Admission is by device memory: a micro-batch is admitted only while the
-estimated scratch of everything in flight stays within `memory_budget` bytes
-(by default half of the device memory free when the server starts, capped at
-16 GiB).  A request larger than the whole budget is admitted alone.
+Admission is by device memory: each request's scratch is the library's own
+estimate for its queries (xtn_search_query_scratch: exact in the queries'
+lengths, the candidate part from the index's candidates per query variant so
+far), and a micro-batch is admitted only while the scratch of everything in
+flight stays within `memory_budget` bytes (by default half of the device
+memory free when the server starts, capped at 16 GiB).  A request larger
+than the whole budget is admitted alone.
 
 Latency is measured from a request's scheduled arrival to the moment its rows
 are ready on the host; `stats()` reports p50 / p99 latency, requests/s,
@@ -34,9 +39,8 @@ import numpy as np
 from . import native
 from .native import check
 
-# Scratch estimate per query sequence for one micro-batch: lookups of ~115
-# variant records (start, count, query id, offsets ~ 24 B each), candidate and
-# survivor words, match vectors and encoded keys.  Deliberately generous.
+# Scratch estimate used only without an index (a stand-in search in tests):
+# per query sequence and per micro-batch.
 BYTES_PER_QUERY = 8 * 1024
 BYTES_PER_BATCH = 8 << 20
 
@@ -47,6 +51,7 @@ class _Pending:
     seqs: np.ndarray
     offsets: np.ndarray
     arrival: float               # scheduled arrival (time.perf_counter() clock)
+    need: int = 0                # admitted device scratch (bytes)
     done: threading.Event = dataclasses.field(default_factory=threading.Event)
     rows: np.ndarray | None = None
     error: BaseException | None = None
@@ -59,15 +64,44 @@ def estimate_bytes(n_queries: int) -> int:
     return BYTES_PER_BATCH + BYTES_PER_QUERY * int(n_queries)
 
 
+class _Staging:
+    """Host buffers of one slot, pinned when torch can pin them, grown to the
+    largest batch seen (doubling)."""
+
+    def __init__(self, pinned: bool):
+        self.pinned = pinned
+        self.bufs = {}
+
+    def array(self, name: str, n: int, dtype) -> np.ndarray:
+        n = max(int(n), 1)
+        a = self.bufs.get(name)
+        if a is None or a.size < n or a.dtype != np.dtype(dtype):
+            size = max(n, 2 * (a.size if a is not None else 0))
+            if self.pinned:
+                import torch
+                t = torch.empty(size * np.dtype(dtype).itemsize, dtype=torch.uint8,
+                                pin_memory=True)
+                a = t.numpy().view(dtype)
+                self.bufs[name + "_keep"] = t
+            else:
+                a = np.empty(size, dtype=dtype)
+            self.bufs[name] = a
+        return a[:n]
+
+
 class Server:
     """Continuous-batching query server for one xtn index.
 
     search_fn(seqs, offsets, stream) -> (rows (k, 3) uint32, sorted by query)
     defaults to xtn_search_query on `index`; tests may pass a stand-in.
+    scratch_fn(offsets) -> bytes is the admission estimate of one request;
+    by default the index's own (xtn_search_query_scratch), or estimate_bytes
+    without an index.
     """
 
     def __init__(self, index=None, slots: int = 3, memory_budget: int | None = None,
-                 max_batch_queries: int = 65536, search_fn=None, device_streams: bool = True):
+                 max_batch_queries: int = 65536, search_fn=None, device_streams: bool = True,
+                 scratch_fn=None):
         self.index = index
         self.slots = max(1, int(slots))
         self.max_batch_queries = int(max_batch_queries)
@@ -81,15 +115,25 @@ class Server:
                 pass
         self.memory_budget = int(memory_budget)
         self._search = search_fn or self._xtn_search
+        if scratch_fn is None:
+            if index is not None and search_fn is None:
+                scratch_fn = index.scratch_bytes
+            else:
+                scratch_fn = lambda offsets: estimate_bytes(np.asarray(offsets).size - 1)
+        self._scratch = scratch_fn
         self._device_streams = device_streams
         self._waiting: list[_Pending] = []
         self._cv = threading.Condition()
         self._in_flight_bytes = 0
         self._free_slots = queue.SimpleQueue()
         self._streams = []
+        self._staging = []
+        self._work = []
         for k in range(self.slots):
             self._free_slots.put(k)
             self._streams.append(self._make_stream())
+            self._staging.append(_Staging(pinned=device_streams))
+            self._work.append(queue.SimpleQueue())
         self._stop = False
         self._batches: list[tuple[int, int, int]] = []   # (batch id, requests, queries)
         self._peak_in_flight = 0
@@ -97,6 +141,11 @@ class Server:
         self._peak_bytes = 0
         self._done: list[_Pending] = []
         self._next_batch = 0
+        # one worker per slot for the server's life, and the scheduler
+        self._workers = [threading.Thread(target=self._worker, args=(k,), daemon=True)
+                         for k in range(self.slots)]
+        for t in self._workers:
+            t.start()
         self._scheduler = threading.Thread(target=self._schedule, daemon=True)
         self._scheduler.start()
 
@@ -107,16 +156,17 @@ class Server:
         import torch
         return torch.cuda.Stream()
 
-    def _xtn_search(self, seqs, offsets, stream):
+    def _xtn_search(self, seqs, offsets, stream, slot=None):
         s = np.ascontiguousarray(seqs, dtype=np.uint8)
         if s.size == 0:
             s = np.zeros(1, np.uint8)
         o = np.ascontiguousarray(offsets, dtype=np.int64)
         n_q = o.size - 1
         st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        staging = self._staging[slot] if slot is not None else _Staging(False)
         cap = 8 * n_q + 1024
         while True:
-            out = np.empty((cap, 3), dtype=np.uint32)
+            out = staging.array("rows", 3 * cap, np.uint32).reshape(cap, 3)
             n_out = ctypes.c_int64(0)
             rc = native.lib().xtn_search_query(self.index.handle, s.ctypes.data, o.ctypes.data,
                                                n_q, out.ctypes.data, cap, ctypes.byref(n_out), st)
@@ -126,21 +176,34 @@ class Server:
             check(rc, "xtn_search_query")
             return out[: n_out.value]
 
+    def _run_search(self, seqs, offsets, slot):
+        if self._search == self._xtn_search:
+            return self._xtn_search(seqs, offsets, self._streams[slot], slot)
+        return self._search(seqs, offsets, self._streams[slot])
+
     # ------------------------------------------------------------- public
     def warm(self, seqs, offsets):
         """Run one search on every slot's stream before serving, so that no
-        request pays first-use costs (pool growth on a new stream)."""
+        request pays first-use costs (pool growth on a new stream, pinned
+        buffers)."""
         s = np.asarray(seqs, np.uint8)
         o = np.asarray(offsets, np.int64)
         for k in range(self.slots):
-            self._search(s, o, self._streams[k])
+            st = self._staging[k]
+            ss = st.array("seqs", s.size, np.uint8)
+            ss[:] = s
+            oo = st.array("offs", o.size, np.int64)
+            oo[:] = o
+            self._run_search(ss, oo, k)
         if self._device_streams:
             import torch
             torch.cuda.synchronize()
 
     def submit(self, rid: int, seqs, offsets, arrival: float | None = None) -> _Pending:
-        p = _Pending(rid, np.asarray(seqs, np.uint8), np.asarray(offsets, np.int64),
-                     time.perf_counter() if arrival is None else arrival)
+        offsets = np.asarray(offsets, np.int64)
+        p = _Pending(rid, np.asarray(seqs, np.uint8), offsets,
+                     time.perf_counter() if arrival is None else arrival,
+                     need=int(self._scratch(offsets)))
         with self._cv:
             self._waiting.append(p)
             self._cv.notify_all()
@@ -161,15 +224,18 @@ class Server:
             self._stop = True
             self._cv.notify_all()
         self._scheduler.join(timeout=60)
+        for q in self._work:
+            q.put(None)
+        for t in self._workers:
+            t.join(timeout=60)
 
     # ---------------------------------------------------------- scheduling
     def _take_batch(self):
         """Waiting requests that fit the memory budget, oldest first."""
-        batch, queries, need = [], 0, BYTES_PER_BATCH
+        batch, queries, need = [], 0, 0
         for p in list(self._waiting):
             nq = p.offsets.size - 1
-            add = BYTES_PER_QUERY * nq
-            fits = self._in_flight_bytes + need + add <= self.memory_budget
+            fits = self._in_flight_bytes + need + p.need <= self.memory_budget
             alone = not batch and self._in_flight_bytes == 0
             if batch and (queries + nq > self.max_batch_queries or not fits):
                 break
@@ -177,7 +243,7 @@ class Server:
                 break
             batch.append(p)
             queries += nq
-            need += add
+            need += p.need
         for p in batch:
             self._waiting.remove(p)
         return batch, queries, need
@@ -201,23 +267,34 @@ class Server:
                 bid = self._next_batch
                 self._next_batch += 1
                 self._batches.append((bid, len(batch), queries))
-            threading.Thread(target=self._run_batch, args=(slot, bid, batch, need),
-                             daemon=True).start()
+            self._work[slot].put((bid, batch, need))
+
+    def _worker(self, slot):
+        while True:
+            item = self._work[slot].get()
+            if item is None:
+                return
+            self._run_batch(slot, *item)
 
     def _run_batch(self, slot, bid, batch, need):
         try:
+            st = self._staging[slot]
             lens = [p.offsets.size - 1 for p in batch]
             q_base = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
-            seqs = np.concatenate([p.seqs for p in batch]) if batch else np.zeros(0, np.uint8)
-            offs = [np.asarray(p.offsets, np.int64) for p in batch]
-            byte_base = np.concatenate([[0], np.cumsum([o[-1] for o in offs])]).astype(np.int64)
-            offsets = np.concatenate([[0]] + [o[1:] + byte_base[k] for k, o in enumerate(offs)])
-            rows = self._search(seqs, offsets.astype(np.int64), self._streams[slot])
+            n_q = int(q_base[-1])
+            byte_base = np.concatenate([[0], np.cumsum([p.offsets[-1] for p in batch])])
+            seqs = st.array("seqs", int(byte_base[-1]), np.uint8)
+            offsets = st.array("offs", n_q + 1, np.int64)
+            offsets[0] = 0
+            for k, p in enumerate(batch):
+                seqs[byte_base[k]:byte_base[k + 1]] = p.seqs[: p.offsets[-1]]
+                offsets[q_base[k] + 1:q_base[k + 1] + 1] = p.offsets[1:] + byte_base[k]
+            rows = self._run_search(seqs[: int(byte_base[-1])], offsets, slot)
             q = rows[:, 0].astype(np.int64) if rows.size else np.zeros(0, np.int64)
             cut = np.searchsorted(q, q_base)
             now = time.perf_counter()
             for k, p in enumerate(batch):
-                part = rows[cut[k]:cut[k + 1]].copy()
+                part = np.array(rows[cut[k]:cut[k + 1]], dtype=np.uint32, copy=True)
                 part[:, 0] -= np.uint32(q_base[k])
                 p.rows = part
                 p.finished = now

@@ -95,6 +95,26 @@ def search_self(seqs, offsets, d: int, rep_offsets=None, cap: int | None = None,
     return _call_with_rows(fn, cap, seqs, entry)
 
 
+def search_paired(a_seqs, a_offsets, b_seqs, b_offsets, d: int, cap: int | None = None):
+    """All receptor pairs (i < j) whose chains are within d edits in all:
+    Lev(alpha_i, alpha_j) + Lev(beta_i, beta_j) <= d; see xtn_search_paired."""
+    n = _n_items(a_offsets)
+    if _n_items(b_offsets) != n:
+        raise ValueError("both chains need one offset per receptor")
+    ap, ak, _ = _ptr(a_seqs, np.uint8)
+    aop, aok, _ = _ptr(a_offsets, np.int64)
+    bp, bk, _ = _ptr(b_seqs, np.uint8)
+    bop, bok, _ = _ptr(b_offsets, np.int64)
+    stream = _stream(a_seqs)
+    if cap is None:
+        cap = 4 * n + 4096
+
+    def fn(optr, c, nref):
+        return native.lib().xtn_search_paired(ap, aop, bp, bop, n, int(d), optr, c, nref, stream)
+
+    return _call_with_rows(fn, cap, a_seqs, "xtn_search_paired")
+
+
 def search_between(seqs, offsets, d: int, rep_offsets, cap: int | None = None,
                    metric: str = "levenshtein"):
     """All pairs (i < j) within distance d whose sequences lie in different
@@ -163,6 +183,16 @@ class Index:
         check(native.lib().xtn_index_info(self._h, ctypes.byref(n), ctypes.byref(d),
                                           ctypes.byref(nr), ctypes.byref(nb)), "xtn_index_info")
         return {"n": n.value, "d": d.value, "n_records": nr.value, "device_bytes": nb.value}
+
+    def scratch_bytes(self, q_offsets) -> int:
+        """Device scratch a query search of these queries takes (an estimate for
+        admission control; see xtn_search_query_scratch).  q_offsets: host."""
+        o = np.ascontiguousarray(q_offsets, dtype=np.int64)
+        out = ctypes.c_int64(0)
+        check(native.lib().xtn_search_query_scratch(self._h, o.ctypes.data_as(ctypes.c_void_p),
+                                                    o.size - 1, ctypes.byref(out)),
+              "xtn_search_query_scratch")
+        return int(out.value)
 
     def free(self):
         if self._h:

@@ -120,3 +120,17 @@ def test_wait_limit_range(lib):
     assert lib.xtn_set_wait_limit((1 << 20) + 1) == native.XTN_ERR_INVALID_ARG
     assert lib.xtn_set_wait_limit(5) == native.XTN_OK
     assert lib.xtn_set_wait_limit(0) == native.XTN_OK
+
+
+def test_paired_argument_checks(lib):
+    n_out = ctypes.c_int64(7)
+    off = (ctypes.c_int64 * 2)(0, 3)
+    seq = ctypes.c_char_p(b"CAS")
+    # a missing second chain, d above 2, missing n_out: refused on the host
+    assert lib.xtn_search_paired(seq, off, seq, None, 1, 1, None, 0,
+                                 ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert n_out.value == 0
+    assert lib.xtn_search_paired(seq, off, seq, off, 1, 3, None, 0,
+                                 ctypes.byref(n_out), None) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_search_paired(seq, off, seq, off, 1, 1, None, 0, None,
+                                 None) == native.XTN_ERR_INVALID_ARG

@@ -705,3 +705,58 @@ def test_bounded_wait_gives_up_and_reports(xtn):
     small_s, small_o = gen.workload(gen.SELF_1M, 20_000)
     assert np.array_equal(_rows(xtn.search_self(small_s, small_o, 2)),
                           oracle.symdel_self(small_s, small_o, 2))
+
+
+# --------------------------------------------------------- paired chains ---
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_paired_matches_oracle(xtn, d):
+    a, ao, b, bo = gen.paired(6_000, 80 + d)
+    want = oracle.symdel_paired(a, ao, b, bo, d)
+    got = _rows(xtn.search_paired(a, ao, b, bo, d))
+    assert got.shape == want.shape and np.array_equal(got, want)
+    if d >= 1:
+        assert want.shape[0] > 100
+    # device inputs give the same rows
+    da, dao = _dev(a, ao)
+    db, dbo = _dev(b, bo)
+    assert np.array_equal(_rows(xtn.search_paired(da, dao, db, dbo, d)), want)
+
+
+def test_paired_small_alphabet_and_edges(xtn):
+    rng = np.random.default_rng(83)
+    a = _rand_strings(rng, 700, "AC", 0, 6)
+    b = _rand_strings(rng, 700, "AC", 0, 6)
+    sa, oa = gen.from_strings(a)
+    sb, ob = gen.from_strings(b)
+    for d in (0, 1, 2):
+        assert np.array_equal(_rows(xtn.search_paired(sa, oa, sb, ob, d)),
+                              oracle.bruteforce_paired(sa, oa, sb, ob, d)), d
+    # longest chains, empty chains, a receptor repeated many times
+    strs_a = ["W" * 25, "W" * 24, "", "", "CASSF"] + ["CAVF"] * 300
+    strs_b = ["Y" * 25, "Y" * 25, "", "A", ""] + ["CASSF"] * 300
+    sa, oa = gen.from_strings(strs_a)
+    sb, ob = gen.from_strings(strs_b)
+    for d in (1, 2):
+        assert np.array_equal(_rows(xtn.search_paired(sa, oa, sb, ob, d)),
+                              oracle.bruteforce_paired(sa, oa, sb, ob, d)), d
+
+
+def test_paired_with_empty_second_chains_is_the_self_search(xtn):
+    seqs, off = gen.workload(gen.SELF_1M, 30_000)
+    empty = np.zeros(0, np.uint8)
+    zero = np.zeros(off.size, np.int64)
+    assert np.array_equal(_rows(xtn.search_paired(seqs, off, empty, zero, 2)),
+                          _rows(xtn.search_self(seqs, off, 2)))
+
+
+def test_paired_rejects_bad_arguments(xtn):
+    from paper_2403_09010_gb300 import native
+    a, ao, b, bo = gen.paired(50, 9)
+    with pytest.raises(native.XtnError) as ei:
+        xtn.search_paired(a, ao, b, bo, 3)
+    assert ei.value.status == native.XTN_ERR_INVALID_ARG
+    bad = b.copy()
+    bad[0] = ord("X")
+    with pytest.raises(native.XtnError) as ei:
+        xtn.search_paired(a, ao, bad, bo, 1)
+    assert ei.value.status == native.XTN_ERR_BAD_RESIDUE

@@ -26,6 +26,7 @@ def test_served_results_identical_alone_and_in_the_mix():
     assert st["requests"] == len(reqs)
     assert st["p99_ms"] >= st["p50_ms"] > 0
     assert st["max_requests_per_batch"] > 1        # continuous batching happened
+    assert st["peak_batches_in_flight"] > 1        # micro-batches overlapped on the GPU
     for r, p in zip(reqs, pend):
         alone = xtn.search_query(idx, r.seqs, r.offsets).astype(np.uint32)
         assert np.array_equal(p.rows, alone), r.rid

@@ -113,3 +113,41 @@ def test_warm_runs_one_search_per_slot():
     srv.warm(seqs, off)
     srv.close()
     assert len(calls) == 3
+
+
+def test_slot_workers_are_started_once():
+    srv = serve.Server(slots=3, memory_budget=1 << 40, search_fn=fake_search(0.002),
+                       device_streams=False)
+    before = threading.active_count()
+    reqs = _requests(60, 5)
+    pend = []
+    for r, s, o in reqs:
+        pend.append(srv.submit(r, s, o))
+        time.sleep(0.001)
+    for p in pend:
+        assert p.done.wait(30)
+    during = threading.active_count()
+    srv.close()
+    assert srv.stats()["batches"] > 3
+    assert during == before          # no thread per micro-batch
+    for (r, s, o), p in zip(reqs, pend):
+        assert np.array_equal(p.rows, alone(s, o))
+
+
+def test_admission_by_scratch_estimate():
+    # each request's scratch comes from scratch_fn; what is in flight never
+    # exceeds the budget, and a request alone may exceed it
+    per_query = 1000
+    budget = 30 * per_query
+    srv = serve.Server(slots=4, memory_budget=budget, search_fn=fake_search(0.01),
+                       device_streams=False,
+                       scratch_fn=lambda o: per_query * (np.asarray(o).size - 1))
+    reqs = _requests(30, 6)
+    pend = [srv.submit(r, s, o) for r, s, o in reqs]
+    for p in pend:
+        assert p.done.wait(30)
+    srv.close()
+    st = srv.stats()
+    big = max(per_query * (o.size - 1) for _, _, o in reqs)
+    assert st["peak_admitted_bytes"] <= max(budget, big)
+    assert all(p.need == per_query * (o.size - 1) for (_, _, o), p in zip(reqs, pend))
