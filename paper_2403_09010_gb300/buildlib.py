@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libxtn.so")
 SOURCES = ["api.cu", "k_variants.cu", "k_radix.cu", "k_pairs.cu", "k_verify.cu", "k_query.cu",
-           "noalloc.cu", "k_bucket.cu", "k_paired.cu"]
+           "noalloc.cu", "k_bucket.cu", "k_paired.cu", "k_filter.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

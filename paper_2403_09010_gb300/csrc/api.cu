@@ -504,7 +504,15 @@ struct GroupScratch {
   uint64_t* cand = nullptr;
   uint64_t cand_cap = 0;
   uint64_t* cand_count = nullptr;
+  // with cand (grouping mode 0): seg_area_bytes() for the singleton filter's
+  // segment counter (first 16 bytes) and one flag byte per block of buckets
+  uint8_t* seg_area = nullptr;
 };
+
+size_t seg_area_bytes(uint64_t rec_cap, int hs) {
+  const GroupingShape g = choose_grouping(rec_cap, hs, true);
+  return 16 + (((size_t)1 << g.G) >> g.kbits);
+}
 
 size_t bucket_start_words(uint64_t rec_cap, int hs, int mode) {
   if (mode == 1) return 1;
@@ -572,9 +580,21 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
     XTN_CK(cudaMemsetAsync(gs.gstatus, 0, group_status_bytes((int64_t)rec_cap), s));
     tile_counts = group_tile_counts(gs.gstatus, (int64_t)rec_cap);
   }
-  launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo,
-                mode == 2 ? 512 : 0, gs.flags, tile_counts, hash ? gs.cand : nullptr, gs.cand_cap,
-                gs.cand_count, id_bits, err, s);
+  if (hash && gs.cand && gs.seg_area && mode == 0) {
+    // the singleton filter groups and emits nearly every block of buckets;
+    // k_bucket takes only the blocks it flags
+    XTN_CK(cudaMemsetAsync(gs.seg_area, 0, seg_area_bytes(rec_cap, 64 - lo), s));
+    uint8_t* seg_flags = gs.seg_area + 16;
+    launch_bucket_filter(X, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo, gs.cand,
+                         gs.cand_cap, gs.cand_count, id_bits, seg_flags,
+                         reinterpret_cast<uint32_t*>(gs.seg_area), sms, err, s);
+    launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo, 0, gs.flags,
+                  tile_counts, gs.cand, gs.cand_cap, gs.cand_count, id_bits, err, s, seg_flags);
+  } else {
+    launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo,
+                  mode == 2 ? 512 : 0, gs.flags, tile_counts, hash ? gs.cand : nullptr,
+                  gs.cand_cap, gs.cand_count, id_bits, err, s);
+  }
   XTN_CK(cudaGetLastError());
   *sorted = Y;
   return XTN_OK;
@@ -602,6 +622,7 @@ int expand_and_sort(const Encoded& e, int64_t n, int d, const uint32_t* seq_rep,
     gs.cand = direct->cand;
     gs.cand_cap = direct->cand_cap;
     gs.cand_count = direct->cand_count;
+    if (mode == 0) gs.seg_area = ar.get<uint8_t>(seg_area_bytes(n_rec, out->hs));
   }
   gs.bucket_start = ar.get<uint64_t>(bucket_start_words(n_rec, out->hs, mode));
   if (want_flags) {
@@ -894,6 +915,7 @@ int search_stream_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, i
   uint64_t* status = ar.get<uint64_t>(radix_status_bytes(P, cfg) / 8 + 1);
   GroupScratch gs0;
   gs0.bucket_start = ar.get<uint64_t>(bucket_start_words(P, hs, 0));
+  gs0.seg_area = ar.get<uint8_t>(seg_area_bytes(P, hs));
   gs0.flags = ar.get<uint64_t>(group_flag_words((int64_t)P));
   gs0.gstatus = ar.get<uint64_t>(
       std::max(group_status_bytes((int64_t)P), scan_status_bytes((int64_t)g_cap)) / 8 + 1);
@@ -1426,6 +1448,7 @@ struct xtn_plan {
   uint32_t id_bits = 0;
   int hs = 0, cfg_rec = 0, cfg_pair = 0, hist_mode = 0, group_mode = 0, sms = 0;
   uint64_t* bucket_start = nullptr;
+  uint8_t* seg_area = nullptr;  // singleton filter's segment counter and flags
   std::vector<void*> allocs;
   int64_t bytes = 0;
   int64_t* off = nullptr;
@@ -1517,6 +1540,7 @@ int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* re
   p->status = p->alloc<uint64_t>(st / 8 + 1);
   p->flags = p->alloc<uint64_t>(group_flag_words((int64_t)rec_cap));
   p->bucket_start = p->alloc<uint64_t>(bucket_start_words(rec_cap, p->hs, p->group_mode));
+  p->seg_area = p->alloc<uint8_t>(seg_area_bytes(rec_cap, p->hs));
   p->counters = p->alloc<uint64_t>(4);
   p->err = p->alloc<uint32_t>(4);
   p->peq = p->alloc<uint32_t>((size_t)n * PEQ_STRIDE);
@@ -1530,7 +1554,7 @@ int plan_create_impl(const int64_t* offsets, int64_t n, int d, const int64_t* re
   if (rep_offsets) p->seq_rep = p->alloc<uint32_t>(n);
   bool ok = p->rows && p->back.counters && p->back.status && p->back.digit_base && p->back.hist &&
             p->back.P2 && p->back.P1 && p->peq && p->err && p->counters && p->flags && p->status &&
-            p->bucket_start &&
+            p->bucket_start && p->seg_area &&
             p->digit_base && p->hist && p->B && p->A && p->rec_off && p->vcount && p->eqprev &&
             p->lens && p->keys && p->off && (!rep_offsets || p->seq_rep);
   if (!ok) {
@@ -1585,6 +1609,7 @@ int plan_run_impl(xtn_plan* p, const uint8_t* seqs, cudaStream_t s) {
     gs.cand = p->back.P1;
     gs.cand_cap = p->pair_cap;
     gs.cand_count = p->counters + 2;
+    gs.seg_area = p->seg_area;
   }
   XTN_CK(expand_sort_launch(p->keys, p->lens, p->eqprev, p->rec_off, n, p->d, p->seq_rep,
                             p->id_bits, p->A, p->B, p->rec_cap, lo, p->hist, p->digit_base,

@@ -61,12 +61,6 @@ struct Bk {
 };
 static_assert(Bk<true>::H >= 2 * Bk<true>::CAP, "hash load factor <= 1/2");
 
-// Singleton filter of the candidate mode: two bitmaps of 2^FILTER_BITS bits
-// in the table region.
-constexpr int FILTER_BITS = 16;
-constexpr int FILTER_WORDS = (1 << FILTER_BITS) / 32;
-static_assert(2 * FILTER_WORDS * 4 <= Bk<true>::region, "bitmaps fit the table region");
-
 constexpr unsigned long long NO_START = ~0ull;
 constexpr uint32_t EMPTY_SLOT = 0xffffffffu;
 constexpr uint64_t NO_GROUP = ~0ull;  // above every group key (at most 40 bits)
@@ -243,7 +237,9 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
              int cap, uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts,
              uint64_t* __restrict__ cand, uint64_t cand_cap,
              unsigned long long* __restrict__ cand_count, int id_bits,
-             uint32_t* __restrict__ err) {
+             const uint8_t* __restrict__ seg_flags, uint32_t* __restrict__ err) {
+  // with seg_flags, only the segments the singleton filter flagged
+  if (seg_flags && !seg_flags[blockIdx.x]) return;
   using C = Bk<HASH>;
   constexpr int ITEMS = C::ITEMS;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -254,7 +250,6 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   __shared__ uint32_t s_wsum[BK_WARPS];
   __shared__ int64_t s_range[2];
   __shared__ unsigned long long s_acc[2];
-  __shared__ uint32_t s_nlist;  // records kept by the singleton filter
 
   const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
   const int64_t nb = 1ll << G;
@@ -296,10 +291,6 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
         v = bf >= nb ? n : first_start(bucket_start, bf, nb, n, lane);
       }
       if (lane == 0) s_range[warp] = v;
-    } else if (cand) {
-      // candidate mode starts with the singleton filter: zeroed bitmaps
-      for (int k = threadIdx.x - 64; k < 2 * FILTER_WORDS / 4; k += BK_THREADS - 64)
-        reinterpret_cast<uint4*>(s_wh)[k] = make_uint4(0u, 0u, 0u, 0u);
     } else {
       for (int k = threadIdx.x - 64; k < (C::H + C::H / 2) / 4; k += BK_THREADS - 64)
         reinterpret_cast<uint4*>(s_wh)[k] =
@@ -370,10 +361,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
 
   // ---- one segment [p, q) of at most `cap` records, buckets from bA ----
   // composite key: (key >> lo) - (bA << L) = (bucket - bA) << L | low L bits
-  // `list` (shared memory, HASH only): take the records from list[0, q - p)
-  // instead of A[p, q).
-  auto segment = [&](int64_t p, int64_t q, uint64_t bA, int kb, bool cleared,
-                     const uint64_t* list = nullptr) {
+  auto segment = [&](int64_t p, int64_t q, uint64_t bA, int kb, bool cleared) {
     const int m = (int)(q - p);
     const uint64_t cbase = bA << L;
     auto comp = [&](uint64_t k) { return (uint32_t)((k >> lo) - cbase); };
@@ -381,7 +369,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const int pos = wbase + i * 32 + (int)lane;
-      key[i] = pos < m ? (list ? list[pos] : __ldcs(A + p + pos)) : 0ull;
+      key[i] = pos < m ? __ldcs(A + p + pos) : 0ull;
     }
     if constexpr (HASH) {
       uint32_t* tk = s_wh;                                   // H composite keys
@@ -607,82 +595,8 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
     __syncthreads();
   };
 
-  // ---- singleton filter (candidate mode) ----
-  // Nearly every variant record shares its group key with no other record.
-  // Two bitmaps indexed by a hash of the composite key mark the keys seen and
-  // the keys seen again; only records whose bit is marked again can belong to
-  // a group of two or more (a bitmap collision merely lets a lone record
-  // through, and the exact grouping drops it).  Those records are compacted
-  // into s_k and grouped exactly by `segment`'s hash grouping, which writes
-  // their candidate pairs.  Returns false, having emitted nothing, when they
-  // are more than one segment holds; the bitmaps then occupy the table
-  // region.  Block-uniform.
-  auto filter = [&](int64_t p, int64_t q, uint64_t bA) -> bool {
-    uint32_t* seen = s_wh;
-    uint32_t* again = s_wh + FILTER_WORDS;
-    const uint64_t cbase = bA << L;
-    const int64_t m = q - p;
-    // composite keys of at most FILTER_BITS bits index the bitmaps directly
-    // (no collisions), wider ones through a multiplicative hash
-    const bool direct = L + kbits <= FILTER_BITS;
-    auto bit_of = [&](uint64_t k) {
-      const uint32_t c = (uint32_t)((k >> lo) - cbase);
-      return direct ? c : (c * 0x9E3779B1u) >> (32 - FILTER_BITS);
-    };
-    uint64_t key[ITEMS];
-    for (int64_t c0 = 0; c0 < m; c0 += cap) {
-      const int cm = (int)min((int64_t)cap, m - c0);
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const int pos = wbase + i * 32 + (int)lane;
-        key[i] = pos < cm ? A[p + c0 + pos] : 0ull;
-      }
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        if (wbase + i * 32 + (int)lane < cm) {
-          const uint32_t h = bit_of(key[i]), bit = 1u << (h & 31u);
-          if (atomicOr(&seen[h >> 5], bit) & bit) atomicOr(&again[h >> 5], bit);
-        }
-      }
-    }
-    if (threadIdx.x == 0) s_nlist = 0;
-    __syncthreads();
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int64_t c0 = 0; c0 < m; c0 += cap) {
-      const int cm = (int)min((int64_t)cap, m - c0);
-      if (m > cap) {  // more than one chunk: the registers hold the last one
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-          const int pos = wbase + i * 32 + (int)lane;
-          key[i] = pos < cm ? A[p + c0 + pos] : 0ull;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        bool keep = false;
-        if (wbase + i * 32 + (int)lane < cm) {
-          const uint32_t h = bit_of(key[i]);
-          keep = (again[h >> 5] >> (h & 31u)) & 1u;
-        }
-        const uint32_t bal = __ballot_sync(FULL_MASK, keep);
-        uint32_t at = 0;
-        if (lane == 0 && bal) at = atomicAdd(&s_nlist, (uint32_t)__popc(bal));
-        at = __shfl_sync(FULL_MASK, at, 0) + (uint32_t)__popc(bal & lt_mask);
-        if (keep && at < (uint32_t)cap) s_k[at] = key[i];
-      }
-    }
-    __syncthreads();
-    const uint32_t kept = s_nlist;
-    if (kept > (uint32_t)cap) return false;
-    if (kept > 0) segment(0, kept, bA, 0, false, s_k);
-    return true;
-  };
-
-  if constexpr (HASH) {
-    if (cand && filter(s, e, (uint64_t)b0)) return;
-  }
   if (e - s <= cap) {
-    segment(s, e, (uint64_t)b0, kbits, HASH && !cand);
+    segment(s, e, (uint64_t)b0, kbits, HASH);
   } else {
     // too many records for one segment: bucket by bucket
     for (int64_t b = b0; b < b0 + K && b < nb; ++b) {
@@ -735,7 +649,8 @@ GroupingShape choose_grouping(uint64_t n_rec, int hs, bool hash) {
 void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
                    const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
                    uint64_t* flags, uint64_t* tile_counts, uint64_t* cand, uint64_t cand_cap,
-                   uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s) {
+                   uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s,
+                   const uint8_t* seg_flags) {
   if (n <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -756,15 +671,15 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
                                       : (double)n * 16.0 + (flags ? (double)n / 4.0 : 0.0);
   const unsigned long long* bs = reinterpret_cast<const unsigned long long*>(bucket_start);
   if (hash) {
-    prof_begin(s, "k_bucket_group", bytes);
+    prof_begin(s, seg_flags ? "k_bucket_group_flagged" : "k_bucket_group", seg_flags ? 0.0 : bytes);
     k_bucket<true><<<(unsigned)blocks, BK_THREADS, Bk<true>::bytes, s>>>(
         A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, cand, cand_cap,
-        reinterpret_cast<unsigned long long*>(cand_count), id_bits, err);
+        reinterpret_cast<unsigned long long*>(cand_count), id_bits, seg_flags, err);
   } else {
     prof_begin(s, "k_bucket_sort", bytes);
     k_bucket<false><<<(unsigned)blocks, BK_THREADS, Bk<false>::bytes, s>>>(
         A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, nullptr, 0, nullptr,
-        0, err);
+        0, nullptr, err);
   }
   prof_end(s);
 }

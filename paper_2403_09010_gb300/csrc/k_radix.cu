@@ -374,245 +374,13 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
 }
 
-// ---------------------------------------------------------------------------
-// Pipelined onesweep pass: persistent blocks (a few per SM) take tiles in
-// start order and keep the next tile's load in flight while they rank,
-// scatter and write the current one.  Each full tile arrives in shared memory
-// by one bulk asynchronous copy (cp.async.bulk, completion counted on an
-// mbarrier); the last, partial tile is read by the threads themselves.  A tile
-// is read from its buffer into registers, ranked, scattered back into the
-// same buffer in digit order and written out from there, so two tile buffers
-// per block suffice.  Same ranking, look-back and outputs as k_onesweep.
-template <int THREADS, int ITEMS, int MATCH>
-struct PipeSmem {
-  static constexpr int WARPS = THREADS / 32;
-  static constexpr int TILE = THREADS * ITEMS;
-  static constexpr size_t buf_bytes = (size_t)TILE * 8;
-  static constexpr size_t whist_bytes = (size_t)WARPS * RADIX * 4;
-  static constexpr size_t match_bytes = MATCH == 2 ? whist_bytes : 0;
-  static constexpr size_t bytes = 2 * buf_bytes + whist_bytes + match_bytes + RADIX * 4 + RADIX * 8;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
-// global memory into this block's shared memory, counted on `bar`.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-template <int THREADS, int ITEMS, int MIN_BLOCKS, int MATCH>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
-    k_onesweep_pipe(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                    const uint64_t* __restrict__ n_dev, int64_t n_cap, int shift, int bits,
-                    const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
-                    uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
-                    uint32_t* __restrict__ next_hist, int next_bits,
-                    unsigned long long* __restrict__ bucket_start, int bucket_shift) {
-  using SM = PipeSmem<THREADS, ITEMS, MATCH>;
-  constexpr int WARPS = SM::WARPS;
-  constexpr int TILE = SM::TILE;
-  static_assert(THREADS >= RADIX, "one thread per digit");
-  static_assert(SM::buf_bytes % 16 == 0, "both buffers stay 16-byte aligned for bulk copies");
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* s_buf[2] = {reinterpret_cast<uint64_t*>(smem),
-                        reinterpret_cast<uint64_t*>(smem + SM::buf_bytes)};
-  uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem + 2 * SM::buf_bytes);
-  uint32_t* s_match = s_whist + WARPS * RADIX;  // MATCH == 2 only
-  uint32_t* s_tstart = reinterpret_cast<uint32_t*>(smem + 2 * SM::buf_bytes + SM::whist_bytes +
-                                                   SM::match_bytes);
-  int64_t* s_obase = reinterpret_cast<int64_t*>(s_tstart + RADIX);
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ uint32_t s_tile[2];
-  __shared__ uint32_t s_wsum[WARPS];
-  __shared__ uint32_t s_next[RADIX];
-
-  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
-  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  const uint32_t dmask = (1u << bits) - 1u;
-  const uint32_t limit = spin_limit(err);
-  if (next_hist)
-    for (int k = threadIdx.x; k < RADIX; k += THREADS) s_next[k] = 0;
-  for (int k = threadIdx.x; k < WARPS * RADIX; k += THREADS) {
-    s_whist[k] = 0;
-    if (MATCH == 2) s_match[k] = 0;
-  }
-  // a bulk copy needs a 16-byte aligned source: otherwise every tile is read
-  // by the threads
-  const bool bulk_ok = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
-  // take a tile and, when it is full, start its bulk load into buffer b
-  auto take = [&](int b) {
-    const uint32_t t = atomicAdd(ctr, 1u);
-    s_tile[b] = t;
-    const int64_t base = (int64_t)t * TILE;
-    if (bulk_ok && base + TILE <= n) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&s_bar[b], (uint32_t)SM::buf_bytes);
-      bulk_load(s_buf[b], in + base, (uint32_t)SM::buf_bytes, &s_bar[b]);
-    }
-  };
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    take(0);
-  }
-  __syncthreads();
-  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
-  for (int k = 0;; ++k) {
-    const int b = k & 1;
-    const uint32_t tile = s_tile[b];
-    const int64_t tile_base = (int64_t)tile * TILE;
-    if (tile_base >= n) break;  // block-uniform
-    const bool full = tile_base + TILE <= n;
-    // the next tile's load runs while this one is processed (its buffer was
-    // last read before the barrier that ended the previous iteration)
-    if (threadIdx.x == 0) take(b ^ 1);
-    uint64_t* buf = s_buf[b];
-    if (full && bulk_ok) {
-      uint32_t spins = 0;
-      while (!mbar_try_wait(&s_bar[b], (phase >> b) & 1u)) {
-        if (++spins > limit) {  // give up: flag it, wait (bounded) for the copy, leave
-          if (threadIdx.x == 0) atomicOr(err, DERR_TIMEOUT);
-          for (uint32_t w = 0; w < limit && !mbar_try_wait(&s_bar[b], (phase >> b) & 1u); ++w) {
-          }
-          break;
-        }
-      }
-      phase ^= 1u << b;
-    } else {
-      for (int64_t j = threadIdx.x; j < n - tile_base; j += THREADS) buf[j] = __ldcs(in + tile_base + j);
-      __syncthreads();
-    }
-    // 1. keys into registers (warp w holds positions w*32*ITEMS + i*32 + lane)
-    uint64_t key[ITEMS];
-    const int wbase = (int)warp * 32 * ITEMS;
-    const int64_t gwbase = tile_base + wbase;
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const int pos = wbase + i * 32 + (int)lane;
-      key[i] = (full || tile_base + pos < n) ? buf[pos] : 0ull;
-    }
-    // 2. ranking
-    uint32_t* wh = s_whist + warp * RADIX;
-    uint32_t* mb = s_match + warp * RADIX;
-    uint16_t rank[ITEMS];
-    if (full) rank_items<ITEMS, MATCH, true>(key, rank, wh, mb, gwbase, n, shift, dmask, lane);
-    else rank_items<ITEMS, MATCH, false>(key, rank, wh, mb, gwbase, n, shift, dmask, lane);
-    __syncthreads();  // counts complete; every key of the buffer is in registers
-    // 3. per-warp offsets, tile counts, aggregates
-    uint32_t tcount = 0;
-    if (threadIdx.x < RADIX) {
-      uint32_t run = 0;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) {
-        const uint32_t c = s_whist[w * RADIX + threadIdx.x];
-        s_whist[w * RADIX + threadIdx.x] = run;
-        run += c;
-      }
-      tcount = run;
-      st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], (tile == 0 ? ST_INC : ST_AGG) | run);
-    }
-    {
-      const uint32_t v = tcount;
-      uint32_t inc = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(FULL_MASK, inc, o);
-        if (lane >= (uint32_t)o) inc += t;
-      }
-      if (lane == 31) s_wsum[warp] = inc;
-      __syncthreads();
-      if (threadIdx.x < RADIX) {
-        uint32_t off = 0;
-        for (uint32_t w = 0; w < warp; ++w) off += s_wsum[w];
-        const uint32_t ts = off + inc - v;
-        s_tstart[threadIdx.x] = ts;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) s_whist[w * RADIX + threadIdx.x] += ts;
-      }
-      __syncthreads();
-    }
-    // 4. scatter into the same buffer in digit order
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      if (full || gwbase + i * 32 + lane < n) {
-        const uint32_t dig = (uint32_t)(key[i] >> shift) & dmask;
-        const uint32_t pos = wh[dig] + rank[i];
-        if (pos < (uint32_t)TILE) buf[pos] = key[i];
-        else atomicOr(err, DERR_RANGE);
-      }
-    }
-    // 5. look-back per digit
-    if (threadIdx.x < RADIX) {
-      uint64_t excl = 0;
-      if (tile > 0) {
-        excl = thread_lookback(status + threadIdx.x, tile, RADIX, err);
-        st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], ST_INC | (excl + tcount));
-      }
-      s_obase[threadIdx.x] =
-          (int64_t)(digit_base[threadIdx.x] + excl) - (int64_t)s_tstart[threadIdx.x];
-    }
-    __syncthreads();
-    // 6. write out in digit order (next pass's digits and bucket starts as
-    // in k_onesweep); the counters are cleared for the next tile
-    for (int k2 = threadIdx.x; k2 < WARPS * RADIX; k2 += THREADS) s_whist[k2] = 0;
-    const int tile_n = full ? TILE : (int)(n - tile_base);
-    for (int j = threadIdx.x; j < tile_n; j += THREADS) {
-      const uint64_t kv = buf[j];
-      const uint32_t dig = (uint32_t)(kv >> shift) & dmask;
-      if (next_hist) atomicAdd(&s_next[(uint32_t)(kv >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
-      const int64_t o = s_obase[dig] + j;
-      if (o >= 0 && o < n) out[o] = kv;
-      else atomicOr(err, DERR_RANGE);
-      if (bucket_start && o >= 0 && o < n) {
-        const uint64_t bk = kv >> bucket_shift;
-        if (j == 0 || j == (int)s_tstart[dig] || bk != (buf[j - 1] >> bucket_shift))
-          atomicMin(&bucket_start[bk], (unsigned long long)o);
-      }
-    }
-    __syncthreads();  // the buffer and the offsets are reused
-  }
-  if (next_hist) {
-    __syncthreads();
-    if (threadIdx.x < RADIX && s_next[threadIdx.x]) atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
-  }
-}
-
 // Tile configurations (id, threads, items per thread, min blocks per SM,
 // ranking: 0 ballots / 1 match.any / 2 atomic-OR bins / 3 ballots with one
 // leader atomic per group / 4 unstable, one atomic per key, ranking chains).
 // Both sorts use configuration 9 by default; the autotuner may pick others
-// among 0-22 (20-22 are pipelined, k_onesweep_pipe).  Configurations 100-103
-// are unstable, only for the first pass of a sort, whose input order does
-// not matter; 100 matches the tile of 0-19's default 9, 101-103 those of
-// 20-22 (see onesweep_unstable_config).
+// among 0-19.  Configuration 100 is unstable, only for the first pass of a
+// sort, whose input order does not matter; its tile is that of the default 9
+// (see onesweep_unstable_config).
 #define XTN_ONESWEEP_CONFIGS(X) \
   X(0, 256, 16, 3, 0, 1)           \
   X(1, 256, 24, 2, 0, 1)           \
@@ -636,54 +404,19 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   X(19, 512, 12, 2, 3, 1)       \
   X(100, 256, 20, 3, 4, 1)
 
-// Pipelined configurations (id, threads, items per thread, blocks per SM,
-// ranking): 20-22 stable, 101-103 their unstable first passes.
-#define XTN_PIPE_CONFIGS(X) \
-  X(20, 256, 8, 4, 2)        \
-  X(21, 256, 12, 3, 2)       \
-  X(22, 256, 16, 2, 2)       \
-  X(101, 256, 8, 4, 4)       \
-  X(102, 256, 12, 3, 4)      \
-  X(103, 256, 16, 2, 4)
-
 int onesweep_tile(int cfg) {
   switch (cfg) {
 #define X(id, T, I, B, M, C) \
   case id: return T * I;
     XTN_ONESWEEP_CONFIGS(X)
 #undef X
-#define X(id, T, I, B, M) \
-  case id: return T * I;
-    XTN_PIPE_CONFIGS(X)
-#undef X
   }
   return 0;
 }
 
-int onesweep_configs() { return 23; }  // the tunable (stable) ones, 0-22
+int onesweep_configs() { return 20; }  // the tunable (stable) ones, 0-19
 
-int onesweep_unstable_config(int cfg) {
-  switch (cfg) {
-    case 20: return 101;
-    case 21: return 102;
-    case 22: return 103;
-  }
-  return 100;
-}
-
-namespace {
-int device_sms() {
-  static int sms[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (!sms[dev]) {
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    sms[dev] = v > 0 ? v : 152;
-  }
-  return sms[dev];
-}
-}  // namespace
+int onesweep_unstable_config(int) { return 100; }
 
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    const uint64_t* n_dev, int shift, int bits, const uint64_t* digit_base,
@@ -712,27 +445,6 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
     return cudaGetLastError();                                                                \
   }
     XTN_ONESWEEP_CONFIGS(X)
-#undef X
-#define X(id, T, I, B, M)                                                                     \
-  case id: {                                                                                  \
-    using SM = PipeSmem<T, I, M>;                                                             \
-    static std::once_flag once;                                                               \
-    std::call_once(once, [] {                                                                 \
-      cudaFuncSetAttribute(k_onesweep_pipe<T, I, B, M>,                                       \
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);       \
-      cudaFuncSetAttribute(k_onesweep_pipe<T, I, B, M>,                                       \
-                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
-    });                                                                                       \
-    /* persistent: B blocks per SM take the tiles in start order */                          \
-    const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
-    const uint32_t blocks = std::min<uint32_t>(tiles, (uint32_t)(device_sms() * B));          \
-    k_onesweep_pipe<T, I, B, M><<<blocks, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits,  \
-                                                             digit_base, status, ctr, err,    \
-                                                             next_hist, next_bits,            \
-                                                             bucket_start, bucket_shift);     \
-    return cudaGetLastError();                                                                \
-  }
-    XTN_PIPE_CONFIGS(X)
 #undef X
   }
   return cudaErrorInvalidValue;

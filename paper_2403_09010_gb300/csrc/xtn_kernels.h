@@ -101,10 +101,26 @@ int bucket_capacity(bool hash);
 // to cand[0, cand_cap), counting them in cand_count[0] (DERR_CAPACITY past
 // the capacity); larger buckets go the flag route as before and add their
 // record count to cand_count[1].
+// seg_flags (one byte per block of buckets): when given, only the blocks whose
+// flag is set run (the ones k_bucket_filter left).
 void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
                    const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
                    uint64_t* flags, uint64_t* tile_counts, uint64_t* cand, uint64_t cand_cap,
-                   uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s);
+                   uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s,
+                   const uint8_t* seg_flags = nullptr);
+// k_filter.cu --------------------------------------------------------------
+// Candidate mode of the grouping for the blocks of buckets of the shape g
+// (2^kbits buckets each, G global bits): a persistent kernel keeps only the
+// records whose group key occurs twice or more (two bitmaps), groups those
+// exactly in shared memory and appends their pairs to cand as k_bucket does.
+// Blocks of buckets with more records than it holds at once, or too many kept
+// records, get seg_flags[block] = 1 (seg_flags zeroed, seg_ctr zeroed) for
+// launch_bucket(..., seg_flags).
+void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
+                          const uint64_t* bucket_start, const GroupingShape& g, int lo,
+                          uint64_t* cand, uint64_t cand_cap, uint64_t* cand_count, int id_bits,
+                          uint8_t* seg_flags, uint32_t* seg_ctr, int sms, uint32_t* err,
+                          cudaStream_t s);
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
 size_t group_status_bytes(int64_t n);
