@@ -367,6 +367,10 @@ XTN_API int xtn_tcrdist_filter_noalloc(const uint8_t* seqs, const int64_t* offse
  *                           passes on every bit, then a flag pass; 2 = as 0
  *                           with 512-record shared-memory segments (slower;
  *                           more buckets take the large-bucket path)
+ *   XTN_TUNE_FILTER_SEGMENT : grouping mode 0 groups each block of buckets
+ *                           with a singleton filter first; its blocks hold
+ *                           2^value times the buckets of the shared-memory
+ *                           pass (0..3)
  * Every value gives the same result; they differ in threads per block, keys
  * per thread, ranking method and counting, hence in speed per GPU and size.
  * xtn_tune_set returns XTN_ERR_INVALID_ARG for an unknown knob or value.
@@ -375,7 +379,8 @@ enum {
   XTN_TUNE_SORT_RECORDS = 0,
   XTN_TUNE_SORT_PAIRS = 1,
   XTN_TUNE_RECORD_HISTOGRAM = 2,
-  XTN_TUNE_GROUPING = 3
+  XTN_TUNE_GROUPING = 3,
+  XTN_TUNE_FILTER_SEGMENT = 4
 };
 XTN_API int xtn_tune_set(int knob, int value);
 XTN_API int xtn_tune_get(int knob);

@@ -6,8 +6,8 @@ its thin Python binding.  ``build()`` compiles the library.
 """
 from .buildlib import build  # noqa: F401
 from .native import XtnError, LIB_PATH  # noqa: F401
-from .native import (XTN_TUNE_GROUPING, XTN_TUNE_RECORD_HISTOGRAM,  # noqa: F401
-                     XTN_TUNE_SORT_PAIRS, XTN_TUNE_SORT_RECORDS)
+from .native import (XTN_TUNE_FILTER_SEGMENT, XTN_TUNE_GROUPING,  # noqa: F401
+                     XTN_TUNE_RECORD_HISTOGRAM, XTN_TUNE_SORT_PAIRS, XTN_TUNE_SORT_RECORDS)
 from .xtn import (Index, Plan, index_build, profile_enable, profile_report,  # noqa: F401
                   scratch_trim, search_between, search_paired, search_query, search_self,
                   search_self_streaming,

@@ -351,6 +351,8 @@ std::atomic<int> g_record_hist{0};
 // shared-memory segments (more buckets take the large-bucket path).
 std::atomic<int> g_grouping{0};
 }  // namespace
+// Buckets per block of the singleton filter: 2^fx of k_bucket's blocks.
+std::atomic<int> g_filter_fx{1};
 std::atomic<int>& cfg_records() { return g_cfg_records; }
 std::atomic<int>& cfg_pairs() { return g_cfg_pairs; }
 namespace {
@@ -386,9 +388,16 @@ int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar
     XTN_CK(host_sync(s));
     if (first != 0 || total < 0) return XTN_ERR_INVALID_ARG;
   } else {
-    int rc = check_host_offsets(offsets, n);
-    if (rc) return rc;
+    // O(1) on the host: the letters copied are offsets[n] bytes, at most 25
+    // per sequence; a decreasing offset or a sequence longer than 25 inside
+    // that total is found by k_encode on the device (error word).  Past the
+    // total bound, the full host check names the error.
     total = offsets[n];
+    if (offsets[0] != 0 || total < 0) return XTN_ERR_INVALID_ARG;
+    if (total > (int64_t)XTN_MAX_LEN * n) {
+      const int rc = check_host_offsets(offsets, n);
+      return rc ? rc : XTN_ERR_INVALID_ARG;
+    }
     int64_t* d = ar.get<int64_t>(n + 1);
     XTN_ALLOC_OK(ar);
     XTN_CK(cudaMemcpyAsync(d, offsets, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -585,9 +594,9 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
     // k_bucket takes only the blocks it flags
     XTN_CK(cudaMemsetAsync(gs.seg_area, 0, seg_area_bytes(rec_cap, 64 - lo), s));
     uint8_t* seg_flags = gs.seg_area + 16;
-    launch_bucket_filter(X, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo, gs.cand,
-                         gs.cand_cap, gs.cand_count, id_bits, seg_flags,
-                         reinterpret_cast<uint32_t*>(gs.seg_area), sms, err, s);
+    launch_bucket_filter(X, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g,
+                         g_filter_fx.load(), lo, gs.cand, gs.cand_cap, gs.cand_count, id_bits,
+                         seg_flags, err, s);
     launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo, 0, gs.flags,
                   tile_counts, gs.cand, gs.cand_cap, gs.cand_count, id_bits, err, s, seg_flags);
   } else {
@@ -1873,6 +1882,7 @@ int xtn_tune_set(int knob, int value) {
     case XTN_TUNE_GROUPING: xtn::g_grouping.store(value); return XTN_OK;
     case XTN_TUNE_SORT_RECORDS: xtn::cfg_records().store(value); return XTN_OK;
     case XTN_TUNE_SORT_PAIRS: xtn::cfg_pairs().store(value); return XTN_OK;
+    case XTN_TUNE_FILTER_SEGMENT: xtn::g_filter_fx.store(value); return XTN_OK;
   }
   return XTN_ERR_INVALID_ARG;
 }
@@ -1883,6 +1893,7 @@ int xtn_tune_get(int knob) {
     case XTN_TUNE_SORT_PAIRS: return xtn::cfg_pairs().load();
     case XTN_TUNE_RECORD_HISTOGRAM: return xtn::g_record_hist.load();
     case XTN_TUNE_GROUPING: return xtn::g_grouping.load();
+    case XTN_TUNE_FILTER_SEGMENT: return xtn::g_filter_fx.load();
   }
   return XTN_ERR_INVALID_ARG;
 }
@@ -1893,6 +1904,7 @@ int xtn_tune_count(int knob) {
     case XTN_TUNE_SORT_PAIRS: return xtn::onesweep_configs();
     case XTN_TUNE_RECORD_HISTOGRAM: return 2;
     case XTN_TUNE_GROUPING: return 3;
+    case XTN_TUNE_FILTER_SEGMENT: return 4;
   }
   return XTN_ERR_INVALID_ARG;
 }

@@ -109,18 +109,16 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
                    uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s,
                    const uint8_t* seg_flags = nullptr);
 // k_filter.cu --------------------------------------------------------------
-// Candidate mode of the grouping for the blocks of buckets of the shape g
-// (2^kbits buckets each, G global bits): a persistent kernel keeps only the
-// records whose group key occurs twice or more (two bitmaps), groups those
-// exactly in shared memory and appends their pairs to cand as k_bucket does.
-// Blocks of buckets with more records than it holds at once, or too many kept
-// records, get seg_flags[block] = 1 (seg_flags zeroed, seg_ctr zeroed) for
-// launch_bucket(..., seg_flags).
+// Candidate mode of the grouping for the buckets of shape g (G global bits):
+// each block takes 2^(kbits + fx) buckets, keeps only the records whose group
+// key occurs twice or more (two bitmaps), groups those exactly in shared
+// memory and appends their pairs to cand as k_bucket does.  A block whose
+// kept records overflow sets seg_flags (zeroed, one byte per k_bucket block)
+// for the k_bucket blocks it covers, for launch_bucket(..., seg_flags).
 void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
-                          const uint64_t* bucket_start, const GroupingShape& g, int lo,
+                          const uint64_t* bucket_start, const GroupingShape& g, int fx, int lo,
                           uint64_t* cand, uint64_t cand_cap, uint64_t* cand_count, int id_bits,
-                          uint8_t* seg_flags, uint32_t* seg_ctr, int sms, uint32_t* err,
-                          cudaStream_t s);
+                          uint8_t* seg_flags, uint32_t* err, cudaStream_t s);
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
 size_t group_status_bytes(int64_t n);

@@ -27,6 +27,7 @@ XTN_TUNE_SORT_RECORDS = 0
 XTN_TUNE_SORT_PAIRS = 1
 XTN_TUNE_RECORD_HISTOGRAM = 2
 XTN_TUNE_GROUPING = 3
+XTN_TUNE_FILTER_SEGMENT = 4
 XTN_NOALLOC_MAX_SEQS = 1 << 18
 XTN_NOALLOC_MAX_ROWS = 1 << 22
 XTN_MAX_LEN = 25

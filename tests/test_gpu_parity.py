@@ -132,7 +132,8 @@ def test_input_errors(xtn):
     from paper_2403_09010_gb300 import native
     for strs, code in [(["CASSF", "CAXSF"], native.XTN_ERR_BAD_RESIDUE),
                        (["CASSF", "cassf"], native.XTN_ERR_BAD_RESIDUE),
-                       (["A" * 26], native.XTN_ERR_SEQ_TOO_LONG)]:
+                       (["A" * 26], native.XTN_ERR_SEQ_TOO_LONG),
+                       (["A" * 26, "", ""], native.XTN_ERR_SEQ_TOO_LONG)]:
         seqs, off = gen.from_strings(strs)
         with pytest.raises(native.XtnError) as ei:
             xtn.search_self(seqs, off, 1)
@@ -142,6 +143,16 @@ def test_input_errors(xtn):
         with pytest.raises(native.XtnError) as ei:
             xtn.search_self(ds, do, 1)
         assert ei.value.status == code
+
+
+def test_decreasing_offsets_are_rejected(xtn):
+    from paper_2403_09010_gb300 import native
+    seqs, _ = gen.from_strings(["CASSF", "CASF"])
+    off = np.array([0, 5, 3, 9], dtype=np.int64)      # a negative length inside the total
+    for s_, o_ in [(seqs, off), _dev(seqs, off)]:
+        with pytest.raises(native.XtnError) as ei:
+            xtn.search_self(s_, o_, 1)
+        assert ei.value.status == native.XTN_ERR_INVALID_ARG
 
 
 def test_every_sort_configuration(xtn):
