@@ -520,7 +520,7 @@ struct GroupScratch {
 
 size_t seg_area_bytes(uint64_t rec_cap, int hs) {
   const GroupingShape g = choose_grouping(rec_cap, hs, true);
-  return 16 + (((size_t)1 << g.G) >> g.kbits);
+  return 16 + 4 * (((size_t)1 << g.G) >> g.kbits);
 }
 
 size_t bucket_start_words(uint64_t rec_cap, int hs, int mode) {
@@ -591,14 +591,16 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
   }
   if (hash && gs.cand && gs.seg_area && mode == 0) {
     // the singleton filter groups and emits nearly every block of buckets;
-    // k_bucket takes only the blocks it flags
-    XTN_CK(cudaMemsetAsync(gs.seg_area, 0, seg_area_bytes(rec_cap, 64 - lo), s));
-    uint8_t* seg_flags = gs.seg_area + 16;
+    // k_bucket takes only the blocks it lists
+    uint32_t* seg_count = reinterpret_cast<uint32_t*>(gs.seg_area);
+    uint32_t* seg_list = reinterpret_cast<uint32_t*>(gs.seg_area + 16);
+    XTN_CK(cudaMemsetAsync(seg_count, 0, 16, s));
     launch_bucket_filter(X, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g,
                          g_filter_fx.load(), lo, gs.cand, gs.cand_cap, gs.cand_count, id_bits,
-                         seg_flags, err, s);
+                         seg_list, seg_count, err, s);
     launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo, 0, gs.flags,
-                  tile_counts, gs.cand, gs.cand_cap, gs.cand_count, id_bits, err, s, seg_flags);
+                  tile_counts, gs.cand, gs.cand_cap, gs.cand_count, id_bits, err, s, seg_list,
+                  seg_count, sms);
   } else {
     launch_bucket(hash, X, Y, (int64_t)rec_cap, n_rec_dev, gs.bucket_start, g, lo,
                   mode == 2 ? 512 : 0, gs.flags, tile_counts, hash ? gs.cand : nullptr,

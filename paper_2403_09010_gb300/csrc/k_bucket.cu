@@ -229,17 +229,14 @@ __device__ __forceinline__ void write_flags(int64_t p, int64_t m, GKey gkey, uin
   }
 }
 
+// One block of buckets (number blk) of k_bucket.
 template <bool HASH>
-__global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
-    k_bucket(uint64_t* __restrict__ A, uint64_t* __restrict__ Y, int64_t n_cap,
-             const uint64_t* __restrict__ n_dev,
-             const unsigned long long* __restrict__ bucket_start, int G, int kbits, int lo, int L,
-             int cap, uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts,
-             uint64_t* __restrict__ cand, uint64_t cand_cap,
-             unsigned long long* __restrict__ cand_count, int id_bits,
-             const uint8_t* __restrict__ seg_flags, uint32_t* __restrict__ err) {
-  // with seg_flags, only the segments the singleton filter flagged
-  if (seg_flags && !seg_flags[blockIdx.x]) return;
+__device__ __forceinline__ void bucket_block(
+    uint64_t blk, uint64_t* __restrict__ A, uint64_t* __restrict__ Y, int64_t n_cap,
+    const uint64_t* __restrict__ n_dev, const unsigned long long* __restrict__ bucket_start, int G,
+    int kbits, int lo, int L, int cap, uint64_t* __restrict__ flags,
+    uint64_t* __restrict__ tile_counts, uint64_t* __restrict__ cand, uint64_t cand_cap,
+    unsigned long long* __restrict__ cand_count, int id_bits, uint32_t* __restrict__ err) {
   using C = Bk<HASH>;
   constexpr int ITEMS = C::ITEMS;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -254,7 +251,7 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
   const int64_t nb = 1ll << G;
   const int64_t K = 1ll << kbits;
-  const int64_t b0 = (int64_t)blockIdx.x * K;
+  const int64_t b0 = (int64_t)blk * K;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const int wbase = (int)warp * 32 * ITEMS;
 
@@ -623,6 +620,36 @@ __global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
   }
 }
 
+// Every block of buckets, or with seg_list only the *seg_count blocks listed
+// there (the ones the singleton filter left), in a grid-stride loop.
+template <bool HASH>
+__global__ void __launch_bounds__(BK_THREADS, Bk<HASH>::MIN_BLOCKS)
+    k_bucket(uint64_t* __restrict__ A, uint64_t* __restrict__ Y, int64_t n_cap,
+             const uint64_t* __restrict__ n_dev,
+             const unsigned long long* __restrict__ bucket_start, int G, int kbits, int lo, int L,
+             int cap, uint64_t* __restrict__ flags, uint64_t* __restrict__ tile_counts,
+             uint64_t* __restrict__ cand, uint64_t cand_cap,
+             unsigned long long* __restrict__ cand_count, int id_bits,
+             const uint32_t* __restrict__ seg_list, const uint32_t* __restrict__ seg_count,
+             uint32_t* __restrict__ err) {
+  if (!seg_list) {
+    bucket_block<HASH>(blockIdx.x, A, Y, n_cap, n_dev, bucket_start, G, kbits, lo, L, cap, flags,
+                       tile_counts, cand, cand_cap, cand_count, id_bits, err);
+    return;
+  }
+  const uint32_t count = *seg_count;
+  const uint64_t n_blocks = ((uint64_t)1 << G) >> kbits;
+  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const uint32_t blk = seg_list[i];
+    if (blk < n_blocks)
+      bucket_block<HASH>(blk, A, Y, n_cap, n_dev, bucket_start, G, kbits, lo, L, cap, flags,
+                         tile_counts, cand, cand_cap, cand_count, id_bits, err);
+    else if (threadIdx.x == 0)
+      atomicOr(err, DERR_RANGE);
+    __syncthreads();  // shared memory is reused by the next listed block
+  }
+}
+
 }  // namespace
 
 int bucket_capacity(bool hash) { return hash ? Bk<true>::CAP : Bk<false>::CAP; }
@@ -650,7 +677,7 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
                    const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
                    uint64_t* flags, uint64_t* tile_counts, uint64_t* cand, uint64_t cand_cap,
                    uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s,
-                   const uint8_t* seg_flags) {
+                   const uint32_t* seg_list, const uint32_t* seg_count, int sms) {
   if (n <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -663,7 +690,9 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
   });
   const int full = bucket_capacity(hash);
   if (cap <= 0 || cap > full) cap = full;
-  const uint64_t blocks = ((uint64_t)1 << g.G) >> g.kbits;
+  // a listed subset runs in a grid-stride loop over the list
+  const uint64_t blocks = seg_list ? (uint64_t)std::max(1, sms) * Bk<true>::MIN_BLOCKS
+                                   : ((uint64_t)1 << g.G) >> g.kbits;
   // algorithmic bytes: every record read once; written back unless the
   // candidates leave straight from shared memory (their words are not counted:
   // their number is unknown at launch and small next to the records)
@@ -671,15 +700,15 @@ void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_
                                       : (double)n * 16.0 + (flags ? (double)n / 4.0 : 0.0);
   const unsigned long long* bs = reinterpret_cast<const unsigned long long*>(bucket_start);
   if (hash) {
-    prof_begin(s, seg_flags ? "k_bucket_group_flagged" : "k_bucket_group", seg_flags ? 0.0 : bytes);
+    prof_begin(s, seg_list ? "k_bucket_group_listed" : "k_bucket_group", seg_list ? 0.0 : bytes);
     k_bucket<true><<<(unsigned)blocks, BK_THREADS, Bk<true>::bytes, s>>>(
         A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, cand, cand_cap,
-        reinterpret_cast<unsigned long long*>(cand_count), id_bits, seg_flags, err);
+        reinterpret_cast<unsigned long long*>(cand_count), id_bits, seg_list, seg_count, err);
   } else {
     prof_begin(s, "k_bucket_sort", bytes);
     k_bucket<false><<<(unsigned)blocks, BK_THREADS, Bk<false>::bytes, s>>>(
         A, Y, n, n_dev, bs, g.G, g.kbits, lo, g.L, cap, flags, tile_counts, nullptr, 0, nullptr,
-        0, nullptr, err);
+        0, nullptr, nullptr, err);
   }
   prof_end(s);
 }

@@ -18,8 +18,8 @@
 //      id_bits | max id), reserving output space once per warp.
 // Every phase spreads its work over all the block's threads, and the fixed
 // work per block (table clearing and scanning) scales with the kept records,
-// not with the segment.  A segment whose list overflows is flagged instead
-// (one flag per k_bucket block it covers); k_bucket then groups those blocks
+// not with the segment.  A segment whose list overflows appends the k_bucket
+// blocks it covers to a list instead; k_bucket then groups the listed blocks
 // as before.
 #include <algorithm>
 #include <mutex>
@@ -42,6 +42,7 @@ constexpr int BF_WORDS = (1 << BF_BITS) / 32;
 constexpr uint32_t BF_EMPTY = 0xffffffffu;
 constexpr uint32_t BF_NO_PLACE = 0xffffu;
 constexpr int BF_PT = BF_LIST / BF_THREADS;        // kept records per thread, at most
+constexpr uint32_t BF_SMALL = 8;                   // groups up to this size: one lane each
 
 constexpr unsigned long long BF_NO_START = ~0ull;
 
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
                     const unsigned long long* __restrict__ bucket_start, int G, int kf, int fx,
                     int lo, int L, uint64_t* __restrict__ cand, uint64_t cand_cap,
                     unsigned long long* __restrict__ cand_count, int id_bits,
-                    uint8_t* __restrict__ seg_flags, uint32_t* __restrict__ err) {
+                    uint32_t* __restrict__ seg_list, uint32_t* __restrict__ seg_count,
+                    uint32_t* __restrict__ err) {
   __shared__ __align__(16) uint32_t s_seen[BF_WORDS];
   __shared__ __align__(16) uint32_t s_again[BF_WORDS];
   __shared__ uint64_t s_list[BF_LIST];
@@ -158,8 +160,11 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
   __syncthreads();
   const uint32_t kept = s_nlist;
   if (kept > (uint32_t)BF_LIST) {  // too many: k_bucket groups this segment's blocks
-    const int64_t f0 = (int64_t)blockIdx.x << fx;
-    for (int64_t f = f0 + threadIdx.x; f < f0 + (1ll << fx); f += BF_THREADS) seg_flags[f] = 1;
+    __shared__ uint32_t s_at;
+    if (threadIdx.x == 0) s_at = atomicAdd(seg_count, 1u << fx);
+    __syncthreads();
+    const uint32_t f0 = (uint32_t)blockIdx.x << fx;
+    for (uint32_t f = threadIdx.x; f < (1u << fx); f += BF_THREADS) seg_list[s_at + f] = f0 + f;
     return;
   }
   if (kept < 2) return;
@@ -240,7 +245,21 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
       np += b * (b - 1) / 2;
     }
   }
-  // output room of this warp's groups, reserved once
+  // output room of this warp's groups, reserved once: the pairs of a lane's
+  // small groups (at most BF_SMALL ids) at the lane's offset, those of large
+  // groups after all small ones
+  uint32_t np_small = 0;
+  for (uint32_t g = gmask; g; g &= g - 1) {
+    const uint32_t c = s_tk[threadIdx.x * PER + (uint32_t)(__ffs(g) - 1)];
+    if (c <= BF_SMALL) np_small += c * (c - 1) / 2;
+  }
+  uint32_t small_incl = np_small;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL_MASK, small_incl, o);
+    if (lane >= (uint32_t)o) small_incl += t;
+  }
+  const uint32_t small_total = __shfl_sync(FULL_MASK, small_incl, 31);
   uint32_t wp = np;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wp += __shfl_xor_sync(FULL_MASK, wp, o);
@@ -266,8 +285,34 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
     }
   }
   __syncthreads();
-  // 5. every pair of every group of two or more, the warp spreading each
-  // group's pairs over its lanes (colex rank l = b (b - 1) / 2 + a, a < b)
+  auto word = [&](uint64_t ia, uint64_t ib) {
+    return ((ia < ib ? ia : ib) << id_bits) | (ia < ib ? ib : ia);
+  };
+  // 5a. small groups: the owning lane writes all their pairs
+  {
+    unsigned long long o = obase + (small_incl - np_small);
+    uint32_t large = 0;  // this lane's large groups (bit k: slot threadIdx.x * PER + k)
+    for (uint32_t g = gmask; g; g &= g - 1) {
+      const uint32_t k = (uint32_t)(__ffs(g) - 1);
+      const uint32_t h = threadIdx.x * PER + k;
+      const uint32_t c = s_tk[h];
+      if (c > BF_SMALL) {
+        large |= 1u << k;
+        continue;
+      }
+      const uint32_t gst = (s_tc[h >> 1] >> ((h & 1u) * 16)) & 0xffffu;
+      if (gst + c > (uint32_t)BF_LIST) continue;
+      for (uint32_t x = 0; x + 1 < c; ++x) {
+        const uint64_t ia = s_ids[gst + x];
+        for (uint32_t y = x + 1; y < c; ++y, ++o)
+          if (o < cand_cap) cand[o] = word(ia, s_ids[gst + y]);
+      }
+    }
+    gmask = large;
+  }
+  // 5b. large groups: the warp spreads each one's pairs over its lanes
+  // (colex rank l = b (b - 1) / 2 + a, a < b)
+  obase += small_total;
   while (__any_sync(FULL_MASK, gmask != 0)) {
     uint32_t st = 0, c = 0;
     if (gmask) {
@@ -288,11 +333,8 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
         while (bb * (bb - 1) / 2 > l) --bb;
         while ((bb + 1) * bb / 2 <= l) ++bb;
         const uint32_t aa = l - bb * (bb - 1) / 2;
-        if (gst + bb < (uint32_t)BF_LIST) {
-          const uint64_t ia = s_ids[gst + aa], ib = s_ids[gst + bb];
-          if (obase + l < cand_cap)
-            cand[obase + l] = ((ia < ib ? ia : ib) << id_bits) | (ia < ib ? ib : ia);
-        }
+        if (gst + bb < (uint32_t)BF_LIST && obase + l < cand_cap)
+          cand[obase + l] = word(s_ids[gst + aa], s_ids[gst + bb]);
       }
       obase += pairs;
     }
@@ -304,7 +346,7 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
 void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
                           const uint64_t* bucket_start, const GroupingShape& g, int fx, int lo,
                           uint64_t* cand, uint64_t cand_cap, uint64_t* cand_count, int id_bits,
-                          uint8_t* seg_flags, uint32_t* err, cudaStream_t s) {
+                          uint32_t* seg_list, uint32_t* seg_count, uint32_t* err, cudaStream_t s) {
   if (n <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -317,8 +359,8 @@ void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
   prof_begin(s, "k_bucket_filter", (double)n * 8.0);
   k_bucket_filter<<<(uint32_t)blocks, BF_THREADS, 0, s>>>(
       A, n, n_dev, reinterpret_cast<const unsigned long long*>(bucket_start), g.G, kf, fx, lo,
-      g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits, seg_flags,
-      err);
+      g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits, seg_list,
+      seg_count, err);
   prof_end(s);
 }
 

@@ -101,24 +101,26 @@ int bucket_capacity(bool hash);
 // to cand[0, cand_cap), counting them in cand_count[0] (DERR_CAPACITY past
 // the capacity); larger buckets go the flag route as before and add their
 // record count to cand_count[1].
-// seg_flags (one byte per block of buckets): when given, only the blocks whose
-// flag is set run (the ones k_bucket_filter left).
+// seg_list / seg_count: when given, only the *seg_count blocks of buckets
+// listed (the ones k_bucket_filter left), by a grid of sms x 5 blocks.
 void launch_bucket(bool hash, uint64_t* A, uint64_t* Y, int64_t n, const uint64_t* n_dev,
                    const uint64_t* bucket_start, const GroupingShape& g, int lo, int cap,
                    uint64_t* flags, uint64_t* tile_counts, uint64_t* cand, uint64_t cand_cap,
                    uint64_t* cand_count, int id_bits, uint32_t* err, cudaStream_t s,
-                   const uint8_t* seg_flags = nullptr);
+                   const uint32_t* seg_list = nullptr, const uint32_t* seg_count = nullptr,
+                   int sms = 0);
 // k_filter.cu --------------------------------------------------------------
 // Candidate mode of the grouping for the buckets of shape g (G global bits):
 // each block takes 2^(kbits + fx) buckets, keeps only the records whose group
 // key occurs twice or more (two bitmaps), groups those exactly in shared
 // memory and appends their pairs to cand as k_bucket does.  A block whose
-// kept records overflow sets seg_flags (zeroed, one byte per k_bucket block)
-// for the k_bucket blocks it covers, for launch_bucket(..., seg_flags).
+// kept records overflow appends the k_bucket blocks it covers to seg_list
+// (counted in *seg_count, zeroed; room for every k_bucket block), for
+// launch_bucket(..., seg_list, seg_count).
 void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
                           const uint64_t* bucket_start, const GroupingShape& g, int fx, int lo,
                           uint64_t* cand, uint64_t cand_cap, uint64_t* cand_count, int id_bits,
-                          uint8_t* seg_flags, uint32_t* err, cudaStream_t s);
+                          uint32_t* seg_list, uint32_t* seg_count, uint32_t* err, cudaStream_t s);
 // k_pairs.cu ---------------------------------------------------------------
 size_t scan_status_bytes(int64_t n);
 size_t group_status_bytes(int64_t n);
