@@ -33,10 +33,9 @@ namespace {
 
 constexpr int BF_THREADS = 256;
 constexpr int BF_WARPS = BF_THREADS / 32;
-constexpr int BF_ITEMS = 8;                        // records per thread per chunk
-constexpr int BF_CHUNK = BF_THREADS * BF_ITEMS;    // records per chunk
 constexpr int BF_LIST = 1024;                      // records the filter may keep
 constexpr int BF_HMAX = 2 * BF_LIST;               // slots of the exact grouping, at most
+constexpr int BF_HCAP = 2 * BF_HMAX;               // records whose bitmap index is kept
 constexpr int BF_BITS = 16;                        // log2 of the bits of each filter bitmap
 constexpr int BF_WORDS = (1 << BF_BITS) / 32;
 constexpr uint32_t BF_EMPTY = 0xffffffffu;
@@ -113,49 +112,44 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
   auto bit_of = [&](uint32_t c) {
     return (direct ? c : (c * 0x9E3779B1u) >> (32 - BF_BITS)) & ((1u << BF_BITS) - 1u);
   };
-  const int wbase = (int)warp * 32 * BF_ITEMS;
-  // 1. mark keys seen and seen again (chunk by chunk; the last chunk stays in
-  // registers)
-  uint64_t key[BF_ITEMS];
-  for (int64_t c0 = 0; c0 < m; c0 += BF_CHUNK) {
-    const int cm = (int)min((int64_t)BF_CHUNK, m - c0);
+  // each record's bitmap index, kept for the compaction (the first BF_HCAP
+  // records; the key table is free until the exact grouping)
+  uint16_t* s_h = reinterpret_cast<uint16_t*>(s_tk);
+  // 1. mark keys seen and seen again; thread t takes records t + 256 k,
+  // four loads in flight at a time
+  for (int64_t j0 = threadIdx.x; j0 < m; j0 += 4 * BF_THREADS) {
+    uint64_t k4[4];
 #pragma unroll
-    for (int i = 0; i < BF_ITEMS; ++i) {
-      const int pos = wbase + i * 32 + (int)lane;
-      key[i] = pos < cm ? A[s + c0 + pos] : 0ull;
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = j0 + u * BF_THREADS;
+      k4[u] = j < m ? A[s + j] : 0ull;
     }
 #pragma unroll
-    for (int i = 0; i < BF_ITEMS; ++i) {
-      if (wbase + i * 32 + (int)lane < cm) {
-        const uint32_t h = bit_of(comp(key[i])), bit = 1u << (h & 31u);
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = j0 + u * BF_THREADS;
+      if (j < m) {
+        const uint32_t h = bit_of(comp(k4[u])), bit = 1u << (h & 31u);
+        if (j < BF_HCAP) s_h[j] = (uint16_t)h;
         if (atomicOr(&s_seen[h >> 5], bit) & bit) atomicOr(&s_again[h >> 5], bit);
       }
     }
   }
   __syncthreads();
-  // 2. keep the records whose key was seen again
-  for (int64_t c0 = 0; c0 < m; c0 += BF_CHUNK) {
-    const int cm = (int)min((int64_t)BF_CHUNK, m - c0);
-    if (m > BF_CHUNK) {
-#pragma unroll
-      for (int i = 0; i < BF_ITEMS; ++i) {
-        const int pos = wbase + i * 32 + (int)lane;
-        key[i] = pos < cm ? A[s + c0 + pos] : 0ull;
-      }
+  // 2. keep the records whose key was seen again (the same records per
+  // thread as above, warp by warp for the ballots); a kept record is read
+  // again, from L2
+  for (int64_t j0 = (int64_t)warp * 32; j0 < m; j0 += BF_THREADS) {
+    const int64_t j = j0 + lane;
+    bool keep = false;
+    if (j < m) {
+      const uint32_t h = j < BF_HCAP ? (uint32_t)s_h[j] : bit_of(comp(A[s + j]));
+      keep = (s_again[h >> 5] >> (h & 31u)) & 1u;
     }
-#pragma unroll
-    for (int i = 0; i < BF_ITEMS; ++i) {
-      bool keep = false;
-      if (wbase + i * 32 + (int)lane < cm) {
-        const uint32_t h = bit_of(comp(key[i]));
-        keep = (s_again[h >> 5] >> (h & 31u)) & 1u;
-      }
-      const uint32_t bal = __ballot_sync(FULL_MASK, keep);
-      uint32_t at = 0;
-      if (lane == 0 && bal) at = atomicAdd(&s_nlist, (uint32_t)__popc(bal));
-      at = __shfl_sync(FULL_MASK, at, 0) + (uint32_t)__popc(bal & lt_mask);
-      if (keep && at < (uint32_t)BF_LIST) s_list[at] = key[i];
-    }
+    const uint32_t bal = __ballot_sync(FULL_MASK, keep);
+    uint32_t at = 0;
+    if (lane == 0 && bal) at = atomicAdd(&s_nlist, (uint32_t)__popc(bal));
+    at = __shfl_sync(FULL_MASK, at, 0) + (uint32_t)__popc(bal & lt_mask);
+    if (keep && at < (uint32_t)BF_LIST) s_list[at] = A[s + j];
   }
   __syncthreads();
   const uint32_t kept = s_nlist;
