@@ -689,7 +689,8 @@ int launch_sort_unique(uint64_t* surv, uint64_t* tmp, uint64_t cap, const uint64
                            cfg, err, &sorted, "k_onesweep_pairs", s, false, n_dev, nullptr,
                            onesweep_unstable_config(cfg)));
   launch_unique_finalize(sorted, (int64_t)cap, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j,
-                         n_j, metric, rows, row_cap, status, err, n_rows, s, sc);
+                         n_j, metric, rows, row_cap, status, err, n_rows, s, sc,
+                         pair_bits + 8 <= 64 ? (int)pair_bits : 0);
   XTN_CK(cudaGetLastError());
   return XTN_OK;
 }

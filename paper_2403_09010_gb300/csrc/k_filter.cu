@@ -33,14 +33,13 @@ namespace {
 
 constexpr int BF_THREADS = 256;
 constexpr int BF_WARPS = BF_THREADS / 32;
-constexpr int BF_LIST = 1024;                      // records the filter may keep
-constexpr int BF_HMAX = 2 * BF_LIST;               // slots of the exact grouping, at most
-constexpr int BF_HCAP = 2 * BF_HMAX;               // records whose bitmap index is kept
+constexpr int BF_ITEMS = 8;                        // records per thread per chunk
+constexpr int BF_CHUNK = BF_THREADS * BF_ITEMS;    // records per chunk
+
 constexpr int BF_BITS = 16;                        // log2 of the bits of each filter bitmap
 constexpr int BF_WORDS = (1 << BF_BITS) / 32;
 constexpr uint32_t BF_EMPTY = 0xffffffffu;
 constexpr uint32_t BF_NO_PLACE = 0xffffu;
-constexpr int BF_PT = BF_LIST / BF_THREADS;        // kept records per thread, at most
 constexpr uint32_t BF_SMALL = 8;                   // groups up to this size: one lane each
 
 constexpr unsigned long long BF_NO_START = ~0ull;
@@ -61,7 +60,21 @@ __device__ __forceinline__ int64_t bf_first_start(const unsigned long long* __re
   return n;
 }
 
-__global__ void __launch_bounds__(BF_THREADS, 5)
+// Shared memory of a filter block keeping up to LIST records.
+template <int LIST>
+struct BfSmem {
+  uint32_t seen[BF_WORDS];
+  uint32_t again[BF_WORDS];
+  uint64_t list[LIST];
+  uint32_t tk[2 * LIST];
+  uint32_t tc[LIST];
+  uint32_t ids[LIST];
+};
+
+// BF_LIST: records a block may keep (1,024: five blocks per SM; 2,048 for
+// larger segments: three).
+template <int BF_LIST>
+__global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     k_bucket_filter(const uint64_t* __restrict__ A, int64_t n_cap,
                     const uint64_t* __restrict__ n_dev,
                     const unsigned long long* __restrict__ bucket_start, int G, int kf, int fx,
@@ -69,12 +82,16 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
                     unsigned long long* __restrict__ cand_count, int id_bits,
                     uint32_t* __restrict__ seg_list, uint32_t* __restrict__ seg_count,
                     uint32_t* __restrict__ err) {
-  __shared__ __align__(16) uint32_t s_seen[BF_WORDS];
-  __shared__ __align__(16) uint32_t s_again[BF_WORDS];
-  __shared__ uint64_t s_list[BF_LIST];
-  __shared__ __align__(16) uint32_t s_tk[BF_HMAX];      // composite keys, then group sizes
-  __shared__ __align__(16) uint32_t s_tc[BF_HMAX / 2];  // u16 counts, then u16 starts
-  __shared__ uint32_t s_ids[BF_LIST];
+  constexpr int BF_HMAX = 2 * BF_LIST;          // slots of the exact grouping, at most
+  constexpr int BF_PT = BF_LIST / BF_THREADS;   // kept records per thread, at most
+  extern __shared__ __align__(16) unsigned char bf_smem[];
+  BfSmem<BF_LIST>& S = *reinterpret_cast<BfSmem<BF_LIST>*>(bf_smem);
+  uint32_t* s_seen = S.seen;
+  uint32_t* s_again = S.again;
+  uint64_t* s_list = S.list;
+  uint32_t* s_tk = S.tk;  // composite keys, then group sizes
+  uint32_t* s_tc = S.tc;  // u16 counts, then u16 starts
+  uint32_t* s_ids = S.ids;
   __shared__ int64_t s_range[2];
   __shared__ uint32_t s_nlist;
   __shared__ uint32_t s_wsum[BF_WARPS];
@@ -112,44 +129,49 @@ __global__ void __launch_bounds__(BF_THREADS, 5)
   auto bit_of = [&](uint32_t c) {
     return (direct ? c : (c * 0x9E3779B1u) >> (32 - BF_BITS)) & ((1u << BF_BITS) - 1u);
   };
-  // each record's bitmap index, kept for the compaction (the first BF_HCAP
-  // records; the key table is free until the exact grouping)
-  uint16_t* s_h = reinterpret_cast<uint16_t*>(s_tk);
-  // 1. mark keys seen and seen again; thread t takes records t + 256 k,
-  // four loads in flight at a time
-  for (int64_t j0 = threadIdx.x; j0 < m; j0 += 4 * BF_THREADS) {
-    uint64_t k4[4];
+  const int wbase = (int)warp * 32 * BF_ITEMS;
+  // 1. mark keys seen and seen again (chunk by chunk; the last chunk stays in
+  // registers)
+  uint64_t key[BF_ITEMS];
+  for (int64_t c0 = 0; c0 < m; c0 += BF_CHUNK) {
+    const int cm = (int)min((int64_t)BF_CHUNK, m - c0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t j = j0 + u * BF_THREADS;
-      k4[u] = j < m ? A[s + j] : 0ull;
+    for (int i = 0; i < BF_ITEMS; ++i) {
+      const int pos = wbase + i * 32 + (int)lane;
+      key[i] = pos < cm ? A[s + c0 + pos] : 0ull;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t j = j0 + u * BF_THREADS;
-      if (j < m) {
-        const uint32_t h = bit_of(comp(k4[u])), bit = 1u << (h & 31u);
-        if (j < BF_HCAP) s_h[j] = (uint16_t)h;
+    for (int i = 0; i < BF_ITEMS; ++i) {
+      if (wbase + i * 32 + (int)lane < cm) {
+        const uint32_t h = bit_of(comp(key[i])), bit = 1u << (h & 31u);
         if (atomicOr(&s_seen[h >> 5], bit) & bit) atomicOr(&s_again[h >> 5], bit);
       }
     }
   }
   __syncthreads();
-  // 2. keep the records whose key was seen again (the same records per
-  // thread as above, warp by warp for the ballots); a kept record is read
-  // again, from L2
-  for (int64_t j0 = (int64_t)warp * 32; j0 < m; j0 += BF_THREADS) {
-    const int64_t j = j0 + lane;
-    bool keep = false;
-    if (j < m) {
-      const uint32_t h = j < BF_HCAP ? (uint32_t)s_h[j] : bit_of(comp(A[s + j]));
-      keep = (s_again[h >> 5] >> (h & 31u)) & 1u;
+  // 2. keep the records whose key was seen again
+  for (int64_t c0 = 0; c0 < m; c0 += BF_CHUNK) {
+    const int cm = (int)min((int64_t)BF_CHUNK, m - c0);
+    if (m > BF_CHUNK) {
+#pragma unroll
+      for (int i = 0; i < BF_ITEMS; ++i) {
+        const int pos = wbase + i * 32 + (int)lane;
+        key[i] = pos < cm ? A[s + c0 + pos] : 0ull;
+      }
     }
-    const uint32_t bal = __ballot_sync(FULL_MASK, keep);
-    uint32_t at = 0;
-    if (lane == 0 && bal) at = atomicAdd(&s_nlist, (uint32_t)__popc(bal));
-    at = __shfl_sync(FULL_MASK, at, 0) + (uint32_t)__popc(bal & lt_mask);
-    if (keep && at < (uint32_t)BF_LIST) s_list[at] = A[s + j];
+#pragma unroll
+    for (int i = 0; i < BF_ITEMS; ++i) {
+      bool keep = false;
+      if (wbase + i * 32 + (int)lane < cm) {
+        const uint32_t h = bit_of(comp(key[i]));
+        keep = (s_again[h >> 5] >> (h & 31u)) & 1u;
+      }
+      const uint32_t bal = __ballot_sync(FULL_MASK, keep);
+      uint32_t at = 0;
+      if (lane == 0 && bal) at = atomicAdd(&s_nlist, (uint32_t)__popc(bal));
+      at = __shfl_sync(FULL_MASK, at, 0) + (uint32_t)__popc(bal & lt_mask);
+      if (keep && at < (uint32_t)BF_LIST) s_list[at] = key[i];
+    }
   }
   __syncthreads();
   const uint32_t kept = s_nlist;
@@ -344,17 +366,30 @@ void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
   if (n <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_bucket_filter, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_bucket_filter<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(BfSmem<1024>));
+    cudaFuncSetAttribute(k_bucket_filter<1024>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
+    cudaFuncSetAttribute(k_bucket_filter<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(BfSmem<2048>));
+    cudaFuncSetAttribute(k_bucket_filter<2048>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
   });
   // the filter's segments: 2^fx of k_bucket's blocks of buckets each
   while (fx > 0 && (g.kbits + fx > g.G || g.L + g.kbits + fx > 31)) --fx;
   const int kf = g.kbits + fx;
   const uint64_t blocks = ((uint64_t)1 << g.G) >> kf;
   prof_begin(s, "k_bucket_filter", (double)n * 8.0);
-  k_bucket_filter<<<(uint32_t)blocks, BF_THREADS, 0, s>>>(
-      A, n, n_dev, reinterpret_cast<const unsigned long long*>(bucket_start), g.G, kf, fx, lo,
-      g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits, seg_list,
-      seg_count, err);
+  if (fx >= 2)
+    k_bucket_filter<2048><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<2048>), s>>>(
+        A, n, n_dev, reinterpret_cast<const unsigned long long*>(bucket_start), g.G, kf, fx, lo,
+        g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits,
+        seg_list, seg_count, err);
+  else
+    k_bucket_filter<1024><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<1024>), s>>>(
+        A, n, n_dev, reinterpret_cast<const unsigned long long*>(bucket_start), g.G, kf, fx, lo,
+        g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits,
+        seg_list, seg_count, err);
   prof_end(s);
 }
 

@@ -175,8 +175,12 @@ __global__ void __launch_bounds__(256)
       if (!ok) atomicOr(err, DERR_RANGE);
       if (self_mode) ok = ok && i != j;
       if (ok && seq_rep) ok = (seq_rep[i] == seq_rep[j]) == (self_mode != 2);
-      if (ok)
-        ok = cand_distance(metric, d, peq_i, lens_i, keys_j, lens_j, sc, i, j) <= (uint32_t)d;
+      if (ok) {
+        const uint32_t dist = cand_distance(metric, d, peq_i, lens_i, keys_j, lens_j, sc, i, j);
+        ok = dist <= (uint32_t)d;
+        // the distance rides above the pair bits, for the dedup to write it
+        if (ok && hist_hi + 8 <= 64) w |= (uint64_t)dist << hist_hi;
+      }
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
     if (bal) {
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(VER_THREADS)
                       int metric, xtn_triple* __restrict__ out, int64_t cap,
                       uint64_t* __restrict__ status, uint32_t* __restrict__ ctr,
                       uint32_t* __restrict__ err, uint64_t* __restrict__ total_out,
-                      SecondChain sc) {
+                      SecondChain sc, int dist_shift) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_w[VER_THREADS / 32];
   __shared__ uint64_t s_prefix;
@@ -259,15 +263,21 @@ __global__ void __launch_bounds__(VER_THREADS)
     if (p < n) {
       const uint64_t w = pairs[p];
       const uint64_t prev = p > 0 ? pairs[p - 1] : ~w;
-      const uint64_t i = w >> j_bits, j = w & jmask;
+      // with dist_shift the verified distance sits above the pair bits (the
+      // same pair always carries the same distance, so equal pairs are equal
+      // words); else it is computed again
+      const uint64_t pw = dist_shift ? (w & ((1ull << dist_shift) - 1ull)) : w;
+      const uint64_t i = pw >> j_bits, j = pw & jmask;
       ok = w != prev;
       if (i >= n_i || j >= n_j) {
         atomicOr(err, DERR_RANGE);
         ok = false;
       }
       if (ok)
-        dist[it] = cand_distance(metric, 2 * XTN_MAX_LEN, peq_i, lens_i, keys_j, lens_j, sc, i, j);
-      word[it] = w;
+        dist[it] = dist_shift ? (uint32_t)((w >> dist_shift) & 0xffu)
+                              : cand_distance(metric, 2 * XTN_MAX_LEN, peq_i, lens_i, keys_j,
+                                              lens_j, sc, i, j);
+      word[it] = pw;
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
     rank[it] = wtotal + __popc(bal & lt_mask);
@@ -316,7 +326,7 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                             int metric, xtn_triple* out, int64_t cap, uint64_t* status,
                             uint32_t* err, uint64_t* total, cudaStream_t s,
-                            const SecondChain& sc) {
+                            const SecondChain& sc, int dist_shift) {
   if (n <= 0) return;
   const size_t st = verify_status_bytes(n);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st - 16);
@@ -324,7 +334,7 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_
   prof_begin(s, "k_unique_finalize", (double)n * 8.0);
   k_unique_finalize<<<std::min<uint32_t>(div_up_u32(n, VER_TILE), 152 * 8), VER_THREADS, 0, s>>>(
       pairs, n, n_dev, j_bits, peq_i, lens_i, n_i, keys_j, lens_j, n_j, metric, out, cap, status,
-      ctr, err, total, sc);
+      ctr, err, total, sc, dist_shift);
   prof_end(s);
 }
 

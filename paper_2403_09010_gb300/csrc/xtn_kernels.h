@@ -167,7 +167,10 @@ struct SecondChain {
 };
 // metric: 0 = Levenshtein, 1 = Hamming (pairs of equal length only), 2 =
 // paired chains (Levenshtein of the first chains plus that of the second,
-// which `sc` describes).
+// which `sc` describes).  Verify writes a survivor's distance into bits
+// [hist_hi, hist_hi + 8) of its word when they exist (hist_hi + 8 <= 64);
+// the dedup then reads it there (dist_shift = hist_hi) instead of computing
+// it again (dist_shift = 0).
 // self_mode: 0 = query vs reference, 1 = self-search (pairs within a
 // repertoire when seq_rep is given), 2 = self-search keeping only pairs
 // between different repertoires.
@@ -186,7 +189,7 @@ void launch_unique_finalize(const uint64_t* pairs, int64_t n, const uint64_t* n_
                             const Key128* keys_j, const uint8_t* lens_j, uint64_t n_j,
                             int metric, xtn_triple* out, int64_t cap, uint64_t* status,
                             uint32_t* err, uint64_t* total, cudaStream_t s,
-                            const SecondChain& sc = SecondChain());
+                            const SecondChain& sc = SecondChain(), int dist_shift = 0);
 void launch_tcrdist_filter(const xtn_triple* in, int64_t n, const Key128* keys,
                            const uint8_t* lens, int64_t n_seq, int max_score, xtn_triple* out,
                            uint64_t* status, uint32_t* err, uint64_t* total, cudaStream_t s);
