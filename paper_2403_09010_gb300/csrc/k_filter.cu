@@ -33,8 +33,6 @@ namespace {
 
 constexpr int BF_THREADS = 256;
 constexpr int BF_WARPS = BF_THREADS / 32;
-constexpr int BF_ITEMS = 8;                        // records per thread per chunk
-constexpr int BF_CHUNK = BF_THREADS * BF_ITEMS;    // records per chunk
 
 constexpr int BF_BITS = 16;                        // log2 of the bits of each filter bitmap
 constexpr int BF_WORDS = (1 << BF_BITS) / 32;
@@ -73,7 +71,9 @@ struct BfSmem {
 
 // BF_LIST: records a block may keep (1,024: five blocks per SM; 2,048 for
 // larger segments: three).
-template <int BF_LIST>
+// BF_ITEMS: records per thread of one chunk in registers (a segment of up to
+// BF_THREADS * BF_ITEMS records is read once).
+template <int BF_LIST, int BF_ITEMS>
 __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     k_bucket_filter(const uint64_t* __restrict__ A, int64_t n_cap,
                     const uint64_t* __restrict__ n_dev,
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
                     unsigned long long* __restrict__ cand_count, int id_bits,
                     uint32_t* __restrict__ seg_list, uint32_t* __restrict__ seg_count,
                     uint32_t* __restrict__ err) {
+  constexpr int BF_CHUNK = BF_THREADS * BF_ITEMS;  // records per chunk
   constexpr int BF_HMAX = 2 * BF_LIST;          // slots of the exact grouping, at most
   constexpr int BF_PT = BF_LIST / BF_THREADS;   // kept records per thread, at most
   extern __shared__ __align__(16) unsigned char bf_smem[];
@@ -366,30 +367,41 @@ void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
   if (n <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_bucket_filter<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(BfSmem<1024>));
-    cudaFuncSetAttribute(k_bucket_filter<1024>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    const int small = (int)sizeof(BfSmem<1024>), large = (int)sizeof(BfSmem<2048>);
+    cudaFuncSetAttribute(k_bucket_filter<1024, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         small);
+    cudaFuncSetAttribute(k_bucket_filter<1024, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         small);
+    cudaFuncSetAttribute(k_bucket_filter<2048, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         large);
+    cudaFuncSetAttribute(k_bucket_filter<1024, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          100);
-    cudaFuncSetAttribute(k_bucket_filter<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(BfSmem<2048>));
-    cudaFuncSetAttribute(k_bucket_filter<2048>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_bucket_filter<1024, 13>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_bucket_filter<2048, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          100);
   });
   // the filter's segments: 2^fx of k_bucket's blocks of buckets each
   while (fx > 0 && (g.kbits + fx > g.G || g.L + g.kbits + fx > 31)) --fx;
   const int kf = g.kbits + fx;
   const uint64_t blocks = ((uint64_t)1 << g.G) >> kf;
+  const auto bs = reinterpret_cast<const unsigned long long*>(bucket_start);
+  const auto cc = reinterpret_cast<unsigned long long*>(cand_count);
   prof_begin(s, "k_bucket_filter", (double)n * 8.0);
+  // the chunk in registers covers the expected segment: ~1,600 records a
+  // bucket at the sizes G is chosen for
   if (fx >= 2)
-    k_bucket_filter<2048><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<2048>), s>>>(
-        A, n, n_dev, reinterpret_cast<const unsigned long long*>(bucket_start), g.G, kf, fx, lo,
-        g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits,
-        seg_list, seg_count, err);
+    k_bucket_filter<2048, 8><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<2048>), s>>>(
+        A, n, n_dev, bs, g.G, kf, fx, lo, g.L, cand, cand_cap, cc, id_bits, seg_list, seg_count,
+        err);
+  else if (fx == 1)
+    k_bucket_filter<1024, 13><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<1024>), s>>>(
+        A, n, n_dev, bs, g.G, kf, fx, lo, g.L, cand, cand_cap, cc, id_bits, seg_list, seg_count,
+        err);
   else
-    k_bucket_filter<1024><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<1024>), s>>>(
-        A, n, n_dev, reinterpret_cast<const unsigned long long*>(bucket_start), g.G, kf, fx, lo,
-        g.L, cand, cand_cap, reinterpret_cast<unsigned long long*>(cand_count), id_bits,
-        seg_list, seg_count, err);
+    k_bucket_filter<1024, 8><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<1024>), s>>>(
+        A, n, n_dev, bs, g.G, kf, fx, lo, g.L, cand, cand_cap, cc, id_bits, seg_list, seg_count,
+        err);
   prof_end(s);
 }
 
