@@ -379,9 +379,16 @@ int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar
                DevSeqs* out) {
   out->n = n;
   int64_t total = 0;
+  const bool seqs_on_device = is_device_ptr(seqs);
   if (is_device_ptr(offsets)) {
     out->off = offsets;
-    // both ends of the offsets in one wait for the stream
+    if (seqs_on_device) {
+      // nothing to copy: k_encode checks the offsets (first 0, none past the
+      // last, none decreasing) without a wait for the stream here
+      out->seqs = seqs;
+      return XTN_OK;
+    }
+    // host letters: their count is the last offset
     int64_t first = 0;
     XTN_CK(cudaMemcpyAsync(&first, offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     XTN_CK(cudaMemcpyAsync(&total, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -404,7 +411,7 @@ int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar
     out->off = d;
   }
   if (total > 0 && !seqs) return XTN_ERR_INVALID_ARG;
-  if (is_device_ptr(seqs)) {
+  if (seqs_on_device) {
     out->seqs = seqs;
   } else {
     uint8_t* d = ar.get<uint8_t>(total);

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(ENCODE_WARPS * 32)
   const int64_t a = in ? off[i] : 0, b = in ? off[i + 1] : 0;
   bool ok = in && a >= 0 && b >= a && b <= total;
   if (in && !ok) atomicOr(err, DERR_RANGE);
+  if (i == 0 && a != 0) atomicOr(err, DERR_RANGE);  // offsets start at 0
   if (ok && b - a > XTN_MAX_LEN) {
     atomicOr(err, DERR_TOO_LONG);
     ok = false;
