@@ -652,7 +652,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.name, "n": n, "d": WORKLOAD.d,
+        "config": {"workload": (WORKLOAD.name if args.n is None
+                                else f"prefix_n{n}_of_{WORKLOAD.name}"),
+                   "n": n, "d": WORKLOAD.d,
                    "mean_len": float(np.diff(off).mean()),
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"replicas x{world}"},
