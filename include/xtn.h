@@ -353,9 +353,13 @@ XTN_API int xtn_tcrdist_filter_noalloc(const uint8_t* seqs, const int64_t* offse
 /*
  * Tuning knobs (process-wide, take effect for calls that start afterwards).
  *   XTN_TUNE_SORT_RECORDS : tile configuration of the radix sort of variant
- *                           records (0 .. xtn_tune_count(knob)-1)
+ *                           records (0 .. xtn_tune_count(knob)-1): 0-19 rank
+ *                           keys stably with ranks held in registers (the
+ *                           first pass of a sort unstably); 20 and up count
+ *                           and place keys with shared-memory atomics by
+ *                           digit and run of already-sorted bits (default 20)
  *   XTN_TUNE_SORT_PAIRS   : tile configuration of the radix sort of verified
- *                           pair words
+ *                           pair words, the same range (default 21)
  *   XTN_TUNE_RECORD_HISTOGRAM : where the record sort's digit counts are
  *                           taken: 0 = the expand kernel counts the digits
  *                           of every pass, 1 = expand counts the first pass

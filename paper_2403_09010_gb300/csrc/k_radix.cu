@@ -3,10 +3,11 @@
 // the digit offsets of a tile come from a decoupled look-back over the
 // preceding tiles instead of a separate upsweep pass; Adinets & Merrill 2022).
 // This is the grouping step of Appendix A, XTNeighbor step 4 (the paper's
-// `sortKeyValues`) and the pair sort of step 6 (`sort`).  Sorting is stable,
-// so records with equal sorted bits keep their input order.
+// `sortKeyValues`) and the pair sort of step 6 (`sort`).  The output is
+// sorted on [lo, hi); keys equal on those bits come in no particular order
+// (every first pass ranks unstably), which no caller needs.
 //
-// One tile = THREADS x ITEMS keys:
+// k_onesweep, one tile = THREADS x ITEMS keys:
 //   1. load: warp w reads its contiguous 32*ITEMS keys, item-major, so each
 //      load instruction is a 256-byte coalesced run;
 //   2. rank: per item, the lanes holding the same digit are found with one
@@ -19,6 +20,8 @@
 //      with digit t in all earlier tiles;
 //   6. keys leave shared memory in digit order: runs of one digit land on
 //      consecutive addresses.
+// k_onesweep_runs (further down) keeps the same steps but counts and places
+// keys with shared-memory atomics instead of keeping ranks in registers.
 #include <algorithm>
 #include <mutex>
 
@@ -374,6 +377,261 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_onesweep_runs: a pass without per-key rank registers.
+//
+// The input of every pass after the first is sorted on the bits below the
+// current digit, [lo, shift), so a tile of it holds a few runs of equal lower
+// bits, in order.  When a tile spans at most OS_RUNS lower-bit values (its
+// first and last keys tell), its keys are counted, and then placed, with
+// shared-memory atomics on bins (run, digit): each digit leaves the tile with
+// its keys ordered by run, and the tiles leave in order, so the output is
+// sorted on [lo, shift + bits).  Keys equal on all those bits may change
+// places, which no later pass and no caller needs (the first pass has no lower
+// bits: one run).  A tile spanning more lower-bit values (an input with few
+// keys per value) is ranked stably instead: per-warp counts first, then
+// ballots in item order.  Without ranks in registers a block needs about 20
+// fewer registers per thread, so more blocks fit on an SM.
+// The last pass of a grouping sort (bucket_start given; the sort ends at bit
+// 64) records where each bucket (key >> lo) starts: per run of a digit in the
+// fast case, per key at a bucket change otherwise.
+constexpr int OS_RUNS = 4;
+
+template <int THREADS, int ITEMS>
+struct RunsSmem {
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int CNT = (OS_RUNS > WARPS ? OS_RUNS : WARPS) * RADIX;
+  static constexpr size_t keys_bytes = (size_t)TILE * 8;
+  static constexpr size_t bytes = keys_bytes + (size_t)CNT * 4 + RADIX * 4 + RADIX * 8;
+};
+
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int LBW, int DB, int UW>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
+    k_onesweep_runs(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                    const uint64_t* __restrict__ n_dev, int64_t n_cap, int shift, int bits, int lo,
+                    const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
+                    uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
+                    uint32_t* __restrict__ next_hist, int next_bits,
+                    unsigned long long* __restrict__ bucket_start) {
+  using SM = RunsSmem<THREADS, ITEMS>;
+  constexpr int WARPS = SM::WARPS;
+  constexpr int TILE = SM::TILE;
+  static_assert(THREADS >= RADIX, "one thread per digit");
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
+  uint32_t* s_tstart = s_cnt + SM::CNT;
+  int64_t* s_obase = reinterpret_cast<int64_t*>(s_tstart + RADIX);
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wsum[WARPS];
+  __shared__ uint32_t s_next[RADIX];
+  __shared__ uint64_t s_edge[2];  // first and last key of the tile
+  __shared__ int s_shift;         // read back in step 4 (see there)
+
+  if (next_hist)
+    for (int k = threadIdx.x; k < RADIX; k += THREADS) s_next[k] = 0;
+  if (threadIdx.x == 0) s_shift = shift;
+  const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
+  const uint32_t tile = tile_id(ctr, &s_tile);
+  const int64_t tile_base = (int64_t)tile * TILE;
+  if (tile_base >= n) return;
+  const bool full = tile_base + TILE <= n;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t dmask = (1u << bits) - 1u;
+  const int lbits = shift - lo;  // sorted bits below the digit
+  const uint64_t lmask = lbits > 0 ? (~0ull >> (64 - lbits)) : 0ull;
+  for (int k = threadIdx.x; k < SM::CNT; k += THREADS) s_cnt[k] = 0;
+
+  // 1. load: warp w reads its contiguous 32*ITEMS keys item-major
+  uint64_t key[ITEMS];
+  const int64_t wbase = tile_base + (int64_t)warp * 32 * ITEMS;
+  // keys of this warp that exist: items i*32 + lane below wn are valid
+  const int wn = (int)max((int64_t)0, min((int64_t)32 * ITEMS, n - wbase));
+  if (full) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) key[i] = __ldcs(in + wbase + i * 32 + lane);
+    if (threadIdx.x == 0) s_edge[0] = key[0];
+    if (threadIdx.x == THREADS - 1) s_edge[1] = key[ITEMS - 1];
+  } else {
+    const bool holds_last = wbase + wn == n;  // this warp's range ends the tile
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int p = i * 32 + (int)lane;
+      key[i] = p < wn ? __ldcs(in + wbase + p) : 0ull;
+      if (holds_last && p == wn - 1) s_edge[1] = key[i];
+    }
+    if (threadIdx.x == 0) s_edge[0] = key[0];
+  }
+  // DB: the digit's global start is read here, before the look-back, whose
+  // ordered loads would otherwise hold it back until step 5 (one more
+  // register through the pass; configurations short of registers read it in
+  // step 5)
+  const uint64_t dbase = DB && threadIdx.x < RADIX ? digit_base[threadIdx.x] : 0ull;
+  __syncthreads();
+  const uint64_t lf = (s_edge[0] >> lo) & lmask;
+  const bool fast = ((s_edge[1] >> lo) & lmask) - lf < (uint64_t)OS_RUNS;  // block-uniform
+  auto run_of = [&](uint64_t k, int at) {  // at: lo, or step 4's copy of it
+    const uint64_t r = ((k >> at) & lmask) - lf;
+    if (r < (uint64_t)OS_RUNS) return (uint32_t)r;
+    atomicOr(err, DERR_RANGE);  // the input was not sorted on the lower bits
+    return (uint32_t)(OS_RUNS - 1);
+  };
+
+  // 2. counts: bins (run, digit) for the tile, or (warp, digit)
+  if (fast) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      if (full || i * 32 + (int)lane < wn)
+        atomicAdd(&s_cnt[run_of(key[i], lo) * RADIX + ((uint32_t)(key[i] >> shift) & dmask)], 1u);
+  } else {
+    uint32_t* wc = s_cnt + warp * RADIX;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      if (full || i * 32 + (int)lane < wn) atomicAdd(&wc[(uint32_t)(key[i] >> shift) & dmask], 1u);
+  }
+  __syncthreads();
+
+  // 3. bin offsets within each digit, tile counts, aggregates for the look-back
+  uint32_t tcount = 0;
+  if (threadIdx.x < RADIX) {
+    uint32_t acc = 0;
+    if (fast) {
+#pragma unroll
+      for (int r = 0; r < OS_RUNS; ++r) {
+        const uint32_t c = s_cnt[r * RADIX + threadIdx.x];
+        s_cnt[r * RADIX + threadIdx.x] = acc;
+        acc += c;
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_cnt[w * RADIX + threadIdx.x];
+        s_cnt[w * RADIX + threadIdx.x] = acc;
+        acc += c;
+      }
+    }
+    tcount = acc;
+    st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], (tile == 0 ? ST_INC : ST_AGG) | acc);
+  }
+  {  // exclusive scan of the tile counts over digits
+    const uint32_t v = tcount;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL_MASK, inc, o);
+      if (lane >= (uint32_t)o) inc += t;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x < RADIX) {
+      uint32_t off = 0;
+      for (uint32_t w = 0; w < warp; ++w) off += s_wsum[w];
+      const uint32_t ts = off + inc - v;
+      s_tstart[threadIdx.x] = ts;
+      const int slots = fast ? OS_RUNS : WARPS;
+      for (int r = 0; r < slots; ++r) s_cnt[r * RADIX + threadIdx.x] += ts;
+    }
+    __syncthreads();
+  }
+
+  // 4. place the keys in shared memory in digit order.  The digit shift is
+  // read back from shared memory so that the compiler recomputes every bin
+  // here instead of keeping step 2's bins live across the barriers (ITEMS
+  // more registers per thread).
+  const int sh4 = s_shift;
+  const int lo4 = sh4 - lbits;
+  if (fast) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (full || i * 32 + (int)lane < wn) {
+        const uint32_t bin = run_of(key[i], lo4) * RADIX + ((uint32_t)(key[i] >> sh4) & dmask);
+        const uint32_t pos = atomicAdd(&s_cnt[bin], 1u);
+        if (pos < (uint32_t)TILE) s_keys[pos] = key[i];
+        else atomicOr(err, DERR_RANGE);
+      }
+    }
+  } else {
+    uint32_t* wc = s_cnt + warp * RADIX;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool valid = full || i * 32 + (int)lane < wn;
+      const uint32_t dig = (uint32_t)(key[i] >> sh4) & dmask;
+      const uint32_t vmask = full ? FULL_MASK : __ballot_sync(FULL_MASK, valid);
+      const uint32_t peers = digit_peers<0>(dig, vmask);
+      const uint32_t before = peers & lt_mask;
+      const uint32_t base = valid ? wc[dig] : 0u;
+      __syncwarp();
+      if (valid && before == 0) wc[dig] = base + __popc(peers);
+      __syncwarp();
+      if (valid) {
+        const uint32_t pos = base + __popc(before);
+        if (pos < (uint32_t)TILE) s_keys[pos] = key[i];
+        else atomicOr(err, DERR_RANGE);
+      }
+    }
+  }
+
+  // 5. look-back per digit
+  if (threadIdx.x < RADIX) {
+    uint64_t excl = 0;
+    if (tile > 0) {
+      excl = LBW > 1 ? thread_lookback_w<LBW>(status + threadIdx.x, tile, RADIX, err)
+                     : thread_lookback(status + threadIdx.x, tile, RADIX, err);
+      st_status(&status[(uint64_t)tile * RADIX + threadIdx.x], ST_INC | (excl + tcount));
+    }
+    s_obase[threadIdx.x] =
+        (int64_t)((DB ? dbase : digit_base[threadIdx.x]) + excl) - (int64_t)s_tstart[threadIdx.x];
+  }
+  __syncthreads();
+
+  // 6. bucket starts of the fast case: digit t's runs sit at [start, end) of
+  // the tile, end being where step 4 left the bin's counter
+  if (bucket_start && fast && threadIdx.x < RADIX) {
+    uint32_t start = s_tstart[threadIdx.x];
+#pragma unroll
+    for (int r = 0; r < OS_RUNS; ++r) {
+      const uint32_t end = s_cnt[r * RADIX + threadIdx.x];
+      if (end > start) {
+        const int64_t o = s_obase[threadIdx.x] + start;
+        const uint64_t b = ((uint64_t)threadIdx.x << lbits) | (lf + (uint64_t)r);
+        if (o >= 0 && o < n && (b >> (lbits + bits)) == 0)
+          atomicMin(&bucket_start[b], (unsigned long long)o);
+      }
+      start = end;
+    }
+  }
+
+  // 7. write out in digit order (UW: a full tile's ITEMS keys per thread unrolled)
+  const bool mark_each = bucket_start && !fast;
+  const int tile_n = full ? TILE : (int)(n - tile_base);
+  auto write_one = [&](int j) {
+    const uint64_t k = s_keys[j];
+    const uint32_t dig = (uint32_t)(k >> shift) & dmask;
+    if (next_hist) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
+    const int64_t o = s_obase[dig] + j;
+    if (o >= 0 && o < n) out[o] = k;
+    else atomicOr(err, DERR_RANGE);
+    if (mark_each && o >= 0 && o < n) {
+      const uint64_t b = k >> lo;
+      if (j == (int)s_tstart[dig] || b != (s_keys[j - 1] >> lo))
+        atomicMin(&bucket_start[b], (unsigned long long)o);
+    }
+  };
+  if (UW && full) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) write_one((int)threadIdx.x + i * THREADS);
+  } else {
+    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j);
+  }
+  if (next_hist) {  // uniform over the block
+    __syncthreads();
+    if (threadIdx.x < RADIX && s_next[threadIdx.x])
+      atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
+  }
+}
+
 // Tile configurations (id, threads, items per thread, min blocks per SM,
 // ranking: 0 ballots / 1 match.any / 2 atomic-OR bins / 3 ballots with one
 // leader atomic per group / 4 unstable, one atomic per key, ranking chains).
@@ -404,19 +662,41 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   X(19, 512, 12, 2, 3, 1)       \
   X(100, 256, 20, 3, 4, 1)
 
+// k_onesweep_runs configurations (id, threads, items per thread, min blocks
+// per SM, look-back window, digit start read early, write-out unrolled); a
+// sort with one of them uses it for every pass.
+#define XTN_ONESWEEP_RUNS_CONFIGS(X) \
+  X(20, 384, 16, 3, 8, 0, 1)         \
+  X(21, 256, 20, 4, 8, 0, 0)         \
+  X(22, 384, 18, 3, 8, 0, 1)         \
+  X(23, 384, 18, 3, 8, 0, 0)         \
+  X(24, 512, 12, 3, 8, 0, 0)         \
+  X(25, 512, 16, 2, 8, 1, 0)         \
+  X(26, 384, 16, 3, 8, 0, 0)         \
+  X(27, 384, 16, 3, 16, 0, 1)        \
+  X(28, 256, 20, 4, 8, 0, 1)         \
+  X(29, 384, 16, 3, 4, 0, 1)
+
 int onesweep_tile(int cfg) {
   switch (cfg) {
 #define X(id, T, I, B, M, C) \
   case id: return T * I;
     XTN_ONESWEEP_CONFIGS(X)
 #undef X
+#define X(id, T, I, B, W, D, U) \
+  case id: return T * I;
+    XTN_ONESWEEP_RUNS_CONFIGS(X)
+#undef X
   }
   return 0;
 }
 
-int onesweep_configs() { return 20; }  // the tunable (stable) ones, 0-19
+int onesweep_configs() { return 30; }  // the tunable ones, 0-29
 
-int onesweep_unstable_config(int) { return 100; }
+// Configurations 0-19 rank stably in every pass, so their first pass (whose
+// input order does not matter) takes the unstable configuration 100 with the
+// same tile; a k_onesweep_runs configuration serves every pass itself.
+int onesweep_unstable_config(int cfg) { return cfg >= 20 && cfg < 30 ? cfg : 100; }
 
 static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, int64_t n,
                                    const uint64_t* n_dev, int shift, int bits, const uint64_t* digit_base,
@@ -446,6 +726,25 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
   }
     XTN_ONESWEEP_CONFIGS(X)
 #undef X
+#define X(id, T, I, B, W, D, U)                                                                   \
+  case id: {                                                                                  \
+    using SM = RunsSmem<T, I>;                                                                \
+    static std::once_flag once;                                                               \
+    std::call_once(once, [] {                                                                 \
+      cudaFuncSetAttribute(k_onesweep_runs<T, I, B, W, D, U>,                                          \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);      \
+      cudaFuncSetAttribute(k_onesweep_runs<T, I, B, W, D, U>,                                          \
+                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
+    });                                                                                       \
+    const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
+    k_onesweep_runs<T, I, B, W, D, U><<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits,      \
+                                                         bucket_shift, digit_base, status,    \
+                                                         ctr, err, next_hist, next_bits,      \
+                                                         bucket_start);                       \
+    return cudaGetLastError();                                                                \
+  }
+    XTN_ONESWEEP_RUNS_CONFIGS(X)
+#undef X
   }
   return cudaErrorInvalidValue;
 }
@@ -470,6 +769,8 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
                               bool hist_in_passes, const uint64_t* n_dev,
                               uint64_t* bucket_start, int first_cfg) {
   const int passes = (hi - lo + 7) / 8;
+  // buckets are key >> lo: the sorted bits must reach the top of the key
+  if (bucket_start && hi != 64) return cudaErrorInvalidValue;
   // the status words are sized for cfg's tile
   if (first_cfg >= 0 && onesweep_tile(first_cfg) != onesweep_tile(cfg)) first_cfg = -1;
   *sorted = a;

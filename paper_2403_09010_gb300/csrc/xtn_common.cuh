@@ -133,6 +133,46 @@ __device__ __forceinline__ uint64_t thread_lookback(const uint64_t* status, uint
   return excl;
 }
 
+// The same look-back reading W predecessors per step (their loads in flight
+// together), so a walk back over many tiles that have only published their
+// aggregates takes 1/W of the dependent loads.  Statuses past the first
+// unpublished tile of a window are not used; that tile is polled again.
+template <int W>
+__device__ __forceinline__ uint64_t thread_lookback_w(const uint64_t* status, uint32_t tile,
+                                                      uint32_t stride, uint32_t* err) {
+  uint64_t excl = 0;
+  int64_t j = (int64_t)tile - 1;
+  uint32_t spins = 0;
+  const uint32_t limit = spin_limit(err);
+  while (j >= 0) {
+    uint64_t w[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      w[k] = j - k >= 0 ? ld_status(&status[(uint64_t)(j - k) * stride]) : (ST_INC | 0);
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      if (done || used < k) break;  // stopped earlier in this window
+      const uint64_t flag = w[k] >> 62;
+      if (flag == 0) break;  // not published yet
+      excl += w[k] & ST_VAL;
+      used = k + 1;
+      if (flag == 2) done = true;
+    }
+    if (done) break;
+    j -= used;
+    if (used == 0) {
+      if (++spins > limit) {
+        atomicOr(err, DERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  return excl;
+}
+
 // Tile number in block start order: the counter at `ctr` starts at zero.
 __device__ __forceinline__ uint32_t tile_id(uint32_t* ctr, uint32_t* s_slot) {
   if (threadIdx.x == 0) *s_slot = atomicAdd(ctr, 1u);
