@@ -357,7 +357,7 @@ XTN_API int xtn_tcrdist_filter_noalloc(const uint8_t* seqs, const int64_t* offse
  *                           keys stably with ranks held in registers (the
  *                           first pass of a sort unstably); 20 and up count
  *                           and place keys with shared-memory atomics by
- *                           digit and run of already-sorted bits (default 20)
+ *                           digit and run of already-sorted bits (default 22)
  *   XTN_TUNE_SORT_PAIRS   : tile configuration of the radix sort of verified
  *                           pair words, the same range (default 21)
  *   XTN_TUNE_RECORD_HISTOGRAM : where the record sort's digit counts are

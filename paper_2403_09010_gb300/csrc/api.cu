@@ -339,7 +339,7 @@ int choose_hash_bits(uint64_t n_rec, uint32_t id_bits) {
 }
 
 // Tunables (set by the autotuner through xtn_tune_set).
-std::atomic<int> g_cfg_records{20};
+std::atomic<int> g_cfg_records{22};
 std::atomic<int> g_cfg_pairs{21};
 // Where the record sort's digit counts come from: 0 = the expand kernel
 // counts every pass's digit, 1 = expand counts the first and each sort pass

@@ -73,7 +73,9 @@ struct BfSmem {
 // larger segments: three).
 // BF_ITEMS: records per thread of one chunk in registers (a segment of up to
 // BF_THREADS * BF_ITEMS records is read once).
-template <int BF_LIST, int BF_ITEMS>
+// HIW (lo >= 32): the group key lies in the record's high word, so the
+// composite key comes from a 32-bit shift.
+template <int BF_LIST, int BF_ITEMS, bool HIW>
 __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     k_bucket_filter(const uint64_t* __restrict__ A, int64_t n_cap,
                     const uint64_t* __restrict__ n_dev,
@@ -96,6 +98,8 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
   __shared__ int64_t s_range[2];
   __shared__ uint32_t s_nlist;
   __shared__ uint32_t s_wsum[BF_WARPS];
+  __shared__ uint32_t s_wp[BF_WARPS];  // candidate words of each warp
+  __shared__ unsigned long long s_obase;
 
   const int64_t n = n_dev ? min((int64_t)*n_dev, n_cap) : n_cap;
   const int64_t nb = 1ll << G;
@@ -126,7 +130,10 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
   const int64_t m = e - s;
   if (m < 2) return;  // block-uniform
   const uint64_t cbase = (uint64_t)b0 << L;
-  auto comp = [&](uint64_t key) { return (uint32_t)((key >> lo) - cbase); };
+  auto comp = [&](uint64_t key) {
+    return HIW ? ((uint32_t)(key >> 32) >> (lo - 32)) - (uint32_t)cbase
+               : (uint32_t)((key >> lo) - cbase);
+  };
   auto bit_of = [&](uint32_t c) {
     return (direct ? c : (c * 0x9E3779B1u) >> (32 - BF_BITS)) & ((1u << BF_BITS) - 1u);
   };
@@ -160,6 +167,9 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
         key[i] = pos < cm ? A[s + c0 + pos] : 0ull;
       }
     }
+    // the warp's kept records of the chunk, one reservation for all items
+    uint32_t bal[BF_ITEMS];
+    uint32_t wkept = 0;
 #pragma unroll
     for (int i = 0; i < BF_ITEMS; ++i) {
       bool keep = false;
@@ -167,11 +177,19 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
         const uint32_t h = bit_of(comp(key[i]));
         keep = (s_again[h >> 5] >> (h & 31u)) & 1u;
       }
-      const uint32_t bal = __ballot_sync(FULL_MASK, keep);
-      uint32_t at = 0;
-      if (lane == 0 && bal) at = atomicAdd(&s_nlist, (uint32_t)__popc(bal));
-      at = __shfl_sync(FULL_MASK, at, 0) + (uint32_t)__popc(bal & lt_mask);
-      if (keep && at < (uint32_t)BF_LIST) s_list[at] = key[i];
+      bal[i] = __ballot_sync(FULL_MASK, keep);
+      wkept += (uint32_t)__popc(bal[i]);
+    }
+    uint32_t at = 0;
+    if (lane == 0 && wkept) at = atomicAdd(&s_nlist, wkept);
+    at = __shfl_sync(FULL_MASK, at, 0);
+#pragma unroll
+    for (int i = 0; i < BF_ITEMS; ++i) {
+      if ((bal[i] >> lane) & 1u) {
+        const uint32_t a = at + (uint32_t)__popc(bal[i] & lt_mask);
+        if (a < (uint32_t)BF_LIST) s_list[a] = key[i];
+      }
+      at += (uint32_t)__popc(bal[i]);
     }
   }
   __syncthreads();
@@ -262,9 +280,11 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
       np += b * (b - 1) / 2;
     }
   }
-  // output room of this warp's groups, reserved once: the pairs of a lane's
-  // small groups (at most BF_SMALL ids) at the lane's offset, those of large
-  // groups after all small ones
+  // output room: the pairs of a lane's small groups (at most BF_SMALL ids)
+  // at the lane's offset in its warp's room, those of large groups after all
+  // small ones; the block reserves the room of all its warps at once (one
+  // atomic on the shared counter per block, not per warp, which kept the
+  // counter's address busy)
   uint32_t np_small = 0;
   for (uint32_t g = gmask; g; g &= g - 1) {
     const uint32_t c = s_tk[threadIdx.x * PER + (uint32_t)(__ffs(g) - 1)];
@@ -280,13 +300,18 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
   uint32_t wp = np;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wp += __shfl_xor_sync(FULL_MASK, wp, o);
-  unsigned long long obase = 0;
-  if (lane == 0 && wp) {
-    obase = atomicAdd(cand_count, (unsigned long long)wp);
-    if (obase + wp > cand_cap) atomicOr(err, DERR_CAPACITY);
-  }
-  obase = __shfl_sync(FULL_MASK, obase, 0);
+  if (lane == 0) s_wp[warp] = wp;
   __syncthreads();
+  unsigned long long bres = 0;  // thread 0: the block's room (its wait overlaps step 4)
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < BF_WARPS; ++w) tot += s_wp[w];
+    if (tot) {
+      bres = atomicAdd(cand_count, (unsigned long long)tot);
+      if (bres + tot > cand_cap) atomicOr(err, DERR_CAPACITY);
+    }
+  }
   // 4. each group's ids, contiguous
 #pragma unroll
   for (int i = 0; i < BF_PT; ++i) {
@@ -301,7 +326,10 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
       }
     }
   }
+  if (threadIdx.x == 0) s_obase = bres;
   __syncthreads();
+  unsigned long long obase = s_obase;
+  for (uint32_t w = 0; w < warp; ++w) obase += s_wp[w];
   auto word = [&](uint64_t ia, uint64_t ib) {
     return ((ia < ib ? ia : ib) << id_bits) | (ia < ib ? ib : ia);
   };
@@ -360,48 +388,51 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
 
 }  // namespace
 
+template <int LIST, int ITEMS>
+void bucket_filter_launch(uint64_t blocks, bool hiw, const uint64_t* A, int64_t n,
+                          const uint64_t* n_dev, const unsigned long long* bs,
+                          const GroupingShape& g, int kf, int fx, int lo, uint64_t* cand,
+                          uint64_t cand_cap, unsigned long long* cc, int id_bits,
+                          uint32_t* seg_list, uint32_t* seg_count, uint32_t* err,
+                          cudaStream_t s) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (auto f : {k_bucket_filter<LIST, ITEMS, false>, k_bucket_filter<LIST, ITEMS, true>}) {
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(BfSmem<LIST>));
+      cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+  });
+  auto f = hiw ? k_bucket_filter<LIST, ITEMS, true> : k_bucket_filter<LIST, ITEMS, false>;
+  f<<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<LIST>), s>>>(A, n, n_dev, bs, g.G, kf, fx, lo,
+                                                               g.L, cand, cand_cap, cc, id_bits,
+                                                               seg_list, seg_count, err);
+}
+
 void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
                           const uint64_t* bucket_start, const GroupingShape& g, int fx, int lo,
                           uint64_t* cand, uint64_t cand_cap, uint64_t* cand_count, int id_bits,
                           uint32_t* seg_list, uint32_t* seg_count, uint32_t* err, cudaStream_t s) {
   if (n <= 0) return;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    const int small = (int)sizeof(BfSmem<1024>), large = (int)sizeof(BfSmem<2048>);
-    cudaFuncSetAttribute(k_bucket_filter<1024, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         small);
-    cudaFuncSetAttribute(k_bucket_filter<1024, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         small);
-    cudaFuncSetAttribute(k_bucket_filter<2048, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         large);
-    cudaFuncSetAttribute(k_bucket_filter<1024, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
-    cudaFuncSetAttribute(k_bucket_filter<1024, 13>,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_bucket_filter<2048, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
-  });
   // the filter's segments: 2^fx of k_bucket's blocks of buckets each
   while (fx > 0 && (g.kbits + fx > g.G || g.L + g.kbits + fx > 31)) --fx;
   const int kf = g.kbits + fx;
   const uint64_t blocks = ((uint64_t)1 << g.G) >> kf;
   const auto bs = reinterpret_cast<const unsigned long long*>(bucket_start);
   const auto cc = reinterpret_cast<unsigned long long*>(cand_count);
+  const bool hiw = lo >= 32;
   prof_begin(s, "k_bucket_filter", (double)n * 8.0);
   // the chunk in registers covers the expected segment: ~1,600 records a
   // bucket at the sizes G is chosen for
   if (fx >= 2)
-    k_bucket_filter<2048, 8><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<2048>), s>>>(
-        A, n, n_dev, bs, g.G, kf, fx, lo, g.L, cand, cand_cap, cc, id_bits, seg_list, seg_count,
-        err);
+    bucket_filter_launch<2048, 8>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap, cc,
+                                  id_bits, seg_list, seg_count, err, s);
   else if (fx == 1)
-    k_bucket_filter<1024, 13><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<1024>), s>>>(
-        A, n, n_dev, bs, g.G, kf, fx, lo, g.L, cand, cand_cap, cc, id_bits, seg_list, seg_count,
-        err);
+    bucket_filter_launch<1024, 13>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap,
+                                   cc, id_bits, seg_list, seg_count, err, s);
   else
-    k_bucket_filter<1024, 8><<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<1024>), s>>>(
-        A, n, n_dev, bs, g.G, kf, fx, lo, g.L, cand, cand_cap, cc, id_bits, seg_list, seg_count,
-        err);
+    bucket_filter_launch<1024, 8>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap, cc,
+                                  id_bits, seg_list, seg_count, err, s);
   prof_end(s);
 }
 

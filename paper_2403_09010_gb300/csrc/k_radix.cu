@@ -406,7 +406,7 @@ struct RunsSmem {
   static constexpr size_t bytes = keys_bytes + (size_t)CNT * 4 + RADIX * 4 + RADIX * 8;
 };
 
-template <int THREADS, int ITEMS, int MIN_BLOCKS, int LBW, int DB, int UW>
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int LBW, int DB, int UW, bool HIW>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     k_onesweep_runs(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                     const uint64_t* __restrict__ n_dev, int64_t n_cap, int shift, int bits, int lo,
@@ -471,9 +471,19 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   __syncthreads();
   const uint64_t lf = (s_edge[0] >> lo) & lmask;
   const bool fast = ((s_edge[1] >> lo) & lmask) - lf < (uint64_t)OS_RUNS;  // block-uniform
-  auto run_of = [&](uint64_t k, int at) {  // at: lo, or step 4's copy of it
-    const uint64_t r = ((k >> at) & lmask) - lf;
-    if (r < (uint64_t)OS_RUNS) return (uint32_t)r;
+  // HIW (lo >= 32): every sorted bit sits in the key's high word, so digits
+  // and runs come from 32-bit shifts.  A run is the lower bits' difference
+  // from the tile's first key, which modulo 2^32 is exact for the fast case's
+  // differences below OS_RUNS.
+  const uint32_t lmask32 = (uint32_t)lmask, lf32 = (uint32_t)lf;
+  auto digit_of = [&](uint64_t k, int sh) -> uint32_t {
+    if (HIW) return ((uint32_t)(k >> 32) >> (sh - 32)) & dmask;
+    return (uint32_t)(k >> sh) & dmask;
+  };
+  auto run_of = [&](uint64_t k, int at) -> uint32_t {  // at: lo, or step 4's copy of it
+    const uint32_t r = HIW ? (((uint32_t)(k >> 32) >> (at - 32)) & lmask32) - lf32
+                           : (uint32_t)((k >> at) & lmask) - lf32;
+    if (r < (uint32_t)OS_RUNS) return r;
     atomicOr(err, DERR_RANGE);  // the input was not sorted on the lower bits
     return (uint32_t)(OS_RUNS - 1);
   };
@@ -483,12 +493,12 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
       if (full || i * 32 + (int)lane < wn)
-        atomicAdd(&s_cnt[run_of(key[i], lo) * RADIX + ((uint32_t)(key[i] >> shift) & dmask)], 1u);
+        atomicAdd(&s_cnt[run_of(key[i], lo) * RADIX + digit_of(key[i], shift)], 1u);
   } else {
     uint32_t* wc = s_cnt + warp * RADIX;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
-      if (full || i * 32 + (int)lane < wn) atomicAdd(&wc[(uint32_t)(key[i] >> shift) & dmask], 1u);
+      if (full || i * 32 + (int)lane < wn) atomicAdd(&wc[digit_of(key[i], shift)], 1u);
   }
   __syncthreads();
 
@@ -545,7 +555,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       if (full || i * 32 + (int)lane < wn) {
-        const uint32_t bin = run_of(key[i], lo4) * RADIX + ((uint32_t)(key[i] >> sh4) & dmask);
+        const uint32_t bin = run_of(key[i], lo4) * RADIX + digit_of(key[i], sh4);
         const uint32_t pos = atomicAdd(&s_cnt[bin], 1u);
         if (pos < (uint32_t)TILE) s_keys[pos] = key[i];
         else atomicOr(err, DERR_RANGE);
@@ -557,7 +567,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const bool valid = full || i * 32 + (int)lane < wn;
-      const uint32_t dig = (uint32_t)(key[i] >> sh4) & dmask;
+      const uint32_t dig = digit_of(key[i], sh4);
       const uint32_t vmask = full ? FULL_MASK : __ballot_sync(FULL_MASK, valid);
       const uint32_t peers = digit_peers<0>(dig, vmask);
       const uint32_t before = peers & lt_mask;
@@ -608,7 +618,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   const int tile_n = full ? TILE : (int)(n - tile_base);
   auto write_one = [&](int j) {
     const uint64_t k = s_keys[j];
-    const uint32_t dig = (uint32_t)(k >> shift) & dmask;
+    const uint32_t dig = digit_of(k, shift);
     if (next_hist) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
     const int64_t o = s_obase[dig] + j;
     if (o >= 0 && o < n) out[o] = k;
@@ -726,21 +736,22 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
   }
     XTN_ONESWEEP_CONFIGS(X)
 #undef X
-#define X(id, T, I, B, W, D, U)                                                                   \
+#define X(id, T, I, B, W, D, U)                                                               \
   case id: {                                                                                  \
     using SM = RunsSmem<T, I>;                                                                \
     static std::once_flag once;                                                               \
     std::call_once(once, [] {                                                                 \
-      cudaFuncSetAttribute(k_onesweep_runs<T, I, B, W, D, U>,                                          \
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);      \
-      cudaFuncSetAttribute(k_onesweep_runs<T, I, B, W, D, U>,                                          \
-                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);              \
+      for (auto f : {k_onesweep_runs<T, I, B, W, D, U, false>,                                \
+                     k_onesweep_runs<T, I, B, W, D, U, true>}) {                              \
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes); \
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);         \
+      }                                                                                       \
     });                                                                                       \
     const uint32_t tiles = div_up_u32(n, SM::TILE);                                           \
-    k_onesweep_runs<T, I, B, W, D, U><<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits,      \
-                                                         bucket_shift, digit_base, status,    \
-                                                         ctr, err, next_hist, next_bits,      \
-                                                         bucket_start);                       \
+    auto f = bucket_shift >= 32 ? k_onesweep_runs<T, I, B, W, D, U, true>                     \
+                                : k_onesweep_runs<T, I, B, W, D, U, false>;                   \
+    f<<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits, bucket_shift, digit_base,  \
+                                  status, ctr, err, next_hist, next_bits, bucket_start);     \
     return cudaGetLastError();                                                                \
   }
     XTN_ONESWEEP_RUNS_CONFIGS(X)

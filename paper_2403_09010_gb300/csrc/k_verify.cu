@@ -144,6 +144,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_
   return total;
 }
 
+constexpr uint32_t VER_STASH = 256;  // survivor words a warp collects before a flush
+
 __global__ void __launch_bounds__(256)
     k_verify_candidates(const uint64_t* __restrict__ cand, uint64_t n_cap,
                         const uint64_t* __restrict__ n_dev, uint32_t j_bits,
@@ -155,11 +157,27 @@ __global__ void __launch_bounds__(256)
                         unsigned long long* __restrict__ n_surv, uint32_t* __restrict__ hist,
                         int hist_hi, uint32_t* __restrict__ err, SecondChain sc) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  // survivors collect per warp and go out VER_STASH - 31 or more at a time:
+  // one reservation on the shared counter per flush, not per 32 candidates
+  __shared__ uint64_t s_stash[256 / 32][VER_STASH];
   const int passes = (hist_hi + 7) / 8;
   for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x) s_hist[k] = 0;
   __syncthreads();
   const uint64_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
   const uint32_t lane = lane_id();
+  uint64_t* stash = s_stash[threadIdx.x >> 5];
+  uint32_t held = 0;  // words in this warp's stash
+  auto flush = [&]() {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(n_surv, (unsigned long long)held);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    for (uint32_t k = lane; k < held; k += 32) {
+      if (base + k < surv_cap) surv[base + k] = stash[k];
+      else atomicOr(err, DERR_RANGE);
+    }
+    __syncwarp();  // the stash is refilled next
+    held = 0;
+  };
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint64_t jmask = (1ull << j_bits) - 1ull;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -183,26 +201,19 @@ __global__ void __launch_bounds__(256)
       }
     }
     const uint32_t bal = __ballot_sync(FULL_MASK, ok);
-    if (bal) {
-      const uint32_t leader = (uint32_t)(__ffs(bal) - 1);
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(n_surv, (unsigned long long)__popc(bal));
-      base = __shfl_sync(FULL_MASK, base, leader);
-      if (ok) {
-        const uint64_t slot = base + __popc(bal & lt_mask);
-        if (slot < surv_cap) {
-          surv[slot] = w;
-          for (int p = 0; p < passes; ++p) {
-            const int sh = 8 * p;
-            const int bits = min(8, hist_hi - sh);
-            atomicAdd(&s_hist[p * RADIX + (uint32_t)((w >> sh) & ((1u << bits) - 1u))], 1u);
-          }
-        } else {
-          atomicOr(err, DERR_RANGE);
-        }
+    if (ok) {
+      stash[held + __popc(bal & lt_mask)] = w;
+      for (int p = 0; p < passes; ++p) {
+        const int sh = 8 * p;
+        const int bits = min(8, hist_hi - sh);
+        atomicAdd(&s_hist[p * RADIX + (uint32_t)((w >> sh) & ((1u << bits) - 1u))], 1u);
       }
     }
+    held += (uint32_t)__popc(bal);
+    __syncwarp();
+    if (held > VER_STASH - 32) flush();  // warp-uniform
   }
+  if (held) flush();
   __syncthreads();
   for (int k = threadIdx.x; k < passes * RADIX; k += blockDim.x)
     if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
