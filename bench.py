@@ -584,7 +584,10 @@ def main():
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # the timed region: events bracket only the dominant kernel's launches
+    # (two event records per launch would otherwise add ~2% to the step)
     xtn.profile_report()          # clear
+    xtn.profile_only(ROOFLINE_KERNEL)
     xtn.profile_enable(True)
     pairs = 0
     with Clocks(local) as clk:
@@ -596,16 +599,27 @@ def main():
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     xtn.profile_enable(False)
-    prof = xtn.profile_report()
-    # host-side spans (whole calls, scratch allocations, stream waits) apart
-    host = {k: v for k, v in prof.items() if k.startswith("host_")}
-    prof = {k: v for k, v in prof.items() if not k.startswith("host_")}
+    xtn.profile_only(None)
+    prof_main = {k: v for k, v in xtn.profile_report().items() if not k.startswith("host_")}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1000.0
     value = replica_throughput(pairs * args.steps, total_s)
     total_s = _reduce(total_s, "max")
     if world > 1:
         torch.distributed.barrier()
+
+    # the same steps again with every launch bracketed: the per-kernel table
+    xtn.profile_enable(True)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k)
+        step()
+    torch.cuda.synchronize()
+    xtn.profile_enable(False)
+    prof = xtn.profile_report()
+    # host-side spans (whole calls, scratch allocations, stream waits) apart
+    host = {k: v for k, v in prof.items() if k.startswith("host_")}
+    prof = {k: v for k, v in prof.items() if not k.startswith("host_")}
     launches = sum(v[0] for v in prof.values())
 
     # end to end through the C ABI with pinned host buffers
@@ -626,9 +640,9 @@ def main():
     e2e_value = replica_throughput(pairs, e2e_s)
     e2e_s = _reduce(e2e_s, "max")
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel, from the timed region
     peak, peak_kind = _peaks()
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    top = (ROOFLINE_KERNEL, prof_main[ROOFLINE_KERNEL]) if ROOFLINE_KERNEL in prof_main else None
     roofline = None
     if top:
         name, (nl, ms, nbytes) = top

@@ -431,8 +431,13 @@ XTN_API int xtn_set_wait_limit(int64_t polls);
  * _query_hamming (the whole call),
  * host_scratch_alloc (each scratch allocation outside the cache) and
  * host_stream_wait (each wait for the stream to drain).
+ * xtn_profile_only(name) restricts the timing to launches and spans with
+ * that name (NULL or "" = all again), so that a timed loop carries only the
+ * events of the kernel it is after; XTN_ERR_INVALID_ARG for a name of 64
+ * characters or more.
  */
 XTN_API int xtn_profile_enable(int on);
+XTN_API int xtn_profile_only(const char* name);
 XTN_API int xtn_profile_report(char* buf, int64_t buf_len);
 
 #ifdef __cplusplus

@@ -27,9 +27,17 @@ struct ProfRec {
 };
 std::mutex g_prof_mu;
 std::atomic<bool> g_prof_on{false};
+std::atomic<bool> g_prof_filtered{false};  // only launches named g_prof_only
+char g_prof_only[64] = "";                 // guarded by g_prof_mu
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_ev_pool;
 thread_local ProfRec t_pending{nullptr, 0.0, nullptr, nullptr, 0.0};
+
+bool prof_wanted(const char* name) {
+  if (!g_prof_filtered.load(std::memory_order_relaxed)) return true;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  return std::strcmp(name, g_prof_only) == 0;
+}
 
 cudaEvent_t ev_get() {
   {
@@ -47,7 +55,7 @@ cudaEvent_t ev_get() {
 }  // namespace
 
 void prof_begin(cudaStream_t s, const char* name, double bytes) {
-  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  if (!g_prof_on.load(std::memory_order_relaxed) || !prof_wanted(name)) return;
   t_pending.name = name;
   t_pending.bytes = bytes;
   t_pending.a = ev_get();
@@ -69,7 +77,7 @@ namespace {
 class HostSpan {
  public:
   explicit HostSpan(const char* name)
-      : name_(name), on_(g_prof_on.load(std::memory_order_relaxed)) {
+      : name_(name), on_(g_prof_on.load(std::memory_order_relaxed) && prof_wanted(name)) {
     if (on_) t0_ = std::chrono::steady_clock::now();
   }
   ~HostSpan() {
@@ -90,6 +98,7 @@ cudaError_t host_sync(cudaStream_t s) {
   HostSpan span("host_stream_wait");
   return cudaStreamSynchronize(s);
 }
+
 }  // namespace
 
 // --------------------------------------------------------------- device ---
@@ -296,6 +305,80 @@ int map_device_err(uint32_t e) {
   do {                   \
     if ((ar).failed()) return XTN_ERR_OOM; \
   } while (0)
+#define XTN_RC(call)         \
+  do {                       \
+    const int rc_ = (call);  \
+    if (rc_) return rc_;     \
+  } while (0)
+
+// Counts read back in the middle of a call (a few words) go through pinned
+// host memory, one block per thread and device, and one wait: a pageable
+// destination would turn every copy into a staged transfer that waits for
+// the stream by itself.  wait() can queue work that needs none of the values
+// (`overlap`) between the copies and the wait, so the GPU has it to run
+// while the host takes the values and queues what follows.
+class ReadBack {
+ public:
+  explicit ReadBack(cudaStream_t s) : s_(s) {}
+  template <class T>
+  int add(T* host, const T* dev) {
+    static_assert(sizeof(T) <= 8, "one word per value");
+    if (n_ == kSlots) return XTN_ERR_CUDA;
+    Slot& m = slot();
+    if (!m.buf) return XTN_ERR_CUDA;
+    XTN_CK(cudaMemcpyAsync(m.buf + n_, dev, sizeof(T), cudaMemcpyDeviceToHost, s_));
+    dst_[n_] = host;
+    size_[n_] = sizeof(T);
+    ++n_;
+    return XTN_OK;
+  }
+  template <class F>
+  int wait(F&& overlap) {
+    Slot& m = slot();
+    if (!m.buf) return XTN_ERR_CUDA;
+    XTN_CK(cudaEventRecord(m.ev, s_));
+    overlap();
+    XTN_CK(cudaGetLastError());
+    {
+      HostSpan span("host_stream_wait");
+      XTN_CK(cudaEventSynchronize(m.ev));
+    }
+    for (int k = 0; k < n_; ++k) std::memcpy(dst_[k], m.buf + k, size_[k]);
+    n_ = 0;
+    return XTN_OK;
+  }
+  int wait() {
+    return wait([] {});
+  }
+
+ private:
+  static constexpr int kSlots = 8;
+  struct Slot {
+    uint64_t* buf = nullptr;
+    cudaEvent_t ev = nullptr;
+  };
+  static Slot& slot() {
+    thread_local std::map<int, Slot> per_device;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Slot& m = per_device[dev];
+    if (!m.buf) {
+      void* p = nullptr;
+      if (cudaHostAlloc(&p, kSlots * sizeof(uint64_t), cudaHostAllocPortable) != cudaSuccess)
+        return m;
+      if (cudaEventCreateWithFlags(&m.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeHost(p);
+        return m;
+      }
+      m.buf = static_cast<uint64_t*>(p);
+    }
+    return m;
+  }
+  cudaStream_t s_;
+  int n_ = 0;
+  void* dst_[kSlots] = {};
+  size_t size_[kSlots] = {};
+};
 
 // Poll limit of bounded device waits for calls that start from now on (0 =
 // the kernels' default); see xtn_set_wait_limit.
@@ -439,7 +522,7 @@ struct Encoded {
 // allow_large: return the count even when it is 2^32 or more (the caller
 // then searches in passes); otherwise that is TOO_LARGE.
 int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStream_t s,
-                     Encoded* e, bool allow_large = false) {
+                     Encoded* e, bool allow_large = false, uint32_t* peq = nullptr) {
   const int64_t n = in.n;
   e->keys = ar.get<Key128>(n);
   e->lens = ar.get<uint8_t>(n);
@@ -455,9 +538,13 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
     uint64_t n_rec;
     uint32_t err;
   } h{0, 0};
-  XTN_CK(cudaMemcpyAsync(&h.n_rec, e->rec_off + n, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(host_sync(s));
+  ReadBack rb(s);
+  XTN_RC(rb.add(&h.n_rec, e->rec_off + n));
+  XTN_RC(rb.add(&h.err, err));
+  // the match vectors need only the encoded keys: they run during the wait
+  XTN_RC(rb.wait([&] {
+    if (peq) launch_peq(e->keys, e->lens, n, peq, s);
+  }));
   if (h.err) return map_device_err(h.err);
   e->n_rec = h.n_rec;
   if (!allow_large && h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
@@ -467,7 +554,8 @@ int encode_and_count(const DevSeqs& in, int d, Arena& ar, uint32_t* err, cudaStr
 // Paired receptors: both chains encoded, the canonical variant counts of the
 // joined strings (the token never deleted) and their record offsets.
 int encode_and_count_paired(const DevSeqs& a, const DevSeqs& b, int d, Arena& ar, uint32_t* err,
-                            cudaStream_t s, Encoded* e) {
+                            cudaStream_t s, Encoded* e, uint32_t* peq = nullptr,
+                            uint32_t* peq_b = nullptr) {
   const int64_t n = a.n;
   e->keys = ar.get<Key128>(n);
   e->lens = ar.get<uint8_t>(n);
@@ -488,9 +576,13 @@ int encode_and_count_paired(const DevSeqs& a, const DevSeqs& b, int d, Arena& ar
     uint64_t n_rec;
     uint32_t err;
   } h{0, 0};
-  XTN_CK(cudaMemcpyAsync(&h.n_rec, e->rec_off + n, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(host_sync(s));
+  ReadBack rb(s);
+  XTN_RC(rb.add(&h.n_rec, e->rec_off + n));
+  XTN_RC(rb.add(&h.err, err));
+  XTN_RC(rb.wait([&] {
+    if (peq) launch_peq(e->keys, e->lens, n, peq, s);
+    if (peq_b) launch_peq(e->keys_b, e->lens_b, n, peq_b, s);
+  }));
   if (h.err) return map_device_err(h.err);
   e->n_rec = h.n_rec;
   if (h.n_rec >= (1ull << 32)) return XTN_ERR_TOO_LARGE;
@@ -1104,10 +1196,14 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     if (rc) return rc;
   }
 
-  // front: encode (read back the record count), expand, sort, group, offsets
+  // front: encode (read back the record count; the match vectors are
+  // computed meanwhile), expand, sort, group, offsets
+  uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
+  uint32_t* peq_b = paired ? ar.get<uint32_t>((size_t)n * PEQ_STRIDE) : nullptr;
+  XTN_ALLOC_OK(ar);
   Encoded e;
-  rc = paired ? encode_and_count_paired(in, in_b, d, ar, err, s, &e)
-              : encode_and_count(in, d, ar, err, s, &e);
+  rc = paired ? encode_and_count_paired(in, in_b, d, ar, err, s, &e, peq, peq_b)
+              : encode_and_count(in, d, ar, err, s, &e, false, peq);
   if (rc == XTN_ERR_TOO_LARGE && !paired) {  // 2^32 records or more: search in passes
     ar.release();
     return search_stream_impl(seqs, offsets, n, d, rep_offsets, n_rep, metric, between, 0, out,
@@ -1139,9 +1235,11 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   } h{0, 0, 0, 0, 0};
   bool flagged = mode == 1;  // groups to emit through flags and S/E
   if (mode != 1) {
-    XTN_CK(cudaMemcpyAsync(&h.direct, counters + 2, 16, cudaMemcpyDeviceToHost, s));
-    XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-    XTN_CK(host_sync(s));
+    ReadBack rb(s);
+    XTN_RC(rb.add(&h.direct, counters + 2));
+    XTN_RC(rb.add(&h.large, counters + 3));
+    XTN_RC(rb.add(&h.err, err));
+    XTN_RC(rb.wait());
     if (h.err == DERR_CAPACITY) {  // candidate overflow alone: regroup sized exactly
       ar.release();
       return search_self_impl(seqs, offsets, n, d, rep_offsets, n_rep, out, cap, n_out, s, 1,
@@ -1156,9 +1254,11 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
     launch_scan_group_pairs(S, E, (int64_t)g_cap, counters, pair_off, so.gstatus, err, s);
     k_pair_total<<<1, 1, 0, s>>>(pair_off, counters, counters + 1);
     XTN_CK(cudaGetLastError());
-    XTN_CK(cudaMemcpyAsync(&h.groups, counters, 16, cudaMemcpyDeviceToHost, s));
-    XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-    XTN_CK(host_sync(s));
+    ReadBack rb(s);
+    XTN_RC(rb.add(&h.groups, counters));
+    XTN_RC(rb.add(&h.pairs, counters + 1));
+    XTN_RC(rb.add(&h.err, err));
+    XTN_RC(rb.wait());
     if (h.err) return map_device_err(h.err);
   }
   const uint64_t n_pairs = h.direct + h.pairs;
@@ -1184,16 +1284,12 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
   const int cfg_pairs = g_cfg_pairs.load();
   b.status = ar.get<uint64_t>(back_status_bytes(n_pairs, cfg_pairs) / 8 + 1);
   b.counters = ar.get<uint64_t>(2);
-  uint32_t* peq = ar.get<uint32_t>((size_t)n * PEQ_STRIDE);
-  uint32_t* peq_b = paired ? ar.get<uint32_t>((size_t)n * PEQ_STRIDE) : nullptr;
   XTN_ALLOC_OK(ar);
   if (h.pairs)
     launch_emit_pairs(so.rec, e.n_rec, S, pair_off, (int64_t)h.groups, nullptr, h.pairs,
                       so.id_bits, b.P1 + h.direct, nullptr, nullptr, sms, err, s);
-  launch_peq(e.keys, e.lens, n, peq, s);
   SecondChain sc;
   if (paired) {
-    launch_peq(e.keys_b, e.lens_b, n, peq_b, s);
     sc.peq_i = peq_b;
     sc.lens_i = e.lens_b;
     sc.keys_j = e.keys_b;
@@ -1206,9 +1302,10 @@ int search_self_impl(const uint8_t* seqs, const int64_t* offsets, int64_t n, int
                    n, seq_rep, between ? 2 : 1, d, o.dev, o.dev_cap, sms, err, s, cfg_pairs,
                    metric, sc);
   if (rc) return rc;
-  XTN_CK(cudaMemcpyAsync(&h.pairs, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(host_sync(s));
+  ReadBack rb(s);
+  XTN_RC(rb.add(&h.pairs, b.counters + 1));
+  XTN_RC(rb.add(&h.err, err));
+  XTN_RC(rb.wait());
   if (h.err) return map_device_err(h.err);
   return finish_out(o, out, cap, h.pairs, s, n_out);
 }
@@ -1359,9 +1456,12 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
     uint64_t cand;
     uint32_t err;
   } hc{0, 0};
-  XTN_CK(cudaMemcpyAsync(&hc.cand, cand_off + n_qv, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&hc.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(host_sync(s));
+  {
+    ReadBack rb(s);
+    XTN_RC(rb.add(&hc.cand, cand_off + n_qv));
+    XTN_RC(rb.add(&hc.err, err));
+    XTN_RC(rb.wait());
+  }
   if (hc.err) return map_device_err(hc.err);
   const uint64_t n_cand = hc.cand;
   idx->seen_cand += n_cand;
@@ -1396,9 +1496,12 @@ int search_query_impl(const xtn_index* idx, const uint8_t* q_seqs, const int64_t
     uint64_t rows;
     uint32_t err;
   } h{0, 0};
-  XTN_CK(cudaMemcpyAsync(&h.rows, b.counters + 1, 8, cudaMemcpyDeviceToHost, s));
-  XTN_CK(cudaMemcpyAsync(&h.err, err, 4, cudaMemcpyDeviceToHost, s));
-  XTN_CK(host_sync(s));
+  {
+    ReadBack rb(s);
+    XTN_RC(rb.add(&h.rows, b.counters + 1));
+    XTN_RC(rb.add(&h.err, err));
+    XTN_RC(rb.wait());
+  }
   if (h.err) return map_device_err(h.err);
   const uint64_t n_rows = h.rows;
   return finish_out(o, out, cap, n_rows, s, n_out);
@@ -1929,6 +2032,15 @@ int xtn_set_wait_limit(int64_t polls) {
 
 int xtn_profile_enable(int on) {
   xtn::g_prof_on.store(on != 0);
+  return XTN_OK;
+}
+
+int xtn_profile_only(const char* name) {
+  const size_t len = name ? std::strlen(name) : 0;
+  if (len >= sizeof(xtn::g_prof_only)) return XTN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(xtn::g_prof_mu);
+  std::memcpy(xtn::g_prof_only, len ? name : "", len + 1);
+  xtn::g_prof_filtered.store(len > 0);
   return XTN_OK;
 }
 

@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
                     const uint64_t* __restrict__ digit_base, uint64_t* __restrict__ status,
                     uint32_t* __restrict__ ctr, uint32_t* __restrict__ err,
                     uint32_t* __restrict__ next_hist, int next_bits,
-                    unsigned long long* __restrict__ bucket_start) {
+                    unsigned long long* __restrict__ bucket_start,
+                    uint64_t* __restrict__ status_next, uint32_t* __restrict__ ctr_next) {
   using SM = RunsSmem<THREADS, ITEMS>;
   constexpr int WARPS = SM::WARPS;
   constexpr int TILE = SM::TILE;
@@ -640,6 +641,14 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     if (threadIdx.x < RADIX && s_next[threadIdx.x])
       atomicAdd(&next_hist[threadIdx.x], s_next[threadIdx.x]);
   }
+  // clear this tile's status words (and tile counter) for the next pass,
+  // which runs after this kernel with the same tiles: no memset between
+  // passes.  Tiles past the key count leave early; the next pass's tiles
+  // there leave early too and read no status.
+  if (status_next && threadIdx.x < RADIX) {
+    status_next[(uint64_t)tile * RADIX + threadIdx.x] = 0ull;
+    if (tile == 0 && threadIdx.x == 0) *ctr_next = 0u;
+  }
 }
 
 // Tile configurations (id, threads, items per thread, min blocks per SM,
@@ -713,7 +722,7 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
                                    uint64_t* status, uint32_t* ctr, uint32_t* err,
                                    uint32_t* next_hist, int next_bits,
                                    unsigned long long* bucket_start, int bucket_shift,
-                                   cudaStream_t s) {
+                                   uint64_t* status_next, uint32_t* ctr_next, cudaStream_t s) {
   switch (cfg) {
 #define X(id, T, I, B, M, C)                                                                  \
   case id: {                                                                                  \
@@ -751,7 +760,8 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
     auto f = bucket_shift >= 32 ? k_onesweep_runs<T, I, B, W, D, U, true>                     \
                                 : k_onesweep_runs<T, I, B, W, D, U, false>;                   \
     f<<<tiles, T, SM::bytes, s>>>(in, out, n_dev, n, shift, bits, bucket_shift, digit_base,  \
-                                  status, ctr, err, next_hist, next_bits, bucket_start);     \
+                                  status, ctr, err, next_hist, next_bits, bucket_start,      \
+                                  status_next, ctr_next);                                    \
     return cudaGetLastError();                                                                \
   }
     XTN_ONESWEEP_RUNS_CONFIGS(X)
@@ -760,10 +770,14 @@ static cudaError_t onesweep_launch(int cfg, const uint64_t* in, uint64_t* out, i
   return cudaErrorInvalidValue;
 }
 
-size_t radix_status_bytes(int64_t n, int cfg) {
+// One pass's status words and tile counter; a sort holds two, used by
+// alternate passes.
+static size_t status_region_bytes(int64_t n, int cfg) {
   const int64_t tiles = (n + onesweep_tile(cfg) - 1) / onesweep_tile(cfg);
   return (size_t)tiles * RADIX * 8 + 16;
 }
+
+size_t radix_status_bytes(int64_t n, int cfg) { return 2 * status_region_bytes(n, cfg); }
 
 void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t* hist, int sms,
                       cudaStream_t s) {
@@ -789,26 +803,42 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
   // hist_in_passes: `hist` holds pass 0's counts on entry, pass p counts the
   // digits of pass p+1 into hist[(p+1) * RADIX], and each pass's offsets are
   // scanned just before it runs.
-  if (!hist_in_passes) k_digit_scan<<<passes, RADIX, 0, s>>>(hist, digit_base);
-  const size_t st_bytes = radix_status_bytes(n, cfg);
-  uint32_t* ctr = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(status) + st_bytes - 16);
+  if (!hist_in_passes) {
+    prof_begin(s, "k_digit_scan", (double)passes * RADIX * 12.0);
+    k_digit_scan<<<passes, RADIX, 0, s>>>(hist, digit_base);
+    prof_end(s);
+  }
+  // two status regions for alternate passes; k_onesweep_runs clears the next
+  // pass's region as it goes, so only the first is cleared here
+  const size_t region = status_region_bytes(n, cfg);
+  uint64_t* st[2] = {status, reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(status) + region)};
+  auto ctr_of = [&](uint64_t* r) {
+    return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(r) + region - 16);
+  };
+  const bool clears_next = onesweep_unstable_config(cfg) == cfg;  // a k_onesweep_runs config
   uint64_t* src = a;
   uint64_t* dst = b;
   for (int p = 0; p < passes; ++p) {
     const int sh = lo + 8 * p;
     const int bits = std::min(8, hi - sh);
-    if (hist_in_passes)
+    if (hist_in_passes) {
+      prof_begin(s, "k_digit_scan", (double)RADIX * 12.0);
       k_digit_scan<<<1, RADIX, 0, s>>>(hist + p * RADIX, digit_base + p * RADIX);
+      prof_end(s);
+    }
     uint32_t* next = (hist_in_passes && p + 1 < passes) ? hist + (p + 1) * RADIX : nullptr;
     const int next_bits = next ? std::min(8, hi - (sh + 8)) : 0;
-    cudaError_t e = cudaMemsetAsync(status, 0, st_bytes, s);
+    uint64_t* cur = st[p & 1];
+    uint64_t* nxt = clears_next && p + 1 < passes ? st[(p + 1) & 1] : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!clears_next || p == 0) e = cudaMemsetAsync(cur, 0, region, s);
     if (e != cudaSuccess) return e;
     prof_begin(s, tag, (double)n * 16.0);
     unsigned long long* bs =
         p + 1 == passes ? reinterpret_cast<unsigned long long*>(bucket_start) : nullptr;
     e = onesweep_launch(p == 0 && first_cfg >= 0 ? first_cfg : cfg, src, dst, n, n_dev, sh, bits,
-                        digit_base + p * RADIX, status, ctr, err,
-                        next, next_bits, bs, lo, s);
+                        digit_base + p * RADIX, cur, ctr_of(cur), err,
+                        next, next_bits, bs, lo, nxt, nxt ? ctr_of(nxt) : nullptr, s);
     prof_end(s);
     if (e != cudaSuccess) return e;
     std::swap(src, dst);

@@ -66,6 +66,7 @@ SIGNATURES = {
     "xtn_scratch_trim": (_I, []),
     "xtn_set_wait_limit": (_I, [_I64]),
     "xtn_profile_enable": (_I, [_I]),
+    "xtn_profile_only": (_I, [ctypes.c_char_p]),
     "xtn_profile_report": (_I, [ctypes.c_char_p, _I64]),
 }
 

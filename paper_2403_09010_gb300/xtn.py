@@ -371,6 +371,11 @@ def profile_enable(on: bool = True) -> None:
     native.lib().xtn_profile_enable(1 if on else 0)
 
 
+def profile_only(name: str | None = None) -> None:
+    """Time only the launches named `name` (None: all); see xtn_profile_only."""
+    check(native.lib().xtn_profile_only(name.encode() if name else None), "xtn_profile_only")
+
+
 def profile_report() -> dict:
     """{kernel name: (launches, total_ms, algorithmic_bytes)} since the last report."""
     buf = ctypes.create_string_buffer(1 << 16)

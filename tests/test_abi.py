@@ -122,6 +122,16 @@ def test_wait_limit_range(lib):
     assert lib.xtn_set_wait_limit(0) == native.XTN_OK
 
 
+def test_profile_only_names(lib):
+    # a host-side setting: names of 64 characters or more are refused; NULL
+    # and "" time every launch again
+    assert lib.xtn_profile_only(b"k_onesweep_records") == native.XTN_OK
+    assert lib.xtn_profile_only(b"x" * 64) == native.XTN_ERR_INVALID_ARG
+    assert lib.xtn_profile_only(b"x" * 63) == native.XTN_OK
+    assert lib.xtn_profile_only(None) == native.XTN_OK
+    assert lib.xtn_profile_only(b"") == native.XTN_OK
+
+
 def test_paired_argument_checks(lib):
     n_out = ctypes.c_int64(7)
     off = (ctypes.c_int64 * 2)(0, 3)
