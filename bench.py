@@ -484,9 +484,10 @@ def run_streaming(reps: int = 3):
 def run_profile_case(args):
     """Small cases of the query search (a resident index of n reference
     sequences, default 2,000,000, and one request of 20,000 queries, half of
-    them one-deletion mutants of reference entries) and of the TCRdist filter (the d<=2 rows of the
-    first n sequences of the TCRdist workload, default 1,000,000), run warm-up
-    plus `steps` times; for ncu captures of their kernels."""
+    them one-deletion mutants of reference entries), of the TCRdist filter (the d<=2 rows of the
+    first n sequences of the TCRdist workload, default 1,000,000) and of the
+    paired-chain search (n receptors, default 400,000), run warm-up plus
+    `steps` times; for ncu captures of their kernels."""
     import torch
     import paper_2403_09010_gb300 as xtn
     xtn.build()
@@ -506,6 +507,15 @@ def run_profile_case(args):
         out = {"case": "query", "ref_n": int(ro.size - 1), "queries": int(qo.size - 1),
                "rows": int(rows.shape[0]), "search_ms": ms_q}
         idx.free()
+    elif args.case == "paired":
+        a, ao, b, bo = gen.paired(args.n or 400_000, 6)
+        da, dao = torch.from_numpy(a).cuda(), torch.from_numpy(ao).cuda()
+        db, dbo = torch.from_numpy(b).cuda(), torch.from_numpy(bo).cuda()
+        rows = xtn.search_paired(da, dao, db, dbo, 2)
+        ms_p = _events_ms(lambda: xtn.search_paired(da, dao, db, dbo, 2),
+                          args.warmup + args.steps, cur)
+        out = {"case": "paired", "receptors": int(ao.size - 1), "rows": int(rows.shape[0]),
+               "search_ms": ms_p}
     else:
         seqs, off = gen.workload(gen.TCRDIST_1M, args.n)
         ds, do = torch.from_numpy(seqs).cuda(), torch.from_numpy(off).cuda()
@@ -530,9 +540,10 @@ def main():
                          "streaming side measurements")
     ap.add_argument("--n", type=int, default=None,
                     help="use only the first n sequences (small cases for profiling)")
-    ap.add_argument("--case", default="self", choices=["self", "query", "tcrdist"],
-                    help="query / tcrdist: a small case of the query search or of the TCRdist "
-                         "filter, for profiling (prints one JSON line of timings)")
+    ap.add_argument("--case", default="self", choices=["self", "query", "tcrdist", "paired"],
+                    help="query / tcrdist / paired: a small case of the query search, the "
+                         "TCRdist filter or the paired-chain search (default 400,000 "
+                         "receptors), for profiling (prints one JSON line of timings)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
