@@ -111,8 +111,21 @@ constexpr int EXPAND_THREADS = 256;
 
 // One count per radix pass for record `rec` (8-bit digits from bit `lo`; the
 // last digit keeps only `last_mask`).
+// HIW: lo >= 32 and every counted digit lies in the high word (32-bit shifts)
+template <bool HIW = false>
 __device__ __forceinline__ void count_digits(uint32_t* s_hist, uint64_t rec, int lo, int passes,
                                              uint32_t last_mask) {
+  if (HIW) {
+    const uint32_t r = (uint32_t)(rec >> 32) >> (lo - 32);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (p < passes) {
+        const uint32_t m = p == passes - 1 ? last_mask : 0xffu;
+        atomicAdd(&s_hist[p * RADIX + ((r >> (8 * p)) & m)], 1u);
+      }
+    }
+    return;
+  }
   const uint64_t r = rec >> lo;
 #pragma unroll
   for (int p = 0; p < MAX_PASSES; ++p) {
@@ -162,7 +175,7 @@ __device__ __forceinline__ void flush_stage(WarpStage& st, uint64_t* __restrict_
 //   SEL_COUNT  only its fingerprint bin counted (s_hist holds the bins)
 //   SEL_APPEND staged for appending when its bin lies in [sel.lo, sel.hi);
 //              its digits counted
-template <int SEL>
+template <int SEL, bool HIW = false>
 __device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t pos,
                                              uint64_t* __restrict__ out, uint64_t n_rec,
                                              uint32_t* s_hist, int hist_lo, int hist_passes,
@@ -171,7 +184,7 @@ __device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t 
   if constexpr (SEL == SEL_ALL) {
     if (valid) {
       out[pos] = rec;
-      count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+      count_digits<HIW>(s_hist, rec, hist_lo, hist_passes, last_mask);
     }
   } else {
     const uint32_t bin = (uint32_t)(rec >> sel.shift) & sel.mask;
@@ -182,7 +195,7 @@ __device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t 
       const uint32_t bal = __ballot_sync(FULL_MASK, keep);
       if (keep) {
         st.buf[st.n + __popc(bal & ((1u << lane) - 1u))] = rec;  // st.n + 32 <= STAGE_CAP
-        count_digits(s_hist, rec, hist_lo, hist_passes, last_mask);
+        count_digits<HIW>(s_hist, rec, hist_lo, hist_passes, last_mask);
       }
       st.n += __popc(bal);
       if (st.n >= STAGE_FLUSH) flush_stage(st, out, n_rec, sel, lane, err);
@@ -306,13 +319,16 @@ constexpr int PACK_SEQS = 16;
 constexpr int PACK_STRIDE = XTN_MAX_LEN + 3;  // P[0 .. L + 2]
 
 struct PackedSeqs {
-  uint32_t Plo[PACK_SEQS][PACK_STRIDE];
-  uint32_t Phi[PACK_SEQS][PACK_STRIDE];
+  uint64_t P[PACK_SEQS][PACK_STRIDE];
   uint8_t rs[PACK_SEQS][XTN_MAX_LEN + 1];
   uint8_t ds[PACK_SEQS][XTN_MAX_LEN / 2 + 1];
 };
 
-template <int SEL>
+// PK_SALT: sequences carry a repertoire salt (seq_rep given); PK_HIW: the
+// histogram's digits lie in the record's high word (hist_lo >= 32).
+constexpr int PK_SALT = 1, PK_HIW = 2;
+
+template <int SEL, int PK>
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_expand_packed(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens,
                     const uint32_t* __restrict__ eqprev, const uint64_t* __restrict__ rec_off,
@@ -349,23 +365,18 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
       const uint32_t eq = eqprev[my];
       base = rec_off[my];
       const uint64_t cnt = rec_off[my + 1] - base;
-      if (seq_rep) salt = rep_salt(seq_rep[my]);
+      if ((PK & PK_SALT) && seq_rep) salt = rep_salt(seq_rep[my]);
       if (L > XTN_MAX_LEN) L = XTN_MAX_LEN;  // encode rejects longer ones
       uint64_t acc = 0, pw = 1;
-      ps->Plo[lane][0] = 0u;
-      ps->Phi[lane][0] = 0u;
+      ps->P[lane][0] = 0ull;
       for (uint32_t p = 0; p < L; ++p) {
         acc += (uint64_t)(uint32_t)(k.lo & 31u) * pw;
         pw *= HASH_B;
         k.lo = (k.lo >> 5) | (k.hi << 59);
         k.hi >>= 5;
-        ps->Plo[lane][p + 1] = (uint32_t)acc;
-        ps->Phi[lane][p + 1] = (uint32_t)(acc >> 32);
+        ps->P[lane][p + 1] = acc;
       }
-      for (uint32_t p = L + 1; p <= L + 2; ++p) {
-        ps->Plo[lane][p] = (uint32_t)acc;
-        ps->Phi[lane][p] = (uint32_t)(acc >> 32);
-      }
+      for (uint32_t p = L + 1; p <= L + 2; ++p) ps->P[lane][p] = acc;
       const uint32_t all = L ? (0xffffffffu >> (32 - L)) : 0u;
       uint32_t runs = ~eq & all;
       uint32_t dbl = runs & (eq >> 1);
@@ -403,7 +414,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
       const uint32_t Lj = __shfl_sync(FULL_MASK, L, (int)j);
       const uint32_t Rj = __shfl_sync(FULL_MASK, R, (int)j);
       const uint32_t Dj = __shfl_sync(FULL_MASK, nD, (int)j);
-      const uint64_t saltj = __shfl_sync(FULL_MASK, salt, (int)j);
+      const uint64_t saltj = (PK & PK_SALT) ? __shfl_sync(FULL_MASK, salt, (int)j) : 0ull;
       uint64_t rec = 0;
       if (t < T) {
         const uint32_t v = t - sj;
@@ -419,15 +430,13 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
         const uint32_t c = ps->ds[j][dbl ? u - c2 : 0u];
         const uint32_t p1 = single || pair ? a : (dbl ? c : Lj);
         const uint32_t p2 = pair ? b : (dbl ? c + 1 : (single ? Lj : Lj + 1));
-        auto P = [&](uint32_t x) {
-          return ((uint64_t)ps->Phi[j][x] << 32) | ps->Plo[j][x];
-        };
+        auto P = [&](uint32_t x) { return ps->P[j][x]; };
         const uint64_t h = P(p1) + HASH_BINV * ((P(p2) - P(p1 + 1)) +
                                                 HASH_BINV * (P(Lj) - P(p2 + 1)));
-        rec = (mix64(h ^ saltj) & ~idmask) | (uint64_t)(s0 + j);
+        rec = (mix64((PK & PK_SALT) ? h ^ saltj : h) & ~idmask) | (uint64_t)(s0 + j);
       }
-      place_record<SEL>(rec, t < T, base0 + t, out, n_rec, s_hist, hist_lo, hist_passes,
-                        last_mask, sel, lane, st, err);
+      place_record<SEL, (PK & PK_HIW) != 0>(rec, t < T, base0 + t, out, n_rec, s_hist, hist_lo,
+                                            hist_passes, last_mask, sel, lane, st, err);
     }
     __syncwarp();  // the next batch overwrites the tables
   }
@@ -507,9 +516,16 @@ static void expand_launch(const Key128* keys, const uint8_t* lens, const uint32_
   if (d <= 2) {
     const int pblocks = (int)std::min<int64_t>(
         (n + PACK_WARPS * PACK_SEQS - 1) / (PACK_WARPS * PACK_SEQS), (int64_t)sms * 8);
-    k_expand_packed<SEL><<<pblocks > 0 ? pblocks : 1, PACK_WARPS * 32, 0, s>>>(
-        keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec, hist, hist_lo, passes,
-        hist_hi, sel, err);
+    // the plain expansion picks its variant; the bin passes take the general one
+    auto f = k_expand_packed<SEL, PK_SALT>;
+    if (SEL == SEL_ALL) {
+      const bool hiw = hist_lo >= 32 && hist_hi <= 64;
+      f = seq_rep ? (hiw ? k_expand_packed<SEL, PK_SALT | PK_HIW> : k_expand_packed<SEL, PK_SALT>)
+                  : (hiw ? k_expand_packed<SEL, PK_HIW> : k_expand_packed<SEL, 0>);
+    }
+    f<<<pblocks > 0 ? pblocks : 1, PACK_WARPS * 32, 0, s>>>(keys, lens, eqprev, rec_off, n, d,
+                                                              seq_rep, id_bits, out, n_rec, hist,
+                                                              hist_lo, passes, hist_hi, sel, err);
   } else {
     int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     if (blocks < 1) blocks = 1;
