@@ -6,16 +6,17 @@
 // (about 91% of the 1M workload's records are alone), so the exact grouping
 // only needs the few that do.  Each block of k_bucket_filter takes a segment
 // of 2^kf consecutive buckets (contiguous in the sorted records) and
-//   1. marks, in two bitmaps indexed by the composite key (bucket offset in
-//      the segment above the low L key bits; hashed to 16 bits when wider),
-//      the keys seen and the keys seen again;
+//   1. marks, in two bitmaps, the keys seen (indexed by the composite key:
+//      bucket offset in the segment above the low L key bits, hashed when
+//      wider than the bitmap's index) and the keys seen again (a 16-bit
+//      hash of it);
 //   2. keeps the records whose key was seen again -- all members of groups
 //      of two or more, plus the rare lone record whose bit another key also
 //      hit -- in a short list;
 //   3. groups the list exactly in a hash table sized to it (at least twice
 //      the kept records), places each group's ids contiguously, and writes
 //      every pair of a group of two or more as a candidate word (min id <<
-//      id_bits | max id), reserving output space once per warp.
+//      id_bits | max id), reserving output space once per block.
 // Every phase spreads its work over all the block's threads, and the fixed
 // work per block (table clearing and scanning) scales with the kept records,
 // not with the segment.  A segment whose list overflows appends the k_bucket
@@ -58,10 +59,11 @@ __device__ __forceinline__ int64_t bf_first_start(const unsigned long long* __re
   return n;
 }
 
-// Shared memory of a filter block keeping up to LIST records.
-template <int LIST>
+// Shared memory of a filter block keeping up to LIST records, with a
+// 2^SEEN-bit "seen" bitmap (the "seen again" one has 2^BF_BITS bits).
+template <int LIST, int SEEN>
 struct BfSmem {
-  uint32_t seen[BF_WORDS];
+  uint32_t seen[(1 << SEEN) / 32];
   uint32_t again[BF_WORDS];
   uint64_t list[LIST];
   uint32_t tk[2 * LIST];
@@ -69,13 +71,19 @@ struct BfSmem {
   uint32_t ids[LIST];
 };
 
-// BF_LIST: records a block may keep (1,024: five blocks per SM; 2,048 for
-// larger segments: three).
+// BF_LIST: records a block may keep (512 for two-bucket segments, whose
+// direct 17-bit "seen" bitmap keeps about 8% of ~3,200 records; 1,024 for
+// one bucket and 2,048 for larger segments with 16-bit bitmaps).
 // BF_ITEMS: records per thread of one chunk in registers (a segment of up to
 // BF_THREADS * BF_ITEMS records is read once).
 // HIW (lo >= 32): the group key lies in the record's high word, so the
 // composite key comes from a 32-bit shift.
-template <int BF_LIST, int BF_ITEMS, bool HIW>
+// SEEN: log2 of the bits of the "seen" bitmap.  With SEEN = 17 a two-bucket
+// segment's composite keys (17 bits) index it directly, so only keys that
+// really occur twice (or share their 32-bit group key) set "seen again"; its
+// own 16-bit index is hashed, and a rare collision there only keeps a
+// record that the exact grouping then finds alone.
+template <int BF_LIST, int BF_ITEMS, bool HIW, int SEEN>
 __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     k_bucket_filter(const uint64_t* __restrict__ A, int64_t n_cap,
                     const uint64_t* __restrict__ n_dev,
@@ -88,7 +96,8 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
   constexpr int BF_HMAX = 2 * BF_LIST;          // slots of the exact grouping, at most
   constexpr int BF_PT = BF_LIST / BF_THREADS;   // kept records per thread, at most
   extern __shared__ __align__(16) unsigned char bf_smem[];
-  BfSmem<BF_LIST>& S = *reinterpret_cast<BfSmem<BF_LIST>*>(bf_smem);
+  BfSmem<BF_LIST, SEEN>& S = *reinterpret_cast<BfSmem<BF_LIST, SEEN>*>(bf_smem);
+  constexpr int SEEN_WORDS = (1 << SEEN) / 32;
   uint32_t* s_seen = S.seen;
   uint32_t* s_again = S.again;
   uint64_t* s_list = S.list;
@@ -107,7 +116,7 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
   const int64_t b0 = (int64_t)blockIdx.x * K;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const bool direct = L + kf <= BF_BITS;
+  const bool direct = L + kf <= SEEN;
   const uint64_t idmask = (1ull << id_bits) - 1ull;
   // warps 0 and 1 find the segment's first and end record, the rest clear
   if (warp < 2) {
@@ -118,9 +127,9 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     }
     if (lane == 0) s_range[warp] = v;
   } else {
-    for (int k = threadIdx.x - 64; k < 2 * BF_WORDS / 4; k += BF_THREADS - 64) {
-      uint4* z = k < BF_WORDS / 4 ? reinterpret_cast<uint4*>(s_seen) + k
-                                  : reinterpret_cast<uint4*>(s_again) + (k - BF_WORDS / 4);
+    for (int k = threadIdx.x - 64; k < (SEEN_WORDS + BF_WORDS) / 4; k += BF_THREADS - 64) {
+      uint4* z = k < SEEN_WORDS / 4 ? reinterpret_cast<uint4*>(s_seen) + k
+                                    : reinterpret_cast<uint4*>(s_again) + (k - SEEN_WORDS / 4);
       *z = make_uint4(0u, 0u, 0u, 0u);
     }
   }
@@ -134,8 +143,11 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     return HIW ? ((uint32_t)(key >> 32) >> (lo - 32)) - (uint32_t)cbase
                : (uint32_t)((key >> lo) - cbase);
   };
-  auto bit_of = [&](uint32_t c) {
-    return (direct ? c : (c * 0x9E3779B1u) >> (32 - BF_BITS)) & ((1u << BF_BITS) - 1u);
+  auto bit_of = [&](uint32_t c) {  // index in "seen"
+    return (direct ? c : (c * 0x9E3779B1u) >> (32 - SEEN)) & ((1u << SEEN) - 1u);
+  };
+  auto again_of = [&](uint32_t c) {  // index in "seen again"
+    return SEEN == BF_BITS ? bit_of(c) : (c * 0x9E3779B1u) >> (32 - BF_BITS);
   };
   const int wbase = (int)warp * 32 * BF_ITEMS;
   // 1. mark keys seen and seen again (chunk by chunk; the last chunk stays in
@@ -151,8 +163,12 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
 #pragma unroll
     for (int i = 0; i < BF_ITEMS; ++i) {
       if (wbase + i * 32 + (int)lane < cm) {
-        const uint32_t h = bit_of(comp(key[i])), bit = 1u << (h & 31u);
-        if (atomicOr(&s_seen[h >> 5], bit) & bit) atomicOr(&s_again[h >> 5], bit);
+        const uint32_t c = comp(key[i]);
+        const uint32_t h = bit_of(c), bit = 1u << (h & 31u);
+        if (atomicOr(&s_seen[h >> 5], bit) & bit) {
+          const uint32_t a = again_of(c);
+          atomicOr(&s_again[a >> 5], 1u << (a & 31u));
+        }
       }
     }
   }
@@ -174,8 +190,8 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
     for (int i = 0; i < BF_ITEMS; ++i) {
       bool keep = false;
       if (wbase + i * 32 + (int)lane < cm) {
-        const uint32_t h = bit_of(comp(key[i]));
-        keep = (s_again[h >> 5] >> (h & 31u)) & 1u;
+        const uint32_t a = again_of(comp(key[i]));
+        keep = (s_again[a >> 5] >> (a & 31u)) & 1u;
       }
       bal[i] = __ballot_sync(FULL_MASK, keep);
       wkept += (uint32_t)__popc(bal[i]);
@@ -388,7 +404,7 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
 
 }  // namespace
 
-template <int LIST, int ITEMS>
+template <int LIST, int ITEMS, int SEEN>
 void bucket_filter_launch(uint64_t blocks, bool hiw, const uint64_t* A, int64_t n,
                           const uint64_t* n_dev, const unsigned long long* bs,
                           const GroupingShape& g, int kf, int fx, int lo, uint64_t* cand,
@@ -397,14 +413,14 @@ void bucket_filter_launch(uint64_t blocks, bool hiw, const uint64_t* A, int64_t 
                           cudaStream_t s) {
   static std::once_flag once;
   std::call_once(once, [] {
-    for (auto f : {k_bucket_filter<LIST, ITEMS, false>, k_bucket_filter<LIST, ITEMS, true>}) {
+    for (auto f : {k_bucket_filter<LIST, ITEMS, false, SEEN>, k_bucket_filter<LIST, ITEMS, true, SEEN>}) {
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(BfSmem<LIST>));
+                           (int)sizeof(BfSmem<LIST, SEEN>));
       cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
   });
-  auto f = hiw ? k_bucket_filter<LIST, ITEMS, true> : k_bucket_filter<LIST, ITEMS, false>;
-  f<<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<LIST>), s>>>(A, n, n_dev, bs, g.G, kf, fx, lo,
+  auto f = hiw ? k_bucket_filter<LIST, ITEMS, true, SEEN> : k_bucket_filter<LIST, ITEMS, false, SEEN>;
+  f<<<(uint32_t)blocks, BF_THREADS, sizeof(BfSmem<LIST, SEEN>), s>>>(A, n, n_dev, bs, g.G, kf, fx, lo,
                                                                g.L, cand, cand_cap, cc, id_bits,
                                                                seg_list, seg_count, err);
 }
@@ -425,14 +441,14 @@ void launch_bucket_filter(const uint64_t* A, int64_t n, const uint64_t* n_dev,
   // the chunk in registers covers the expected segment: ~1,600 records a
   // bucket at the sizes G is chosen for
   if (fx >= 2)
-    bucket_filter_launch<2048, 8>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap, cc,
-                                  id_bits, seg_list, seg_count, err, s);
+    bucket_filter_launch<2048, 8, BF_BITS>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand,
+                                           cand_cap, cc, id_bits, seg_list, seg_count, err, s);
   else if (fx == 1)
-    bucket_filter_launch<1024, 13>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap,
-                                   cc, id_bits, seg_list, seg_count, err, s);
+    bucket_filter_launch<512, 13, 17>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap,
+                                      cc, id_bits, seg_list, seg_count, err, s);
   else
-    bucket_filter_launch<1024, 8>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand, cand_cap, cc,
-                                  id_bits, seg_list, seg_count, err, s);
+    bucket_filter_launch<1024, 8, BF_BITS>(blocks, hiw, A, n, n_dev, bs, g, kf, fx, lo, cand,
+                                           cand_cap, cc, id_bits, seg_list, seg_count, err, s);
   prof_end(s);
 }
 
