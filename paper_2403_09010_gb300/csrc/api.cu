@@ -646,7 +646,9 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
                        int hist_mode, int mode, const GroupScratch& gs, int sms, uint32_t* err,
                        cudaStream_t s, const uint64_t* n_rec_dev, uint64_t** sorted,
                        const BinSel* sel = nullptr, const Encoded* paired = nullptr) {
-  // the expansion: one chain, or paired receptors (no bin selection)
+  // the expansion: one chain, or paired receptors (no bin selection).  The
+  // single-chain expansion also clears the record sort's status area.
+  const bool zeroed = !paired;
   auto expand = [&](int hist_lo, int hist_hi) {
     if (paired)
       launch_expand_paired(paired->keys, paired->lens, paired->eqprev, paired->keys_b,
@@ -654,7 +656,7 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
                            hist_lo, hist_hi, sms, err, s);
     else
       launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, hist_lo,
-                    hist_hi, sms, err, s, sel);
+                    hist_hi, sms, err, s, sel, status, radix_status_bytes((int64_t)rec_cap, cfg));
   };
   if (mode == 1) {
     const bool in_passes = hist_mode == 1;
@@ -662,7 +664,7 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
     XTN_CK(cudaGetLastError());
     XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, lo, 64, hist, digit_base, status, cfg, err,
                              sorted, "k_onesweep_records", s, in_passes, n_rec_dev, nullptr,
-                             onesweep_unstable_config(cfg)));
+                             onesweep_unstable_config(cfg), zeroed));
     if (gs.flags) {
       XTN_CK(cudaMemsetAsync(gs.gstatus, 0, group_status_bytes((int64_t)rec_cap), s));
       launch_group_flags(*sorted, (int64_t)rec_cap, n_rec_dev, lo, gs.flags, gs.gstatus, s);
@@ -680,7 +682,7 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
   uint64_t* X = A;
   XTN_CK(radix_sort_passes(A, B, (int64_t)rec_cap, glo, 64, hist, digit_base, status, cfg, err,
                            &X, "k_onesweep_records", s, in_passes, n_rec_dev, gs.bucket_start,
-                           onesweep_unstable_config(cfg)));
+                           onesweep_unstable_config(cfg), zeroed));
   uint64_t* Y = X == A ? B : A;
   uint64_t* tile_counts = nullptr;
   if (gs.flags) {

@@ -792,7 +792,7 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
                               bool hist_in_passes, const uint64_t* n_dev,
-                              uint64_t* bucket_start, int first_cfg) {
+                              uint64_t* bucket_start, int first_cfg, bool status_zeroed) {
   const int passes = (hi - lo + 7) / 8;
   // buckets are key >> lo: the sorted bits must reach the top of the key
   if (bucket_start && hi != 64) return cudaErrorInvalidValue;
@@ -828,10 +828,14 @@ cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int h
     }
     uint32_t* next = (hist_in_passes && p + 1 < passes) ? hist + (p + 1) * RADIX : nullptr;
     const int next_bits = next ? std::min(8, hi - (sh + 8)) : 0;
+    // a region is fresh for the first two passes when the caller cleared both;
+    // later passes reuse one, cleared by the pass before (or by a memset)
     uint64_t* cur = st[p & 1];
-    uint64_t* nxt = clears_next && p + 1 < passes ? st[(p + 1) & 1] : nullptr;
+    const bool fresh_next = status_zeroed && p + 1 < 2;
+    uint64_t* nxt = clears_next && p + 1 < passes && !fresh_next ? st[(p + 1) & 1] : nullptr;
     cudaError_t e = cudaSuccess;
-    if (!clears_next || p == 0) e = cudaMemsetAsync(cur, 0, region, s);
+    const bool fresh = status_zeroed && p < 2;
+    if (!fresh && (!clears_next || p == 0)) e = cudaMemsetAsync(cur, 0, region, s);
     if (e != cudaSuccess) return e;
     prof_begin(s, tag, (double)n * 16.0);
     unsigned long long* bs =

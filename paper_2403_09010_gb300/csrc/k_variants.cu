@@ -203,16 +203,27 @@ __device__ __forceinline__ void place_record(uint64_t rec, bool valid, uint64_t 
   }
 }
 
+// Clears n 16-byte words for a later kernel (the record sort's look-back
+// status), grid-stride: the expansion is bound by instruction issue, so these
+// stores cost it almost nothing and spare the sort a memset or the clearing.
+__device__ __forceinline__ void zero_fill(uint4* __restrict__ p, uint64_t n) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x)
+    p[k] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 template <int SEL>
 __global__ void __launch_bounds__(EXPAND_THREADS)
     k_expand(const Key128* __restrict__ keys, const uint8_t* __restrict__ lens,
              const uint32_t* __restrict__ eqprev, const uint64_t* __restrict__ rec_off, int64_t n,
              int d, const uint32_t* __restrict__ seq_rep, uint32_t id_bits,
              uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist, int hist_lo,
-             int hist_passes, int hist_hi, BinSel sel, uint32_t* __restrict__ err) {
+             int hist_passes, int hist_hi, BinSel sel, uint32_t* __restrict__ err,
+             uint4* __restrict__ zero, uint64_t n_zero) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   __shared__ VariantTables s_tab;
   __shared__ WarpVariants s_warp[EXPAND_THREADS / 32];
+  zero_fill(zero, n_zero);
   constexpr int STAGE_WARPS = SEL == SEL_APPEND ? EXPAND_THREADS / 32 : 1;
   __shared__ uint64_t s_stage[STAGE_WARPS][SEL == SEL_APPEND ? STAGE_CAP : 1];
   WarpStage st{s_stage[SEL == SEL_APPEND ? threadIdx.x >> 5 : 0], 0u};
@@ -335,7 +346,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
                     int64_t n, int d, const uint32_t* __restrict__ seq_rep, uint32_t id_bits,
                     uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist,
                     int hist_lo, int hist_passes, int hist_hi, BinSel sel,
-                    uint32_t* __restrict__ err) {
+                    uint32_t* __restrict__ err, uint4* __restrict__ zero, uint64_t n_zero) {
+  zero_fill(zero, n_zero);
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
   __shared__ VariantTables s_tab;
   __shared__ PackedSeqs s_seq[PACK_WARPS];
@@ -512,7 +524,7 @@ static void expand_launch(const Key128* keys, const uint8_t* lens, const uint32_
                           const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
                           uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist,
                           int hist_lo, int passes, int hist_hi, const BinSel& sel, int sms,
-                          uint32_t* err, cudaStream_t s) {
+                          uint32_t* err, cudaStream_t s, uint4* zero, uint64_t n_zero) {
   if (d <= 2) {
     const int pblocks = (int)std::min<int64_t>(
         (n + PACK_WARPS * PACK_SEQS - 1) / (PACK_WARPS * PACK_SEQS), (int64_t)sms * 8);
@@ -525,35 +537,39 @@ static void expand_launch(const Key128* keys, const uint8_t* lens, const uint32_
     }
     f<<<pblocks > 0 ? pblocks : 1, PACK_WARPS * 32, 0, s>>>(keys, lens, eqprev, rec_off, n, d,
                                                               seq_rep, id_bits, out, n_rec, hist,
-                                                              hist_lo, passes, hist_hi, sel, err);
+                                                              hist_lo, passes, hist_hi, sel, err,
+                                                              zero, n_zero);
   } else {
     int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     if (blocks < 1) blocks = 1;
     k_expand<SEL><<<blocks, EXPAND_THREADS, 0, s>>>(keys, lens, eqprev, rec_off, n, d, seq_rep,
                                                     id_bits, out, n_rec, hist, hist_lo, passes,
-                                                    hist_hi, sel, err);
+                                                    hist_hi, sel, err, zero, n_zero);
   }
 }
 
 void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
                    const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
                    uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
-                   int hist_hi, int sms, uint32_t* err, cudaStream_t s, const BinSel* sel) {
+                   int hist_hi, int sms, uint32_t* err, cudaStream_t s, const BinSel* sel,
+                   void* zero, size_t zero_bytes) {
+  uint4* z = static_cast<uint4*>(zero);
+  const uint64_t nz = z ? zero_bytes / 16 : 0;
   if (n <= 0) return;
   const int passes = (hist_hi - hist_lo + 7) / 8;
   const BinSel none{};
   if (!sel) {
     prof_begin(s, "k_expand", (double)n_rec * 8.0 + (double)n * 29.0);
     expand_launch<SEL_ALL>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec, hist,
-                           hist_lo, passes, hist_hi, none, sms, err, s);
+                           hist_lo, passes, hist_hi, none, sms, err, s, z, nz);
   } else if (sel->append) {
     prof_begin(s, "k_expand_bins", (double)n_rec * 8.0 + (double)n * 29.0);
     expand_launch<SEL_APPEND>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec,
-                              hist, hist_lo, passes, hist_hi, *sel, sms, err, s);
+                              hist, hist_lo, passes, hist_hi, *sel, sms, err, s, z, nz);
   } else {
     prof_begin(s, "k_expand_count", (double)n * 29.0);
     expand_launch<SEL_COUNT>(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, out, n_rec,
-                             hist, hist_lo, passes, hist_hi, *sel, sms, err, s);
+                             hist, hist_lo, passes, hist_hi, *sel, sms, err, s, z, nz);
   }
   prof_end(s);
 }

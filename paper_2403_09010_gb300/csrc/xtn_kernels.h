@@ -40,11 +40,13 @@ struct BinSel {
 constexpr int MAX_BIN_BITS = 11;
 
 // sel null: every record of sequence i goes to out[rec_off[i] ...].
+// zero: when not null, zero_bytes (a multiple of 16, 16-byte aligned) are
+// cleared there as well (the record sort's look-back status).
 void launch_expand(const Key128* keys, const uint8_t* lens, const uint32_t* eqprev,
                    const uint64_t* rec_off, int64_t n, int d, const uint32_t* seq_rep,
                    uint32_t id_bits, uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo,
                    int hist_hi, int sms, uint32_t* err, cudaStream_t s,
-                   const BinSel* sel = nullptr);
+                   const BinSel* sel = nullptr, void* zero = nullptr, size_t zero_bytes = 0);
 void launch_peq(const Key128* keys, const uint8_t* lens, int64_t n, uint32_t* peq,
                 cudaStream_t s);
 void launch_seq_rep(const int64_t* rep_off, int64_t n_rep, uint32_t* seq_rep, int64_t n,
@@ -68,11 +70,14 @@ void launch_histogram(const uint64_t* keys, int64_t n, int lo, int hi, uint32_t*
 // first_cfg: configuration of the first pass (>= 0), e.g. the unstable one;
 // LSD order needs only the later passes to be stable.  Ignored when its tile
 // differs from cfg's.
+// status_zeroed: the whole status area (radix_status_bytes) is zero on entry,
+// so the first two passes need no clearing.
 cudaError_t radix_sort_passes(uint64_t* a, uint64_t* b, int64_t n, int lo, int hi, uint32_t* hist,
                               uint64_t* digit_base, uint64_t* status, int cfg, uint32_t* err,
                               uint64_t** sorted, const char* tag, cudaStream_t s,
                               bool hist_in_passes = false, const uint64_t* n_dev = nullptr,
-                              uint64_t* bucket_start = nullptr, int first_cfg = -1);
+                              uint64_t* bucket_start = nullptr, int first_cfg = -1,
+                              bool status_zeroed = false);
 // Unstable configuration with the same tile as cfg, for a sort's first pass.
 int onesweep_unstable_config(int cfg);
 
