@@ -59,7 +59,10 @@ __device__ __forceinline__ uint32_t edit_distance(const uint32_t* __restrict__ p
   const uint32_t hb = 1u << (m - 1);
 #pragma unroll
   for (int j = 0; j < XTN_MAX_LEN; ++j) {
-    if ((uint32_t)j < n) {
+    // a lane leaves after its own text, so a warp runs the steps of its
+    // longest text, not XTN_MAX_LEN
+    if ((uint32_t)j >= n) break;
+    {
       const uint32_t eq = eqv[j];
       const uint32_t xv = eq | mv;
       const uint32_t xh = (((eq & pv) + pv) ^ pv) | eq;
