@@ -22,9 +22,12 @@
  *   packs them into 16 bytes and so admits up to 25.
  * - Every pointer argument except `n_out` and the index handle may be a host
  *   pointer or a device pointer of the current CUDA device; the library
- *   inspects it (cudaPointerGetAttributes) and copies host data to and from
- *   the device itself.  The caller owns all buffers it passes.  `n_out` is
- *   always a host pointer.
+ *   inspects it (cudaPointerGetAttributes) and copies pageable host data to
+ *   and from the device itself.  The xtn_search_* calls read pinned host
+ *   sequences and offsets (cudaHostAlloc / cudaHostRegister) in place from
+ *   their first kernel and write rows into a pinned host buffer in place,
+ *   without a staging copy.  The caller owns all buffers it passes.
+ *   `n_out` is always a host pointer.
  * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Kernels
  *   and copies are issued on it; every call returns only after the stream has
  *   finished the call's work, because the result count is read back.

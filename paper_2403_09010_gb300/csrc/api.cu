@@ -141,6 +141,25 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Pinned host memory that this device's kernels can read and write in place
+// (over the chip-to-chip link of a Grace-Blackwell node): its device address,
+// else null (pageable memory is copied instead).
+void* mapped_host_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost) return nullptr;
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, const_cast<void*>(p), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return d;
+}
+
 // Cached scratch.  Each call carves its buffers out of one workspace, a
 // device block taken from a per-device cache and given back when the call
 // returns, so that a call in steady state allocates nothing: the stream-
@@ -488,14 +507,22 @@ int stage_seqs(const uint8_t* seqs, const int64_t* offsets, int64_t n, Arena& ar
       const int rc = check_host_offsets(offsets, n);
       return rc ? rc : XTN_ERR_INVALID_ARG;
     }
-    int64_t* d = ar.get<int64_t>(n + 1);
-    XTN_ALLOC_OK(ar);
-    XTN_CK(cudaMemcpyAsync(d, offsets, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    out->off = d;
+    // pinned host offsets and letters are read in place by k_encode, the
+    // only kernel that reads them; pageable ones are copied first
+    if (void* m = mapped_host_ptr(offsets)) {
+      out->off = static_cast<const int64_t*>(m);
+    } else {
+      int64_t* d = ar.get<int64_t>(n + 1);
+      XTN_ALLOC_OK(ar);
+      XTN_CK(cudaMemcpyAsync(d, offsets, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      out->off = d;
+    }
   }
   if (total > 0 && !seqs) return XTN_ERR_INVALID_ARG;
   if (seqs_on_device) {
     out->seqs = seqs;
+  } else if (void* m = total > 0 ? mapped_host_ptr(seqs) : nullptr) {
+    out->seqs = static_cast<const uint8_t*>(m);
   } else {
     uint8_t* d = ar.get<uint8_t>(total);
     XTN_ALLOC_OK(ar);
@@ -829,6 +856,9 @@ int prepare_out(xtn_triple* out, int64_t cap, uint64_t max_rows, Arena& ar, OutR
   }
   if (is_device_ptr(out)) {
     o->dev = out;
+    o->dev_cap = cap;
+  } else if (void* m = mapped_host_ptr(out)) {  // pinned host rows: written in place
+    o->dev = static_cast<xtn_triple*>(m);
     o->dev_cap = cap;
   } else {
     o->host = true;

@@ -43,6 +43,42 @@ def _rand_strings(rng, n, alphabet, lmin, lmax):
 
 
 # ------------------------------------------------------------ self search ---
+def test_pinned_host_buffers_read_and_written_in_place(xtn):
+    """Pinned host letters, offsets and rows (read and written by the kernels
+    in place) give the oracle's rows, as pageable and device buffers do; a
+    short pinned output gets the first rows and the full count."""
+    import ctypes
+    from paper_2403_09010_gb300 import native
+    seqs, off = gen.workload(gen.SELF_1M, 30_000)
+    n = off.size - 1
+    want = oracle.symdel_self(seqs, off, 2)
+    hs = torch.from_numpy(seqs).pin_memory()
+    ho = torch.from_numpy(off).pin_memory()
+    lib = native.lib()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    for cap in (len(want) + 16, 5):
+        out = torch.full((cap, 3), -1, dtype=torch.int32).pin_memory()
+        n_out = ctypes.c_int64(0)
+        rc = lib.xtn_search_self(ptr(hs), ptr(ho), n, 2, None, 0, ptr(out), cap,
+                                 ctypes.byref(n_out), None)
+        assert n_out.value == len(want)
+        w = min(cap, len(want))
+        assert rc == (native.XTN_OK if cap >= len(want) else native.XTN_ERR_BUFFER_TOO_SMALL)
+        assert np.array_equal(out[:w].numpy().astype(np.uint32), want[:w])
+    assert np.array_equal(_rows(xtn.search_self(seqs, off, 2)), want)          # pageable
+    ds, do = _dev(seqs, off)
+    assert np.array_equal(_rows(xtn.search_self(ds, do, 2)), want)             # device
+    # queries from pinned memory against a resident index
+    idx = xtn.index_build(seqs[: off[20_000]], off[: 20_001], 2)
+    q_off = off[20_000:22_001] - off[20_000]
+    q = seqs[off[20_000]:off[22_000]]
+    qw = oracle.bruteforce_query(seqs[: off[20_000]], off[: 20_001], q, q_off, 2, threads=0)
+    got = _rows(xtn.search_query(idx, torch.from_numpy(q).pin_memory(),
+                                 torch.from_numpy(q_off).pin_memory()))
+    idx.free()
+    assert np.array_equal(got, qw)
+
+
 def test_selfsearch_n1e4_d1_full(xtn):
     seqs, off = gen.workload(gen.SELF_SMALL)
     want = oracle.symdel_self(seqs, off, 1)
