@@ -673,14 +673,15 @@ int expand_sort_launch(const Key128* keys, const uint8_t* lens, const uint32_t* 
                        int hist_mode, int mode, const GroupScratch& gs, int sms, uint32_t* err,
                        cudaStream_t s, const uint64_t* n_rec_dev, uint64_t** sorted,
                        const BinSel* sel = nullptr, const Encoded* paired = nullptr) {
-  // the expansion: one chain, or paired receptors (no bin selection).  The
-  // single-chain expansion also clears the record sort's status area.
-  const bool zeroed = !paired;
+  // the expansion: one chain, or paired receptors (no bin selection); it
+  // also clears the record sort's status area
+  const bool zeroed = true;
   auto expand = [&](int hist_lo, int hist_hi) {
     if (paired)
       launch_expand_paired(paired->keys, paired->lens, paired->eqprev, paired->keys_b,
                            paired->lens_b, paired->eq_b, rec_off, n, d, id_bits, A, rec_cap, hist,
-                           hist_lo, hist_hi, sms, err, s);
+                           hist_lo, hist_hi, sms, err, s, status,
+                           radix_status_bytes((int64_t)rec_cap, cfg));
     else
       launch_expand(keys, lens, eqprev, rec_off, n, d, seq_rep, id_bits, A, rec_cap, hist, hist_lo,
                     hist_hi, sms, err, s, sel, status, radix_status_bytes((int64_t)rec_cap, cfg));

@@ -59,20 +59,26 @@ __global__ void k_paired_counts(const uint8_t* __restrict__ lens_a,
 }
 
 struct PairedWarp {
-  uint32_t Plo[PAIRED_MAX + 3];  // P[0 .. Lt + 2]
-  uint32_t Phi[PAIRED_MAX + 3];
+  uint64_t P[PAIRED_MAX + 3];    // P[0 .. Lt + 2]
   uint8_t rs[PAIRED_MAX + 1];    // run starts (positions in the joined string)
   uint8_t ds[PAIRED_MAX + 1];    // starts of runs of length >= 2
 };
 
+// HIW: the histogram's digits lie in the record's high word (hist_lo >= 32).
+// zero / n_zero: 16-byte words cleared for the record sort's status.
+template <bool HIW>
 __global__ void __launch_bounds__(PAIRED_WARPS * 32)
     k_expand_paired(const Key128* __restrict__ keys_a, const uint8_t* __restrict__ lens_a,
                     const uint32_t* __restrict__ eq_a, const Key128* __restrict__ keys_b,
                     const uint8_t* __restrict__ lens_b, const uint32_t* __restrict__ eq_b,
                     const uint64_t* __restrict__ rec_off, int64_t n, int d, uint32_t id_bits,
                     uint64_t* __restrict__ out, uint64_t n_rec, uint32_t* __restrict__ hist,
-                    int hist_lo, int hist_passes, int hist_hi, uint32_t* __restrict__ err) {
+                    int hist_lo, int hist_passes, int hist_hi, uint32_t* __restrict__ err,
+                    uint4* __restrict__ zero, uint64_t n_zero) {
   __shared__ uint32_t s_hist[MAX_PASSES * RADIX];
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_zero;
+       k += (uint64_t)gridDim.x * blockDim.x)
+    zero[k] = make_uint4(0u, 0u, 0u, 0u);
   __shared__ uint64_t s_pow[64];
   __shared__ PairedWarp s_w[PAIRED_WARPS];
   for (int k = threadIdx.x; k < hist_passes * RADIX; k += blockDim.x) s_hist[k] = 0;
@@ -115,14 +121,9 @@ __global__ void __launch_bounds__(PAIRED_WARPS * 32)
                                  : __shfl_sync(FULL_MASK, i1, (int)Lt - 33);
     // P[q + 1] for q < Lt, P[x] = P[Lt] up to Lt + 2
     for (uint32_t q = lane; q < Lt + 2; q += 32) {
-      const uint64_t v = q < Lt ? (q < 32 ? i0 : i1) : PL;
-      w->Plo[q + 1] = (uint32_t)v;
-      w->Phi[q + 1] = (uint32_t)(v >> 32);
+      w->P[q + 1] = q < Lt ? (q < 32 ? i0 : i1) : PL;
     }
-    if (lane == 0) {
-      w->Plo[0] = 0u;
-      w->Phi[0] = 0u;
-    }
+    if (lane == 0) w->P[0] = 0ull;
     // run starts of both chains as joined positions (alpha at q, beta at
     // La + 1 + q); the token is never a deletion
     const uint32_t ra = runs_of(La, ea), rb = runs_of(Lb, eb);
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(PAIRED_WARPS * 32)
       total = 0;
     }
     const uint32_t c2 = R * (R - 1) / 2;
-    auto P = [&](uint32_t x) { return ((uint64_t)w->Phi[x] << 32) | w->Plo[x]; };
+    auto P = [&](uint32_t x) { return w->P[x]; };
     for (uint32_t v = lane; v < total; v += 32) {
       // canonical variant v: none, one run start, two run starts (colex
       // rank u = b(b-1)/2 + a, a < b), or the first two of a long run
@@ -165,12 +166,23 @@ __global__ void __launch_bounds__(PAIRED_WARPS * 32)
       const uint64_t h = P(p1) + HASH_BINV * ((P(p2) - P(p1 + 1)) + HASH_BINV * (P(Lt) - P(p2 + 1)));
       const uint64_t rec = (mix64(h) & ~idmask) | (uint64_t)r;
       out[base + v] = rec;
-      const uint64_t rr = rec >> hist_lo;
+      if (HIW) {
+        const uint32_t rr = (uint32_t)(rec >> 32) >> (hist_lo - 32);
 #pragma unroll
-      for (int p = 0; p < MAX_PASSES; ++p) {
-        if (p < hist_passes) {
-          const uint32_t m = p == hist_passes - 1 ? last_mask : 0xffu;
-          atomicAdd(&s_hist[p * RADIX + ((uint32_t)(rr >> (8 * p)) & m)], 1u);
+        for (int p = 0; p < 4; ++p) {
+          if (p < hist_passes) {
+            const uint32_t m = p == hist_passes - 1 ? last_mask : 0xffu;
+            atomicAdd(&s_hist[p * RADIX + ((rr >> (8 * p)) & m)], 1u);
+          }
+        }
+      } else {
+        const uint64_t rr = rec >> hist_lo;
+#pragma unroll
+        for (int p = 0; p < MAX_PASSES; ++p) {
+          if (p < hist_passes) {
+            const uint32_t m = p == hist_passes - 1 ? last_mask : 0xffu;
+            atomicAdd(&s_hist[p * RADIX + ((uint32_t)(rr >> (8 * p)) & m)], 1u);
+          }
         }
       }
     }
@@ -195,15 +207,17 @@ void launch_expand_paired(const Key128* keys_a, const uint8_t* lens_a, const uin
                           const Key128* keys_b, const uint8_t* lens_b, const uint32_t* eq_b,
                           const uint64_t* rec_off, int64_t n, int d, uint32_t id_bits,
                           uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo, int hist_hi,
-                          int sms, uint32_t* err, cudaStream_t s) {
+                          int sms, uint32_t* err, cudaStream_t s, void* zero,
+                          size_t zero_bytes) {
   if (n <= 0) return;
   const int passes = (hist_hi - hist_lo + 7) / 8;
   const int blocks = (int)std::min<int64_t>((n + PAIRED_WARPS - 1) / PAIRED_WARPS,
                                             (int64_t)sms * 8);
   prof_begin(s, "k_expand_paired", (double)n_rec * 8.0 + (double)n * 58.0);
-  k_expand_paired<<<blocks > 0 ? blocks : 1, PAIRED_WARPS * 32, 0, s>>>(
+  auto f = hist_lo >= 32 && hist_hi <= 64 ? k_expand_paired<true> : k_expand_paired<false>;
+  f<<<blocks > 0 ? blocks : 1, PAIRED_WARPS * 32, 0, s>>>(
       keys_a, lens_a, eq_a, keys_b, lens_b, eq_b, rec_off, n, d, id_bits, out, n_rec, hist,
-      hist_lo, passes, hist_hi, err);
+      hist_lo, passes, hist_hi, err, static_cast<uint4*>(zero), zero ? zero_bytes / 16 : 0);
   prof_end(s);
 }
 

@@ -211,7 +211,8 @@ void launch_expand_paired(const Key128* keys_a, const uint8_t* lens_a, const uin
                           const Key128* keys_b, const uint8_t* lens_b, const uint32_t* eq_b,
                           const uint64_t* rec_off, int64_t n, int d, uint32_t id_bits,
                           uint64_t* out, uint64_t n_rec, uint32_t* hist, int hist_lo, int hist_hi,
-                          int sms, uint32_t* err, cudaStream_t s);
+                          int sms, uint32_t* err, cudaStream_t s, void* zero = nullptr,
+                          size_t zero_bytes = 0);
 
 // k_query.cu ---------------------------------------------------------------
 // Directory of the sorted index (entry t = first record whose top dir_bits
