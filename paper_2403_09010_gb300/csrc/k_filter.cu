@@ -132,6 +132,12 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
                                     : reinterpret_cast<uint4*>(s_again) + (k - SEEN_WORDS / 4);
       *z = make_uint4(0u, 0u, 0u, 0u);
     }
+    // the exact grouping's tables, whole (they are first used after several
+    // barriers; clearing them here saves that phase its own barrier)
+    for (int k = threadIdx.x - 64; k < 2 * BF_LIST / 4; k += BF_THREADS - 64)
+      reinterpret_cast<uint4*>(s_tk)[k] = make_uint4(BF_EMPTY, BF_EMPTY, BF_EMPTY, BF_EMPTY);
+    for (int k = threadIdx.x - 64; k < BF_LIST / 4; k += BF_THREADS - 64)
+      reinterpret_cast<uint4*>(s_tc)[k] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (threadIdx.x == 0) s_nlist = 0;
   __syncthreads();
@@ -223,13 +229,8 @@ __global__ void __launch_bounds__(BF_THREADS, BF_LIST <= 1024 ? 5 : 3)
   // two per thread; thread t owns slots [t PER, t PER + PER)
   int hb = 9;
   while ((1u << hb) < 2 * kept) ++hb;
-  const uint32_t H = 1u << hb;  // 512 .. BF_HMAX
+  const uint32_t H = 1u << hb;  // 512 .. BF_HMAX; tables cleared in phase 0
   const uint32_t PER = H / BF_THREADS;
-  for (uint32_t k = threadIdx.x; k < H / 4; k += BF_THREADS)
-    reinterpret_cast<uint4*>(s_tk)[k] = make_uint4(BF_EMPTY, BF_EMPTY, BF_EMPTY, BF_EMPTY);
-  for (uint32_t k = threadIdx.x; k < H / 8; k += BF_THREADS)
-    reinterpret_cast<uint4*>(s_tc)[k] = make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
   uint32_t sr[BF_PT];  // slot << 16 | rank in the slot's group
 #pragma unroll
   for (int i = 0; i < BF_PT; ++i) {
