@@ -807,3 +807,36 @@ def test_paired_rejects_bad_arguments(xtn):
     with pytest.raises(native.XtnError) as ei:
         xtn.search_paired(a, ao, bad, bo, 1)
     assert ei.value.status == native.XTN_ERR_BAD_RESIDUE
+
+
+# ------------------------------------------------------------- profiler ---
+def test_profiler_times_every_kernel_or_only_the_named_one(xtn):
+    """xtn_profile_enable brackets every launch with events, tagged with its
+    algorithmic bytes; xtn_profile_only restricts that to one kernel name."""
+    seqs, off = gen.workload(gen.SELF_1M, 50_000)
+    ds, do = _dev(seqs, off)
+    want = _rows(xtn.search_self(ds, do, 2))
+    xtn.profile_report()
+    try:
+        xtn.profile_enable(True)
+        got = _rows(xtn.search_self(ds, do, 2))
+        every = xtn.profile_report()
+        xtn.profile_only("k_onesweep_records")
+        xtn.search_self(ds, do, 2)
+        only = xtn.profile_report()
+    finally:
+        xtn.profile_enable(False)
+        xtn.profile_only(None)
+    assert np.array_equal(got, want)
+    kernels = {k: v for k, v in every.items() if not k.startswith("host_")}
+    for name in ("k_encode", "k_expand", "k_onesweep_records", "k_bucket_filter",
+                 "k_verify_candidates", "k_onesweep_pairs", "k_unique_finalize"):
+        assert name in kernels, name
+        launches, ms, nbytes = kernels[name]
+        assert launches >= 1 and ms > 0 and nbytes > 0
+    assert "host_call_search_self" in every
+    assert set(only) == {"k_onesweep_records"}
+    assert only["k_onesweep_records"][0] == kernels["k_onesweep_records"][0]
+    # 16 algorithmic bytes per record and pass
+    n_rec = only["k_onesweep_records"][2] / 16 / only["k_onesweep_records"][0]
+    assert n_rec == int(n_rec) and n_rec > 50_000
