@@ -597,8 +597,35 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   }
   __syncthreads();
 
-  // 6. bucket starts of the fast case: digit t's runs sit at [start, end) of
-  // the tile, end being where step 4 left the bin's counter
+  // 6. write out in digit order (UW: a full tile's ITEMS keys per thread
+  // unrolled); the per-key bucket marks of the slow case in a loop of their own
+  const bool mark_each = bucket_start && !fast;
+  const int tile_n = full ? TILE : (int)(n - tile_base);
+  auto write_one = [&](int j, bool mark) {
+    const uint64_t k = s_keys[j];
+    const uint32_t dig = digit_of(k, shift);
+    if (next_hist) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
+    const int64_t o = s_obase[dig] + j;
+    if (o >= 0 && o < n) out[o] = k;
+    else atomicOr(err, DERR_RANGE);
+    if (mark && o >= 0 && o < n) {
+      const uint64_t b = k >> lo;
+      if (j == (int)s_tstart[dig] || b != (s_keys[j - 1] >> lo))
+        atomicMin(&bucket_start[b], (unsigned long long)o);
+    }
+  };
+  if (mark_each) {
+    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, true);
+  } else if (UW && full) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) write_one((int)threadIdx.x + i * THREADS, false);
+  } else {
+    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, false);
+  }
+
+  // 7. bucket starts of the fast case, after the write-out (which they do not
+  // delay): digit t's runs sit at [start, end) of the tile, end being where
+  // step 4 left the bin's counter
   if (bucket_start && fast && threadIdx.x < RADIX) {
     uint32_t start = s_tstart[threadIdx.x];
 #pragma unroll
@@ -614,28 +641,6 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     }
   }
 
-  // 7. write out in digit order (UW: a full tile's ITEMS keys per thread unrolled)
-  const bool mark_each = bucket_start && !fast;
-  const int tile_n = full ? TILE : (int)(n - tile_base);
-  auto write_one = [&](int j) {
-    const uint64_t k = s_keys[j];
-    const uint32_t dig = digit_of(k, shift);
-    if (next_hist) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
-    const int64_t o = s_obase[dig] + j;
-    if (o >= 0 && o < n) out[o] = k;
-    else atomicOr(err, DERR_RANGE);
-    if (mark_each && o >= 0 && o < n) {
-      const uint64_t b = k >> lo;
-      if (j == (int)s_tstart[dig] || b != (s_keys[j - 1] >> lo))
-        atomicMin(&bucket_start[b], (unsigned long long)o);
-    }
-  };
-  if (UW && full) {
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) write_one((int)threadIdx.x + i * THREADS);
-  } else {
-    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j);
-  }
   if (next_hist) {  // uniform over the block
     __syncthreads();
     if (threadIdx.x < RADIX && s_next[threadIdx.x])
