@@ -598,13 +598,14 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   __syncthreads();
 
   // 6. write out in digit order (UW: a full tile's ITEMS keys per thread
-  // unrolled); the per-key bucket marks of the slow case in a loop of their own
+  // unrolled); the per-key bucket marks of the slow case and the next pass's
+  // digit counts in a loop of their own
   const bool mark_each = bucket_start && !fast;
   const int tile_n = full ? TILE : (int)(n - tile_base);
-  auto write_one = [&](int j, bool mark) {
+  auto write_one = [&](int j, bool mark, bool count) {
     const uint64_t k = s_keys[j];
     const uint32_t dig = digit_of(k, shift);
-    if (next_hist) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
+    if (count) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
     const int64_t o = s_obase[dig] + j;
     if (o >= 0 && o < n) out[o] = k;
     else atomicOr(err, DERR_RANGE);
@@ -614,13 +615,14 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
         atomicMin(&bucket_start[b], (unsigned long long)o);
     }
   };
-  if (mark_each) {
-    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, true);
+  const bool count = next_hist != nullptr;
+  if (mark_each || count) {
+    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, mark_each, count);
   } else if (UW && full) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) write_one((int)threadIdx.x + i * THREADS, false);
+    for (int i = 0; i < ITEMS; ++i) write_one((int)threadIdx.x + i * THREADS, false, false);
   } else {
-    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, false);
+    for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, false, false);
   }
 
   // 7. bucket starts of the fast case, after the write-out (which they do not
