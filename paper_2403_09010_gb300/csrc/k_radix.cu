@@ -481,20 +481,29 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
     if (HIW) return ((uint32_t)(k >> 32) >> (sh - 32)) & dmask;
     return (uint32_t)(k >> sh) & dmask;
   };
-  auto run_of = [&](uint64_t k, int at) -> uint32_t {  // at: lo, or step 4's copy of it
+  // a run outside [0, OS_RUNS) means the input was not sorted on the lower
+  // bits: clamped, and reported once per thread (`bad`) after the loop
+  auto run_of = [&](uint64_t k, int at, uint32_t& bad) -> uint32_t {  // at: lo, or step 4's copy
     const uint32_t r = HIW ? (((uint32_t)(k >> 32) >> (at - 32)) & lmask32) - lf32
                            : (uint32_t)((k >> at) & lmask) - lf32;
-    if (r < (uint32_t)OS_RUNS) return r;
-    atomicOr(err, DERR_RANGE);  // the input was not sorted on the lower bits
-    return (uint32_t)(OS_RUNS - 1);
+    bad |= r >= (uint32_t)OS_RUNS;
+    return min(r, (uint32_t)(OS_RUNS - 1));
   };
 
   // 2. counts: bins (run, digit) for the tile, or (warp, digit)
   if (fast) {
+    uint32_t bad = 0;
+    if (full) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i)
-      if (full || i * 32 + (int)lane < wn)
-        atomicAdd(&s_cnt[run_of(key[i], lo) * RADIX + digit_of(key[i], shift)], 1u);
+      for (int i = 0; i < ITEMS; ++i)
+        atomicAdd(&s_cnt[run_of(key[i], lo, bad) * RADIX + digit_of(key[i], shift)], 1u);
+    } else {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        if (i * 32 + (int)lane < wn)
+          atomicAdd(&s_cnt[run_of(key[i], lo, bad) * RADIX + digit_of(key[i], shift)], 1u);
+    }
+    if (bad) atomicOr(err, DERR_RANGE);
   } else {
     uint32_t* wc = s_cnt + warp * RADIX;
 #pragma unroll
@@ -553,15 +562,22 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   const int sh4 = s_shift;
   const int lo4 = sh4 - lbits;
   if (fast) {
+    uint32_t bad = 0;
+    auto place = [&](int i) {
+      const uint32_t bin = run_of(key[i], lo4, bad) * RADIX + digit_of(key[i], sh4);
+      const uint32_t pos = atomicAdd(&s_cnt[bin], 1u);
+      bad |= pos >= (uint32_t)TILE;
+      if (pos < (uint32_t)TILE) s_keys[pos] = key[i];
+    };
+    if (full) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      if (full || i * 32 + (int)lane < wn) {
-        const uint32_t bin = run_of(key[i], lo4) * RADIX + digit_of(key[i], sh4);
-        const uint32_t pos = atomicAdd(&s_cnt[bin], 1u);
-        if (pos < (uint32_t)TILE) s_keys[pos] = key[i];
-        else atomicOr(err, DERR_RANGE);
-      }
+      for (int i = 0; i < ITEMS; ++i) place(i);
+    } else {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        if (i * 32 + (int)lane < wn) place(i);
     }
+    if (bad) atomicOr(err, DERR_RANGE);
   } else {
     uint32_t* wc = s_cnt + warp * RADIX;
     const uint32_t lt_mask = (1u << lane) - 1u;
