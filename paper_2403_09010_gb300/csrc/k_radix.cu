@@ -618,14 +618,16 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   // digit counts in a loop of their own
   const bool mark_each = bucket_start && !fast;
   const int tile_n = full ? TILE : (int)(n - tile_base);
+  uint32_t bad_out = 0;  // an output position out of range, reported once
   auto write_one = [&](int j, bool mark, bool count) {
     const uint64_t k = s_keys[j];
     const uint32_t dig = digit_of(k, shift);
     if (count) atomicAdd(&s_next[(uint32_t)(k >> (shift + 8)) & ((1u << next_bits) - 1u)], 1u);
     const int64_t o = s_obase[dig] + j;
-    if (o >= 0 && o < n) out[o] = k;
-    else atomicOr(err, DERR_RANGE);
-    if (mark && o >= 0 && o < n) {
+    const bool in = o >= 0 && o < n;
+    bad_out |= !in;
+    if (in) out[o] = k;
+    if (mark && in) {
       const uint64_t b = k >> lo;
       if (j == (int)s_tstart[dig] || b != (s_keys[j - 1] >> lo))
         atomicMin(&bucket_start[b], (unsigned long long)o);
@@ -640,6 +642,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
   } else {
     for (int j = threadIdx.x; j < tile_n; j += THREADS) write_one(j, false, false);
   }
+  if (bad_out) atomicOr(err, DERR_RANGE);
 
   // 7. bucket starts of the fast case, after the write-out (which they do not
   // delay): digit t's runs sit at [start, end) of the tile, end being where
